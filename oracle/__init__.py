@@ -1,0 +1,275 @@
+"""FP64 CPU oracle of the split-form DGSEM hot path -- TEST INFRASTRUCTURE ONLY.
+
+A plain, slow restatement (``dgsem_oracle.c``) of what arXiv 2306.12891's solver
+computes: the split-form DGSEM right-hand side on curved hexahedra (Sec. 2, Sec. 4.1),
+its explicit Runge-Kutta step (Sec. 2, Eq. (1)), the modified Persson indicator
+(Sec. 4.1, Eq. (4)) and the DG/FV blend (Sec. 4.1, Eq. (3)).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+may import this package. The CUDA path never does, and this package never imports the
+CUDA path: the two share no code.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "dgsem_oracle.c")
+HDR = os.path.join(HERE, "dgsem_oracle.h")
+LIB_PATH = os.path.join(HERE, "_build", "liboracle.so")
+
+EQUATIONS = {"euler": 0, "ns": 1, "navier_stokes": 1}
+VFLUX = {"kg": 0, "pirozzoli": 1, "ec": 2, "central": 3}
+SFLUX = {"llf": 0, "roe": 1, "ec": 2}
+# s = ln((1 - 1e-4) / 1e-4): the sigmoid sharpness of Hennemann et al. (not printed in the paper)
+DEFAULT_SHARPNESS = float(np.log((1.0 - 1e-4) / 1e-4))
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with plain -O2 and no FMA contraction (same results on x86 and Arm)."""
+    os.makedirs(os.path.dirname(LIB_PATH), exist_ok=True)
+    newest = max(os.path.getmtime(SRC), os.path.getmtime(HDR))
+    if force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < newest:
+        tmp = LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math", "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("n_elems", ctypes.c_int), ("xyz", ctypes.POINTER(ctypes.c_double)),
+                ("n_faces", ctypes.c_int), ("faces", ctypes.POINTER(ctypes.c_int)),
+                ("equations", ctypes.c_int), ("vflux", ctypes.c_int), ("sflux", ctypes.c_int),
+                ("gamma", ctypes.c_double), ("R", ctypes.c_double), ("mu", ctypes.c_double),
+                ("Pr", ctypes.c_double), ("shock_capturing", ctypes.c_int), ("alpha_min", ctypes.c_double),
+                ("alpha_max", ctypes.c_double), ("sharpness", ctypes.c_double),
+                ("alpha_fixed", ctypes.c_double)]
+
+
+_DP = ctypes.POINTER(ctypes.c_double)
+RHS_FN = ctypes.CFUNCTYPE(None, _DP, _DP, ctypes.c_double, ctypes.c_void_p)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(LIB_PATH)
+        vp = ctypes.c_void_p
+        L.orc_create.restype = vp
+        L.orc_create.argtypes = [ctypes.POINTER(_Problem), ctypes.POINTER(ctypes.c_int)]
+        L.orc_destroy.argtypes = [vp]
+        L.orc_state_Ja.restype = vp
+        L.orc_state_Ja.argtypes = [vp]
+        L.orc_state_J.restype = vp
+        L.orc_state_J.argtypes = [vp]
+        L.orc_rhs.argtypes = [vp, vp, vp, vp, vp]
+        L.orc_indicator.argtypes = [vp, vp, vp, vp]
+        L.orc_lserk_step.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double]
+        L.orc_invariants.argtypes = [vp, vp, vp, vp]
+        L.orc_max_dt.argtypes = [vp, vp, ctypes.c_double, vp]
+        L.orc_lgl.argtypes = [ctypes.c_int, vp, vp]
+        L.orc_dmatrix.argtypes = [ctypes.c_int, vp, vp]
+        L.orc_legendre_vandermonde.argtypes = [ctypes.c_int, vp, vp]
+        L.orc_invert.argtypes = [ctypes.c_int, vp, vp]
+        L.orc_metrics.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp]
+        L.orc_logmean.restype = ctypes.c_double
+        L.orc_logmean.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.orc_flux_contra.argtypes = [vp, vp, ctypes.c_double, vp]
+        L.orc_twopoint.argtypes = [ctypes.c_int, vp, vp, vp, vp, ctypes.c_double, vp]
+        L.orc_riemann.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_double, vp]
+        L.orc_viscous_flux.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp]
+        L.orc_lserk_generic.argtypes = [ctypes.c_int, vp, ctypes.c_double, ctypes.c_double, RHS_FN, vp]
+        L.orc_lserk_coefficients.argtypes = [vp, vp, vp]
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------- basis and geometry
+
+def lgl(N: int):
+    xi, w = np.zeros(N + 1), np.zeros(N + 1)
+    if lib().orc_lgl(N, _p(xi), _p(w)) != 0:
+        raise ValueError("N out of range")
+    return xi, w
+
+
+def dmatrix(N: int, xi=None) -> np.ndarray:
+    if xi is None:
+        xi = lgl(N)[0]
+    D = np.zeros((N + 1, N + 1))
+    lib().orc_dmatrix(N, _p(_f64(xi)), _p(D))
+    return D
+
+
+def legendre_vandermonde(N: int, xi=None) -> np.ndarray:
+    if xi is None:
+        xi = lgl(N)[0]
+    V = np.zeros((N + 1, N + 1))
+    lib().orc_legendre_vandermonde(N, _p(_f64(xi)), _p(V))
+    return V
+
+
+def metrics(N: int, xyz: np.ndarray):
+    xyz = _f64(xyz)
+    nE = xyz.shape[0]
+    n = N + 1
+    Ja = np.zeros((nE, 3, 3, n, n, n))
+    J = np.zeros((nE, n, n, n))
+    lib().orc_metrics(N, nE, _p(xyz), _p(Ja), _p(J))
+    return Ja, J
+
+
+# ---------------------------------------------------------------- pointwise fluxes
+
+def logmean(a: float, b: float) -> float:
+    return lib().orc_logmean(a, b)
+
+
+def flux_contra(U, a, gamma=1.4):
+    F = np.zeros(5)
+    lib().orc_flux_contra(_p(_f64(U)), _p(_f64(a)), gamma, _p(F))
+    return F
+
+
+def twopoint(kind: str, UL, UR, aL, aR, gamma=1.4):
+    F = np.zeros(5)
+    lib().orc_twopoint(VFLUX[kind], _p(_f64(UL)), _p(_f64(UR)), _p(_f64(aL)), _p(_f64(aR)), gamma, _p(F))
+    return F
+
+
+def riemann(kind: str, UL, UR, n, gamma=1.4):
+    F = np.zeros(5)
+    lib().orc_riemann(SFLUX[kind], _p(_f64(UL)), _p(_f64(UR)), _p(_f64(n)), gamma, _p(F))
+    return F
+
+
+def viscous_flux(U, gradU, gradT, mu, kappa, gamma=1.4):
+    Fv = np.zeros(15)
+    lib().orc_viscous_flux(_p(_f64(U)), _p(_f64(gradU)), _p(_f64(gradT)), mu, kappa, gamma, _p(Fv))
+    return Fv.reshape(3, 5)
+
+
+def lserk_coefficients():
+    A, B, c = np.zeros(5), np.zeros(5), np.zeros(5)
+    lib().orc_lserk_coefficients(_p(A), _p(B), _p(c))
+    return A, B, c
+
+
+def lserk_generic(u0, dt: float, t: float, f):
+    """One LSERK(5,4) step of u' = f(u, t) for a Python callable f(u, t) -> ndarray."""
+    u = _f64(u0).copy()
+    n = u.size
+
+    def cb(up, utp, tt, ctx):
+        uu = np.ctypeslib.as_array(up, shape=(n,)).copy()
+        out = np.ctypeslib.as_array(utp, shape=(n,))
+        out[:] = f(uu, tt)
+
+    fn = RHS_FN(cb)
+    lib().orc_lserk_generic(n, _p(u), dt, t, fn, None)
+    return u
+
+
+# ---------------------------------------------------------------- solver
+
+class Oracle:
+    """The oracle solver for one mesh and one set of physics parameters."""
+
+    def __init__(self, N, xyz, faces, equations="euler", vflux="kg", sflux="llf", gamma=1.4, R=1.0,
+                 mu=0.0, Pr=0.72, shock_capturing=False, alpha_min=0.01, alpha_max=0.7,
+                 sharpness=DEFAULT_SHARPNESS, alpha_fixed=-1.0):
+        self.N = int(N)
+        self.n = self.N + 1
+        self.xyz = _f64(xyz)
+        self.faces = np.ascontiguousarray(faces, dtype=np.int32)
+        self.nE = self.xyz.shape[0]
+        pb = _Problem()
+        pb.N = self.N
+        pb.n_elems = self.nE
+        pb.xyz = self.xyz.ctypes.data_as(_DP)
+        pb.n_faces = self.faces.shape[0]
+        pb.faces = self.faces.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        pb.equations = EQUATIONS[equations]
+        pb.vflux = VFLUX[vflux]
+        pb.sflux = SFLUX[sflux]
+        pb.gamma, pb.R, pb.mu, pb.Pr = gamma, R, mu, Pr
+        pb.shock_capturing = int(bool(shock_capturing))
+        pb.alpha_min, pb.alpha_max, pb.sharpness = alpha_min, alpha_max, sharpness
+        pb.alpha_fixed = float(alpha_fixed)
+        self._pb = pb
+        st = ctypes.c_int(0)
+        self._s = lib().orc_create(ctypes.byref(pb), ctypes.byref(st))
+        if not self._s:
+            raise ValueError(f"oracle rejected the problem (status {st.value})")
+        self.shape = (self.nE, 5, self.n, self.n, self.n)
+
+    def __del__(self):
+        if getattr(self, "_s", None):
+            lib().orc_destroy(self._s)
+            self._s = None
+
+    @property
+    def Ja(self) -> np.ndarray:
+        n = self.n
+        ptr = ctypes.cast(lib().orc_state_Ja(self._s), _DP)
+        return np.ctypeslib.as_array(ptr, shape=(self.nE, 3, 3, n, n, n)).copy()
+
+    @property
+    def J(self) -> np.ndarray:
+        n = self.n
+        ptr = ctypes.cast(lib().orc_state_J(self._s), _DP)
+        return np.ctypeslib.as_array(ptr, shape=(self.nE, n, n, n)).copy()
+
+    def _U(self, U):
+        U = _f64(U)
+        if U.size != int(np.prod(self.shape)):
+            raise ValueError("U has the wrong size")
+        return U
+
+    def rhs(self, U, mask=None, return_alpha=False):
+        U = self._U(U)
+        Ut = np.zeros(self.shape)
+        alpha = np.zeros(self.nE)
+        m = None
+        if mask is not None:
+            m = np.zeros(self.nE, dtype=np.uint8)
+            m[np.asarray(mask)] = 1
+        lib().orc_rhs(self._s, _p(U), _p(Ut), _p(m) if m is not None else None, _p(alpha))
+        return (Ut, alpha) if return_alpha else Ut
+
+    def indicator(self, U):
+        U = self._U(U)
+        raw, a = np.zeros(self.nE), np.zeros(self.nE)
+        lib().orc_indicator(self._s, _p(U), _p(raw), _p(a))
+        return raw, a
+
+    def lserk_step(self, U, dt, t=0.0):
+        U = self._U(U).copy()
+        lib().orc_lserk_step(self._s, _p(U), float(dt), float(t))
+        return U
+
+    def invariants(self, U, Ut):
+        out = np.zeros(8)
+        lib().orc_invariants(self._s, _p(self._U(U)), _p(self._U(Ut)), _p(out))
+        return out
+
+    def max_dt(self, U, cfl):
+        dt = np.zeros(1)
+        lib().orc_max_dt(self._s, _p(self._U(U)), float(cfl), _p(dt))
+        return float(dt[0])
