@@ -191,7 +191,10 @@ static void dderiv(int N, const double *D, const double *f, int d, double *out) 
 }
 
 /* Ja^i_n = d_k (X_l d_j X_m) - d_j (X_l d_k X_m), (i,j,k) and (n,m,l) cyclic;
- * J = det(dX_c/dxi_j) with derivatives by D. */
+ * J = det(dX_c/dxi_j) with derivatives by D.
+ * The metric terms do not depend on the coordinate origin (a constant added to X_l cancels
+ * since d_j d_k = d_k d_j), so X is taken relative to the element's first node: with absolute
+ * coordinates the products X_l d_j X_m are O(|x|/h) larger than the result and round badly. */
 int orc_metrics(int N, int n_elems, const double *xyz, double *Ja, double *J) {
   if (N < 1 || N > NMAX) return -1;
   int n = N + 1, nnn = n * n * n;
@@ -203,8 +206,11 @@ int orc_metrics(int N, int n_elems, const double *xyz, double *Ja, double *J) {
   double *B = (double *)malloc(sizeof(double) * nnn);
   double *dA = (double *)malloc(sizeof(double) * nnn);
   double *dB = (double *)malloc(sizeof(double) * nnn);
+  double *X = (double *)malloc(sizeof(double) * 3 * nnn);
   for (int e = 0; e < n_elems; ++e) {
-    const double *X = xyz + (size_t)e * 3 * nnn;
+    const double *Xabs = xyz + (size_t)e * 3 * nnn;
+    for (int c = 0; c < 3; ++c)
+      for (int node = 0; node < nnn; ++node) X[c * nnn + node] = Xabs[c * nnn + node] - Xabs[c * nnn];
     for (int c = 0; c < 3; ++c)
       for (int d = 0; d < 3; ++d) dderiv(N, D, X + c * nnn, d, dX + (c * 3 + d) * nnn);
     for (int i = 0; i < 3; ++i) {
@@ -230,7 +236,7 @@ int orc_metrics(int N, int n_elems, const double *xyz, double *Ja, double *J) {
                                   a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
     }
   }
-  free(dX); free(A); free(B); free(dA); free(dB);
+  free(X); free(dX); free(A); free(B); free(dA); free(dB);
   return 0;
 }
 
@@ -403,8 +409,6 @@ struct orc_state {
   double *Gvis;     /* [nE][6][5][nn] outward viscous surface flux */
   double *alpha_raw;
   unsigned char *mark;
-  double *g;        /* LSERK register */
-  double *Ut;       /* stage derivative */
 };
 
 static double kappa_of(const orc_problem *pb) {
@@ -453,13 +457,13 @@ orc_state *orc_create(const orc_problem *pb, int *status) {
     if (s->slot_face[i] < 0) { orc_destroy(s); *status = -2; return NULL; }
   for (size_t i = 0; i < (size_t)nE * nnn; ++i)
     if (!(s->J[i] > 0.0)) { orc_destroy(s); *status = -3; return NULL; }
-  s->grad = (double *)calloc((size_t)nE * 12 * nnn, sizeof(double));
+  if (pb->equations == ORC_NAVIER_STOKES) { /* viscous buffers only where they are used */
+    s->grad = (double *)calloc((size_t)nE * 12 * nnn, sizeof(double));
+    s->Gvis = (double *)calloc((size_t)nE * 6 * NVAR * nn, sizeof(double));
+  }
   s->Gadv = (double *)calloc((size_t)nE * 6 * NVAR * nn, sizeof(double));
-  s->Gvis = (double *)calloc((size_t)nE * 6 * NVAR * nn, sizeof(double));
   s->alpha_raw = (double *)calloc(nE, sizeof(double));
   s->mark = (unsigned char *)calloc(nE, 1);
-  s->g = (double *)calloc((size_t)nE * NVAR * nnn, sizeof(double));
-  s->Ut = (double *)calloc((size_t)nE * NVAR * nnn, sizeof(double));
   *status = 0;
   return s;
 }
@@ -468,7 +472,7 @@ void orc_destroy(orc_state *s) {
   if (!s) return;
   free(s->Ja); free(s->J); free(s->slot_face); free(s->slot_side); free(s->slot_nbelem);
   free(s->slot_nbnode); free(s->grad); free(s->Gadv); free(s->Gvis); free(s->alpha_raw);
-  free(s->mark); free(s->g); free(s->Ut);
+  free(s->mark);
   free(s);
 }
 
@@ -780,8 +784,10 @@ int orc_rhs(orc_state *s, const double *U, double *Ut, const unsigned char *out_
         for (int v = 0; v < NVAR; ++v) {
           s->Gadv[(((size_t)eL * 6 + fL) * NVAR + v) * nn + p + n * q] = sa * Fa[v];
           s->Gadv[(((size_t)eR * 6 + fR) * NVAR + v) * nn + p2 + n * q2] = -sa * Fa[v];
-          s->Gvis[(((size_t)eL * 6 + fL) * NVAR + v) * nn + p + n * q] = sa * Fv[v];
-          s->Gvis[(((size_t)eR * 6 + fR) * NVAR + v) * nn + p2 + n * q2] = -sa * Fv[v];
+          if (ns) {
+            s->Gvis[(((size_t)eL * 6 + fL) * NVAR + v) * nn + p + n * q] = sa * Fv[v];
+            s->Gvis[(((size_t)eR * 6 + fR) * NVAR + v) * nn + p2 + n * q2] = -sa * Fv[v];
+          }
         }
       }
   }

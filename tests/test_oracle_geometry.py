@@ -21,6 +21,23 @@ def test_affine_metrics(oracle_mod):
             np.testing.assert_allclose(Ja[:, d, c], expect[d, c], rtol=0, atol=1e-13)
 
 
+def test_affine_metrics_far_from_the_origin(oracle_mod):
+    """Fine elements at coordinates ~2*pi: the metric terms must not lose accuracy to the
+    coordinate offset (they are translation invariant)."""
+    N = 7
+    for K in (4, 32):
+        xyz, _ = W.box_mesh(N, (K, K, K))
+        last = xyz[-1:]  # the element farthest from the origin
+        Ja, J = oracle_mod.metrics(N, last)
+        h2 = np.pi / K
+        # the node coordinates themselves carry ~1e-16 * 2 pi of rounding, which |D| ~ N^2/4
+        # amplifies to a few 1e-13 relative; absolute coordinates in the products cost 3e-12
+        # (K = 4) and 1e-10 (K = 32)
+        np.testing.assert_allclose(J, h2 ** 3, rtol=5e-13)
+        np.testing.assert_allclose(Ja[:, 0, 0], h2 ** 2, rtol=5e-13)
+        assert np.abs(Ja[:, 0, 1:]).max() < 5e-13 * h2 ** 2
+
+
 def _divergence(D, F):
     """sum_d D_d F^d over one element's nodal arrays F[d][k][j][i]."""
     out = np.einsum("im,kjm->kji", D, F[0])
