@@ -1,0 +1,297 @@
+"""Benchmark of the DGSEM hot path on GB300: LSERK(5,4) steps of the N=7 curved Taylor-Green
+Navier-Stokes workload (Pirozzoli split form, Roe, BR1; 32^3 elements, 16.8M DOF), FP64.
+
+One step = one LSERK(5,4) time step = five right-hand-side evaluations plus the stage updates
+over the whole mesh. Reported metric: DOF-stage updates per second (= 1/PID per GPU, the
+paper's performance index, Sec. 2 Eq. (1), with #cores := #GPUs), plus the PID itself.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+For N > 1 (launched by torch.distributed.run) every rank runs an independent replica of the
+workload (the path is not sharded in this build); value = total DOF-stage updates / max time.
+`--impl reference` times the FP64 CPU oracle (single-threaded) on a bounded sample of the same
+workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2306_12891_gb300.workloads import WORKLOADS  # noqa: E402
+
+WORKLOAD = "tgv_ns_n7_32x32x32_curved"
+METRIC = "DOF-stage updates/s (1/PID), N=7 split-form Navier-Stokes, FP64"
+UNIT = "DOF-stage/s"
+STAGES = 5
+
+
+def volume_kernel_flops_per_element(N: int, navier_stokes: bool) -> float:
+    """Algorithmic FP64 flops of one volume-kernel launch per element (FMA = 2 flops), counted
+    from the formulas the kernel evaluates:
+      pair flux (Pirozzoli, plain sums, 1/2 factors folded into D):
+        6 sums + V (mul + 2 FMA = 5) + F_rho (add + mul = 2) + p-sum 1 + momentum 3 x (mul + FMA) = 9
+        + energy (add + mul = 2) + accumulation into both nodes 10 FMA = 20        -> 45 per pair,
+        3 n^2 n(n-1)/2 pairs per element;
+      per node: primitives 15; direction sum 10; surface terms 10 per face point (6 n^2 per element);
+        Jacobian 5; LSERK update 25; Navier-Stokes: viscous divergence 3*4*N FMA = 24 N,
+        neighbour viscous trace 8 per face point, 4 subtractions."""
+    n = N + 1
+    pairs = 3 * n * n * n * (n - 1) // 2
+    per_node = 15 + 10 + 5 + 25 + ((24 * N + 4) if navier_stokes else 0)
+    per_face_pt = 10 + (8 if navier_stokes else 0)
+    return 45.0 * pairs + per_node * n ** 3 + per_face_pt * 6 * n * n
+
+
+def dist_setup(n_gpus: int):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as td
+
+        torch.cuda.set_device(local)
+        td.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as td
+
+        td.barrier()
+
+
+def max_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as td
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(device_index), "-lms", "200"], stdout=self.file,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.file.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(steps_budget_s: float = 20.0) -> dict:
+    """The FP64 oracle, as it stands, single-threaded on the host: LSERK(5,4) stages of the same
+    physics on a 6^3-element sub-box of the workload (110,592 DOF), until ~steps_budget_s."""
+    import oracle
+
+    oracle.build()
+    w = WORKLOADS[WORKLOAD].with_(nel=(6, 6, 6))
+    xyz, faces = w.mesh()
+    U = w.initial_state(xyz)
+    ref = oracle.Oracle(w.N, xyz, faces, **w.physics())
+    t0 = time.perf_counter()
+    stages = 0
+    while True:
+        ref.rhs(U)
+        stages += 1
+        if time.perf_counter() - t0 > steps_budget_s or stages >= 10:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": w.dofs * stages / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{stages} right-hand sides of the same physics on a 6x6x6-element sub-box "
+                      f"({w.dofs} DOF), single-threaded FP64 C oracle, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the oracle timed on the host cores, on bounded samples of the workload."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    w = WORKLOADS[WORKLOAD].with_(nel=(3, 3, 3))
+    xyz, faces = w.mesh()
+    U = w.initial_state(xyz)
+    ref = oracle.Oracle(w.N, xyz, faces, **w.physics())
+    dt = ref.max_dt(U, w.cfl)
+    for _ in range(args.warmup):
+        U = ref.lserk_step(U, dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U = ref.lserk_step(U, dt)
+    el = time.perf_counter() - t0
+    value = w.dofs * STAGES * args.steps / el
+    sample = (f"each step: one LSERK(5,4) step of the same physics on a 3x3x3-element sub-box ({w.dofs} DOF), "
+              f"single-threaded FP64 C oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_elements": w.n_elems, "N": w.N},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_2306_12891_gb300 import build, dg
+
+    world, rank, local = dist_setup(args.gpus)
+    if rank == 0 or not os.path.exists(dg.LIB_PATH):
+        build.build()
+    barrier(world)
+    w = WORKLOADS[WORKLOAD]
+    xyz, faces = w.mesh()
+    U0 = w.initial_state(xyz)
+    stream = torch.cuda.current_stream()
+    solver = dg.DG(w.N, xyz, faces, stream=stream, **w.physics())
+    U = torch.from_numpy(U0).cuda()
+    dt = solver.max_dt(U, w.cfl)
+    peak_fp64 = dg.probe_fma("fp64", stream)
+
+    # device-resident timed region
+    solver.lserk_steps(U, dt, args.warmup)
+    solver.check()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local)
+    solver.timing_enable(True)
+    solver.timing_get()  # reset
+    l0 = solver.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    solver.lserk_steps(U, dt, args.steps, t=args.warmup * dt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    launches = solver.launch_count() - l0
+    ktimes = solver.timing_get()
+    solver.timing_enable(False)
+    solver.check()
+    ms = max_over_ranks(world, ms)
+
+    # end to end through the host-buffer entry point: copies in and out every step
+    Uh = torch.from_numpy(U.cpu().numpy()).pin_memory()
+    solver.lserk_step_host(Uh, dt)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 5))
+    for k in range(e2e_steps):
+        solver.lserk_step_host(Uh, dt)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+
+    dofs = w.dofs
+    total_updates = world * dofs * STAGES * args.steps
+    value = total_updates / (ms * 1e-3)
+    vol_ms, vol_n = ktimes.get("volume", (0.0, 0))
+    flops_launch = volume_kernel_flops_per_element(w.N, True) * w.n_elems
+    achieved = flops_launch / (vol_ms / vol_n * 1e-3) if vol_n else None
+    state_bytes = U.numel() * 8
+    if rank != 0:
+        return
+    breakdown = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / max(1e-9, sum(x[0] for x in ktimes.values())), 4)}
+                 for k, v in ktimes.items() if v[1]}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": w.N, "elements": w.n_elems, "dofs": dofs,
+                   "physics": "Navier-Stokes, Pirozzoli split form, Roe, BR1, curved mesh, TGV Re 1600 Ma 0.1",
+                   "precision": "fp64", "dt": dt, "cfl": w.cfl,
+                   "l2": f"inputs larger than L2 (state {state_bytes / 1e6:.0f} MB, working set > 5 GB)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "pid_s_per_dof_stage": 1.0 / (value / world),
+        "roofline": {"bound": "alu", "kernel": "volume (split-form flux differencing, FP64 pipe)",
+                     "achieved": achieved / 1e12 if achieved else None, "peak": peak_fp64 / 1e12,
+                     "unit": "TFLOP/s", "frac": (achieved / peak_fp64) if achieved else None, "traffic": None,
+                     "flops_per_launch": flops_launch, "peak_source": "measured FP64 FMA probe (dg_probe_fma), live"},
+        "kernels": breakdown,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "e2e": {"value": world * dofs * STAGES * e2e_steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
+    }
+    if args.cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

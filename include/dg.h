@@ -1,0 +1,143 @@
+/*
+ * dg.h -- C ABI of libdg, a GB300 (sm_103a) implementation of the explicit split-form DGSEM
+ * hot path of "Towards Exascale CFD Simulations Using the Discontinuous Galerkin Solver FLEXI"
+ * (arXiv 2306.12891): the right-hand side of the compressible Euler / Navier-Stokes-Fourier
+ * equations on curved hexahedra with Legendre-Gauss-Lobatto nodes (Sec. 2), its explicit
+ * low-storage Runge-Kutta stage update (Sec. 2, Eq. (1)), and the DG/FV subcell blend with the
+ * modified Persson indicator (Sec. 4.1, Eqs. (3)-(4)).
+ *
+ * Conventions
+ *  - n = N+1; node index = i + n*(j + n*k), i along xi.
+ *  - Solution arrays U, Ut: FP64, layout [n_elems][5][n][n][n] with the conservative variables
+ *    (rho, rho u, rho v, rho w, E). Unless a name ends in _host, every array argument is a
+ *    DEVICE pointer owned by the caller (e.g. a torch tensor) and must stay valid until the
+ *    work queued on the context's stream has finished.
+ *  - All solver calls are asynchronous on the context's CUDA stream, except those documented as
+ *    synchronising. No call throws; a non-zero dg_status is returned and dg_last_error() gives
+ *    text. A context is not thread-safe: one host thread at a time.
+ *  - The library owns its geometry (metrics, Jacobian, face normals), its work buffers and the
+ *    LSERK register; dg_free() releases them.
+ */
+#ifndef DG_H
+#define DG_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_ctx dg_ctx; /* opaque, library-owned */
+
+typedef enum {
+  DG_OK = 0,
+  DG_ERR_ARG = -1,          /* bad argument: null pointer, size, enum value, N out of range */
+  DG_ERR_MESH = -2,         /* inconsistent face table (index out of range, face slot unused or reused) */
+  DG_ERR_JACOBIAN = -3,     /* J <= 0 or not finite at some node */
+  DG_ERR_CUDA = -4,         /* a CUDA runtime call failed (text in dg_last_error) */
+  DG_ERR_NONPHYSICAL = -5,  /* rho <= 0, p <= 0 or a non-finite value met by a kernel */
+  DG_ERR_UNSUPPORTED = -6,  /* valid request this build does not implement */
+  DG_ERR_OOM = -7           /* device allocation failed */
+} dg_status;
+
+enum { DG_EULER = 0, DG_NAVIER_STOKES = 1 };
+/* split-form two-point volume fluxes (Sec. 2: "split-form DG formulation"; Sec. 4.1) */
+enum { DG_VFLUX_KG = 0, DG_VFLUX_PIROZZOLI = 1, DG_VFLUX_EC = 2, DG_VFLUX_CENTRAL = 3 };
+/* surface Riemann fluxes */
+enum { DG_SFLUX_LLF = 0, DG_SFLUX_ROE = 1, DG_SFLUX_EC = 2 };
+/* DG_FP64: all arithmetic FP64. DG_FP32_BULK: volume/surface/lifting arithmetic in FP32 with FP32
+ * accumulation; LSERK state, metrics, Jacobian scaling and reductions stay FP64. U, Ut stay FP64. */
+enum { DG_FP64 = 0, DG_FP32_BULK = 1 };
+/* Legendre-Gauss-Lobatto nodes (Sec. 2), the only node set */
+enum { DG_NODES_LGL = 0 };
+
+/* Unstructured hexahedral mesh; elements are the unit of work (Sec. 2). Host memory, read by
+ * dg_init only (copied). Periodic connections are ordinary faces. */
+typedef struct {
+  int n_elems;
+  int n_geo;          /* geometry degree; must equal N (isoparametric, nodes = LGL nodes) */
+  const double *xyz;  /* [n_elems][3][n_geo+1]^3 physical coordinates of the nodes */
+  int n_faces;
+  const int *face;    /* [n_faces][5]: elemL, faceL, elemR, faceR, orient.
+                         local faces 0:xi-, 1:xi+, 2:eta-, 3:eta+, 4:zeta-, 5:zeta+;
+                         face point (p,q) = the two tangential node indices in increasing
+                         dimension order; orient maps L's (p,q) to R's:
+                         (a,b) = bit2 ? (q,p) : (p,q); a = N-a if bit0; b = N-b if bit1 */
+} dg_mesh;
+
+typedef struct {
+  int equations;      /* DG_EULER | DG_NAVIER_STOKES */
+  int volume_flux;    /* DG_VFLUX_* */
+  int surface_flux;   /* DG_SFLUX_* */
+  int precision;      /* DG_FP64 | DG_FP32_BULK */
+  double gamma, R, mu, Pr; /* ideal gas, constant viscosity, Prandtl number */
+  int shock_capturing;     /* 1: DG/FV subcell blend (Sec. 4.1, Eq. (3)) */
+  double alpha_min;        /* alpha < alpha_min -> pure DG (Sec. 4.2: 0.01) */
+  double alpha_max;        /* alpha clipped to alpha_max (Sec. 4.2: 0.7) */
+  double sharpness;        /* s of the indicator sigmoid (Sec. 4.1, Eq. (4)) */
+  double alpha_fixed;      /* >= 0: use this blending coefficient on every element; < 0: indicator */
+} dg_params;
+
+/* Build a solver for `mesh` at polynomial degree N (1..7) with `nodes` = DG_NODES_LGL.
+ * Copies the mesh to the device, computes curl-form metrics, Jacobian and face normals on the
+ * GPU, and checks them. `cuda_stream` (cudaStream_t, may be NULL = legacy default stream) is the
+ * stream every later call is queued on. Synchronising. On success *out owns all device memory. */
+dg_status dg_init(const dg_mesh *mesh, int N, int nodes, const dg_params *params, void *cuda_stream,
+                  dg_ctx **out);
+
+/* Ut = L(U): the DGSEM time derivative at time t (Sec. 2; Sec. 4.1, Eq. (3) when shock capturing
+ * is on). U and Ut are device arrays [n_elems][5][n]^3 and must not overlap. */
+dg_status dg_rhs(dg_ctx *ctx, const double *U, double *Ut, double t);
+
+/* One LSERK(5,4) step (Carpenter-Kennedy 2N-storage, five stages, Sec. 2 "explicit Runge-Kutta"):
+ * U <- U(t + dt), in place. The register g is library-owned. */
+dg_status dg_lserk_step(dg_ctx *ctx, double *U, double dt, double t);
+
+/* n_steps LSERK steps of size dt starting at time t (one graph-free launch sequence). */
+dg_status dg_lserk_steps(dg_ctx *ctx, double *U, double dt, double t, int n_steps);
+
+/* The same step on a HOST array U_host: copies it to a library-owned device buffer, steps, and
+ * copies the result back; synchronising. U_host should be pinned for full copy bandwidth. */
+dg_status dg_lserk_step_host(dg_ctx *ctx, double *U_host, double dt, double t);
+
+/* alpha[e] = blending coefficient of element e (Sec. 4.1, Eq. (4): modified Persson indicator on
+ * rho*p, clipped to [alpha_min, alpha_max] (Sec. 4.2), extended to face neighbours by 1/2).
+ * alpha: device array [n_elems]. */
+dg_status dg_indicator(dg_ctx *ctx, const double *U, double *alpha);
+
+/* Integral diagnostics over the mesh with LGL quadrature (synchronising; host out[8]):
+ * out[0..4] = sum J w Ut_v; out[5] = sum J w v.Ut (v = entropy variables);
+ * out[6] = sum J w rho|u|^2/2; out[7] = sum J w d/dt(rho|u|^2/2). */
+dg_status dg_invariants(dg_ctx *ctx, const double *U, const double *Ut, double out[8]);
+
+/* *dt = cfl * min over nodes of 2J / ((2N+1) sum_d (|u.Ja^d| + c|Ja^d|)) (synchronising). */
+dg_status dg_max_dt(dg_ctx *ctx, const double *U, double cfl, double *dt);
+
+/* DG_OK, or DG_ERR_NONPHYSICAL if any kernel since the last call met rho <= 0, p <= 0 or a
+ * non-finite state (clears the flag; synchronising). */
+dg_status dg_check(dg_ctx *ctx);
+
+/* Copy the device metrics to caller device arrays Ja [n_elems][3 d][3 c][n]^3 and J [n_elems][n]^3. */
+dg_status dg_get_metrics(dg_ctx *ctx, double *Ja, double *J);
+
+/* Kernel timing on the context stream: when enabled, CUDA events bracket every launch and
+ * per-kernel totals accumulate (ms, launches). Names: "face", "lift", "volume", "indicator",
+ * "spread", "other". dg_timing_get fills up to `cap` entries and returns the count. */
+dg_status dg_timing_enable(dg_ctx *ctx, int enable);
+int dg_timing_get(dg_ctx *ctx, const char **names, double *ms, long long *launches, int cap);
+/* total kernel launches issued by this context */
+long long dg_launch_count(const dg_ctx *ctx);
+
+void dg_free(dg_ctx *ctx);
+const char *dg_last_error(const dg_ctx *ctx);
+const char *dg_status_string(int status);
+
+/* Host-only (no GPU needed): the LGL nodes xi[n], weights w[n] and derivative matrix D[n*n]
+ * (D[i*n+j] = l_j'(xi_i)) this library builds its kernels' tables from. */
+dg_status dg_basis(int N, double *xi, double *w, double *D);
+
+/* Measure the GPU's FMA throughput: kind 0 = FP64, 1 = FP32. Runs a bounded FMA-chain kernel on
+ * `cuda_stream` (synchronising) and returns FLOP/s in *flops. */
+dg_status dg_probe_fma(int kind, void *cuda_stream, double *flops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

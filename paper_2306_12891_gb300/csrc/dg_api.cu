@@ -1,0 +1,409 @@
+// dg_api.cu -- the C ABI of libdg (declared in include/dg.h): context set-up, mesh validation,
+// device buffers, the per-stage launch sequence and the LSERK(5,4) driver.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/dg.h"
+#include "dg_internal.h"
+
+namespace {
+
+const DgKernelTable *kernels_for(int N) {
+  switch (N) {
+    case 1: return &dg_kernels_n1;
+    case 2: return &dg_kernels_n2;
+    case 3: return &dg_kernels_n3;
+    case 4: return &dg_kernels_n4;
+    case 5: return &dg_kernels_n5;
+    case 6: return &dg_kernels_n6;
+    case 7: return &dg_kernels_n7;
+    default: return nullptr;
+  }
+}
+
+// constant-memory tables are per device and per degree; upload once
+std::mutex g_upload_mutex;
+std::vector<unsigned> g_uploaded;  // bitmask of degrees per device
+
+enum KernelClass { KC_FACE = 0, KC_LIFT, KC_VOLUME, KC_INDICATOR, KC_SPREAD, KC_OTHER, KC_COUNT };
+const char *kKernelNames[KC_COUNT] = {"face", "lift", "volume", "indicator", "spread", "other"};
+
+// LSERK(5,4) of Carpenter and Kennedy, 2N-storage form (published coefficients)
+const double kA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                      -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+const double kB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                      1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                      2277821191437.0 / 14882151754819.0};
+// (the stage times t + c_s dt are not needed: no boundary condition or source depends on t)
+
+}  // namespace
+
+struct dg_ctx {
+  int N = 0, device = 0;
+  dg_params params{};
+  DgDevice d{};
+  const DgKernelTable *K = nullptr;
+  cudaStream_t stream = nullptr;
+  std::vector<void *> allocs;
+  double *g = nullptr;         // LSERK register
+  double *Ustage = nullptr;    // device copy for the host-buffer entry point (lazy)
+  double *small = nullptr;     // 16 doubles of device scratch for reductions' results
+  int *flag_host = nullptr;
+  std::string err;
+  long long launches = 0;
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+  std::vector<int> ev_class;
+  size_t ev_used = 0;
+  double t_ms[KC_COUNT] = {0};
+  long long t_count[KC_COUNT] = {0};
+  size_t n_state = 0;          // doubles in U
+};
+
+namespace {
+
+dg_status fail(dg_ctx *c, dg_status s, const std::string &msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+dg_status cuda_fail(dg_ctx *c, cudaError_t e, const char *where) {
+  return fail(c, DG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <class T>
+dg_status dev_alloc(dg_ctx *c, T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return DG_OK;
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, DG_ERR_OOM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) + " bytes failed");
+  }
+  c->allocs.push_back(q);
+  *p = static_cast<T *>(q);
+  return DG_OK;
+}
+
+// Run one launch (a callable) with launch counting, optional event timing and error check.
+template <class F>
+dg_status launch(dg_ctx *c, int kc, F &&f) {
+  if (c->timing) {
+    if (c->ev_used == c->ev_pool.size()) {
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      c->ev_pool.push_back({a, b});
+      c->ev_class.push_back(kc);
+    }
+    c->ev_class[c->ev_used] = kc;
+    cudaEventRecord(c->ev_pool[c->ev_used].first, c->stream);
+  }
+  f();
+  cudaError_t e = cudaGetLastError();
+  if (c->timing) {
+    cudaEventRecord(c->ev_pool[c->ev_used].second, c->stream);
+    ++c->ev_used;
+  }
+  ++c->launches;
+  if (e != cudaSuccess) return cuda_fail(c, e, kKernelNames[kc]);
+  return DG_OK;
+}
+
+#define DG_TRY(x)                  \
+  do {                             \
+    dg_status _s = (x);            \
+    if (_s != DG_OK) return _s;    \
+  } while (0)
+
+// alpha for this stage (shock capturing with the indicator)
+dg_status stage_alpha(dg_ctx *c, const double *U) {
+  if (!c->d.shock_capturing || c->d.alpha_fixed >= 0.0) return DG_OK;
+  DG_TRY(launch(c, KC_INDICATOR, [&] { c->K->indicator(c->d, U, c->stream); }));
+  DG_TRY(launch(c, KC_SPREAD, [&] { c->K->spread(c->d, c->d.alpha, c->stream); }));
+  return DG_OK;
+}
+
+// one right-hand-side evaluation; mode 0 writes Ut, mode 1 performs LSERK stage `stage`
+dg_status stage(dg_ctx *c, const double *U, double *out, int mode, int st, double dt) {
+  DG_TRY(stage_alpha(c, U));
+  DG_TRY(launch(c, KC_FACE, [&] { c->K->face(c->d, U, c->stream); }));
+  if (c->d.equations == DG_NAVIER_STOKES) DG_TRY(launch(c, KC_LIFT, [&] { c->K->lift(c->d, U, c->stream); }));
+  const double A = mode ? kA[st] : 0.0, B = mode ? kB[st] : 0.0;
+  DG_TRY(launch(c, KC_VOLUME, [&] { c->K->volume(c->d, U, out, c->g, mode, st == 0, dt, A, B, c->stream); }));
+  return DG_OK;
+}
+
+__global__ void k_fill(double *p, int count, double v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) p[i] = v;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dg_status_string(int s) {
+  switch (s) {
+    case DG_OK: return "ok";
+    case DG_ERR_ARG: return "invalid argument";
+    case DG_ERR_MESH: return "inconsistent mesh";
+    case DG_ERR_JACOBIAN: return "non-positive Jacobian";
+    case DG_ERR_CUDA: return "CUDA error";
+    case DG_ERR_NONPHYSICAL: return "non-physical state";
+    case DG_ERR_UNSUPPORTED: return "unsupported";
+    case DG_ERR_OOM: return "out of device memory";
+    default: return "unknown status";
+  }
+}
+
+const char *dg_last_error(const dg_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+dg_status dg_basis(int N, double *xi, double *w, double *D) {
+  if (N < 1 || N > DG_NMAX || !xi || !w || !D) return DG_ERR_ARG;
+  DgTables t;
+  if (dg_build_tables(N, &t) != 0) return DG_ERR_ARG;
+  const int n = N + 1;
+  for (int i = 0; i < n; ++i) { xi[i] = t.xi[i]; w[i] = t.w[i]; }
+  for (int i = 0; i < n * n; ++i) D[i] = t.D[i];
+  return DG_OK;
+}
+
+void dg_free(dg_ctx *c) {
+  if (!c) return;
+  for (void *p : c->allocs) cudaFree(p);
+  for (auto &pr : c->ev_pool) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+  if (c->flag_host) cudaFreeHost(c->flag_host);
+  delete c;
+}
+
+dg_status dg_init(const dg_mesh *mesh, int N, int nodes, const dg_params *prm, void *cuda_stream, dg_ctx **out) {
+  if (!out) return DG_ERR_ARG;
+  *out = nullptr;
+  if (!mesh || !prm || !mesh->xyz || !mesh->face) return DG_ERR_ARG;
+  if (N < 1 || N > DG_NMAX || nodes != DG_NODES_LGL || mesh->n_geo != N) return DG_ERR_ARG;
+  if (mesh->n_elems <= 0 || mesh->n_faces <= 0) return DG_ERR_ARG;
+  if (prm->equations < 0 || prm->equations > 1 || prm->volume_flux < 0 || prm->volume_flux > 3 ||
+      prm->surface_flux < 0 || prm->surface_flux > 2 || prm->precision < 0 || prm->precision > 1)
+    return DG_ERR_ARG;
+  if (!(prm->gamma > 1.0) || !(prm->R > 0.0) || !(prm->mu >= 0.0) || !(prm->Pr > 0.0)) return DG_ERR_ARG;
+  if (prm->precision != DG_FP64) return DG_ERR_UNSUPPORTED;
+  const int nE = mesh->n_elems, nF = mesh->n_faces, n = N + 1, nn = n * n, nnn = nn * n;
+  if ((long long)nF * 2 != (long long)nE * 6) return DG_ERR_MESH;
+
+  // element-face connectivity: every (element, local face) slot used exactly once
+  std::vector<int> ef((size_t)nE * 24, -1);
+  for (int f = 0; f < nF; ++f) {
+    const int *F = mesh->face + 5 * f;
+    const int eL = F[0], fL = F[1], eR = F[2], fR = F[3], o = F[4];
+    if (eL < 0 || eL >= nE || eR < 0 || eR >= nE || fL < 0 || fL > 5 || fR < 0 || fR > 5 || o < 0 || o > 7)
+      return DG_ERR_MESH;
+    int *sL = &ef[((size_t)eL * 6 + fL) * 4], *sR = &ef[((size_t)eR * 6 + fR) * 4];
+    if (sL[0] >= 0 || sR[0] >= 0 || (eL == eR && fL == fR)) return DG_ERR_MESH;
+    // inverse orientation: a transposed map swaps the roles of the two flip bits
+    const int inv = (o & 4) ? (4 | ((o & 1) << 1) | ((o & 2) >> 1)) : o;
+    sL[0] = eR; sL[1] = fR; sL[2] = o; sL[3] = f;
+    sR[0] = eL; sR[1] = fL; sR[2] = inv; sR[3] = f;
+  }
+
+  dg_ctx *c = new dg_ctx();
+  c->N = N;
+  c->params = *prm;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) { dg_status s = cuda_fail(c, e, "cudaGetDevice"); *out = nullptr; delete c; return s; }
+  c->K = kernels_for(N);
+  {
+    std::lock_guard<std::mutex> lk(g_upload_mutex);
+    if ((int)g_uploaded.size() <= c->device) g_uploaded.resize(c->device + 1, 0u);
+    if (!(g_uploaded[c->device] & (1u << N))) {
+      DgTables t;
+      dg_build_tables(N, &t);
+      e = c->K->upload(t);
+      if (e != cudaSuccess) { cuda_fail(c, e, "constant tables"); dg_free(c); return DG_ERR_CUDA; }
+      g_uploaded[c->device] |= (1u << N);
+    }
+  }
+  DgDevice &d = c->d;
+  d.N = N; d.nE = nE; d.nF = nF;
+  d.equations = prm->equations; d.vflux = prm->volume_flux; d.sflux = prm->surface_flux;
+  d.precision = prm->precision; d.shock_capturing = prm->shock_capturing ? 1 : 0;
+  d.gamma = prm->gamma; d.R = prm->R; d.mu = prm->mu;
+  d.kappa = prm->mu * prm->gamma * prm->R / ((prm->gamma - 1.0) * prm->Pr);
+  d.alpha_min = prm->alpha_min; d.alpha_max = prm->alpha_max; d.sharpness = prm->sharpness;
+  d.alpha_fixed = prm->alpha_fixed;
+  c->n_state = (size_t)nE * 5 * nnn;
+
+  double *xyz = nullptr;
+  int *face = nullptr;
+  dg_status s = DG_OK;
+#define DG_ALLOC(p, cnt) if (s == DG_OK) s = dev_alloc(c, &(p), (size_t)(cnt))
+  DG_ALLOC(xyz, (size_t)nE * 3 * nnn);
+  DG_ALLOC(face, (size_t)nF * 5);
+  DG_ALLOC(d.ef, (size_t)nE * 24);
+  DG_ALLOC(d.Ja, (size_t)nE * 9 * nnn);
+  DG_ALLOC(d.J, (size_t)nE * nnn);
+  DG_ALLOC(d.invJ, (size_t)nE * nnn);
+  DG_ALLOC(d.nrm, (size_t)nF * 4 * nn);
+  DG_ALLOC(d.Fsurf, (size_t)nE * 6 * 5 * nn);
+  if (prm->equations == DG_NAVIER_STOKES) {
+    DG_ALLOC(d.Wsurf, (size_t)nE * 6 * 4 * nn);
+    DG_ALLOC(d.Fv, (size_t)nE * 12 * nnn);
+  }
+  DG_ALLOC(d.alpha_raw, (size_t)nE);
+  DG_ALLOC(d.alpha, (size_t)nE);
+  DG_ALLOC(d.red, (size_t)DG_RED_DOUBLES);
+  DG_ALLOC(d.flag, (size_t)1);
+  DG_ALLOC(c->g, c->n_state);
+  DG_ALLOC(c->small, (size_t)16);
+#undef DG_ALLOC
+  if (s != DG_OK) { dg_free(c); return s; }
+  d.xyz = xyz;
+  d.face = face;
+  if ((e = cudaMallocHost(&c->flag_host, sizeof(int))) != cudaSuccess) {
+    cuda_fail(c, e, "cudaMallocHost");
+    dg_free(c);
+    return DG_ERR_OOM;
+  }
+  cudaStream_t st = c->stream;
+  e = cudaMemcpyAsync(xyz, mesh->xyz, sizeof(double) * (size_t)nE * 3 * nnn, cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaMemcpyAsync(face, mesh->face, sizeof(int) * (size_t)nF * 5, cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaMemcpyAsync(d.ef, ef.data(), sizeof(int) * (size_t)nE * 24, cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaMemsetAsync(d.flag, 0, sizeof(int), st);
+  if (!e) e = cudaMemsetAsync(d.alpha, 0, sizeof(double) * nE, st);
+  if (!e) e = cudaMemsetAsync(d.alpha_raw, 0, sizeof(double) * nE, st);
+  if (e) { cuda_fail(c, e, "init copies"); dg_free(c); return DG_ERR_CUDA; }
+  if ((s = launch(c, KC_OTHER, [&] { c->K->metrics(c->d, st); })) != DG_OK) { dg_free(c); return s; }
+  if ((s = launch(c, KC_OTHER, [&] { c->K->face_normals(c->d, st); })) != DG_OK) { dg_free(c); return s; }
+  if (d.shock_capturing && d.alpha_fixed >= 0.0) {
+    if ((s = launch(c, KC_OTHER, [&] { k_fill<<<(nE + 255) / 256, 256, 0, st>>>(d.alpha, nE, d.alpha_fixed); })) !=
+        DG_OK) { dg_free(c); return s; }
+  }
+  e = cudaMemcpyAsync(c->flag_host, d.flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  if (e) { cuda_fail(c, e, "init"); dg_free(c); return DG_ERR_CUDA; }
+  if (*c->flag_host & 2) { dg_free(c); return DG_ERR_JACOBIAN; }
+  d.xyz = nullptr;  // coordinates are not needed after the metrics
+  *out = c;
+  return DG_OK;
+}
+
+dg_status dg_rhs(dg_ctx *c, const double *U, double *Ut, double t) {
+  (void)t;
+  if (!c || !U || !Ut || U == Ut) return fail(c, DG_ERR_ARG, "dg_rhs: null or aliased arrays");
+  return stage(c, U, Ut, 0, 0, 0.0);
+}
+
+dg_status dg_lserk_step(dg_ctx *c, double *U, double dt, double t) {
+  (void)t;
+  if (!c || !U || !std::isfinite(dt)) return fail(c, DG_ERR_ARG, "dg_lserk_step: bad argument");
+  for (int st = 0; st < 5; ++st) DG_TRY(stage(c, U, U, 1, st, dt));
+  return DG_OK;
+}
+
+dg_status dg_lserk_steps(dg_ctx *c, double *U, double dt, double t, int n_steps) {
+  if (!c || !U || n_steps < 0) return fail(c, DG_ERR_ARG, "dg_lserk_steps: bad argument");
+  for (int k = 0; k < n_steps; ++k) DG_TRY(dg_lserk_step(c, U, dt, t + k * dt));
+  return DG_OK;
+}
+
+dg_status dg_lserk_step_host(dg_ctx *c, double *U_host, double dt, double t) {
+  if (!c || !U_host) return fail(c, DG_ERR_ARG, "dg_lserk_step_host: null array");
+  if (!c->Ustage) DG_TRY(dev_alloc(c, &c->Ustage, c->n_state));
+  const size_t bytes = sizeof(double) * c->n_state;
+  cudaError_t e = cudaMemcpyAsync(c->Ustage, U_host, bytes, cudaMemcpyHostToDevice, c->stream);
+  if (e) return cuda_fail(c, e, "H2D");
+  DG_TRY(dg_lserk_step(c, c->Ustage, dt, t));
+  e = cudaMemcpyAsync(U_host, c->Ustage, bytes, cudaMemcpyDeviceToHost, c->stream);
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_fail(c, e, "D2H");
+  return DG_OK;
+}
+
+dg_status dg_indicator(dg_ctx *c, const double *U, double *alpha) {
+  if (!c || !U || !alpha) return fail(c, DG_ERR_ARG, "dg_indicator: null array");
+  DG_TRY(launch(c, KC_INDICATOR, [&] { c->K->indicator(c->d, U, c->stream); }));
+  DG_TRY(launch(c, KC_SPREAD, [&] { c->K->spread(c->d, alpha, c->stream); }));
+  return DG_OK;
+}
+
+dg_status dg_invariants(dg_ctx *c, const double *U, const double *Ut, double out[8]) {
+  if (!c || !U || !Ut || !out) return fail(c, DG_ERR_ARG, "dg_invariants: null array");
+  DG_TRY(launch(c, KC_OTHER, [&] { c->K->invariants(c->d, U, Ut, c->small, c->stream); }));
+  cudaError_t e = cudaMemcpyAsync(out, c->small, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_fail(c, e, "dg_invariants");
+  return DG_OK;
+}
+
+dg_status dg_max_dt(dg_ctx *c, const double *U, double cfl, double *dt) {
+  if (!c || !U || !dt || !(cfl > 0.0)) return fail(c, DG_ERR_ARG, "dg_max_dt: bad argument");
+  DG_TRY(launch(c, KC_OTHER, [&] { c->K->max_dt(c->d, U, c->small + 8, c->stream); }));
+  double v = 0.0;
+  cudaError_t e = cudaMemcpyAsync(&v, c->small + 8, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_fail(c, e, "dg_max_dt");
+  *dt = cfl * v;
+  return DG_OK;
+}
+
+dg_status dg_check(dg_ctx *c) {
+  if (!c) return DG_ERR_ARG;
+  cudaError_t e = cudaMemcpyAsync(c->flag_host, c->d.flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_fail(c, e, "dg_check");
+  const int f = *c->flag_host;
+  e = cudaMemsetAsync(c->d.flag, 0, sizeof(int), c->stream);
+  if (e) return cuda_fail(c, e, "dg_check");
+  if (f & 1) return fail(c, DG_ERR_NONPHYSICAL, "a kernel met rho <= 0, p <= 0 or a non-finite state");
+  return DG_OK;
+}
+
+dg_status dg_get_metrics(dg_ctx *c, double *Ja, double *J) {
+  if (!c || !Ja || !J) return fail(c, DG_ERR_ARG, "dg_get_metrics: null array");
+  const int n = c->N + 1;
+  const size_t nnn = (size_t)n * n * n;
+  cudaError_t e = cudaMemcpyAsync(Ja, c->d.Ja, sizeof(double) * c->d.nE * 9 * nnn, cudaMemcpyDeviceToDevice, c->stream);
+  if (!e) e = cudaMemcpyAsync(J, c->d.J, sizeof(double) * c->d.nE * nnn, cudaMemcpyDeviceToDevice, c->stream);
+  if (e) return cuda_fail(c, e, "dg_get_metrics");
+  return DG_OK;
+}
+
+dg_status dg_timing_enable(dg_ctx *c, int enable) {
+  if (!c) return DG_ERR_ARG;
+  c->timing = enable != 0;
+  return DG_OK;
+}
+
+int dg_timing_get(dg_ctx *c, const char **names, double *ms, long long *launches, int cap) {
+  if (!c) return -1;
+  if (c->ev_used) {
+    cudaStreamSynchronize(c->stream);
+    for (size_t i = 0; i < c->ev_used; ++i) {
+      float t = 0.0f;
+      cudaEventElapsedTime(&t, c->ev_pool[i].first, c->ev_pool[i].second);
+      c->t_ms[c->ev_class[i]] += t;
+      c->t_count[c->ev_class[i]] += 1;
+    }
+    c->ev_used = 0;
+  }
+  int k = 0;
+  for (; k < KC_COUNT && k < cap; ++k) {
+    if (names) names[k] = kKernelNames[k];
+    if (ms) ms[k] = c->t_ms[k];
+    if (launches) launches[k] = c->t_count[k];
+  }
+  for (int j = 0; j < KC_COUNT; ++j) { c->t_ms[j] = 0.0; c->t_count[j] = 0; }
+  return k;
+}
+
+long long dg_launch_count(const dg_ctx *c) { return c ? c->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// dg_internal.h -- shared between the C-ABI layer (dg_api.cu) and the per-degree kernel
+// translation units (dg_kernels_nN.cu). Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#define DG_NMAX 7           // highest polynomial degree with compiled kernels
+#define DG_NVAR 5
+
+// Basis tables for one N, built on the host (dg_basis.cpp) and copied into each kernel
+// translation unit's constant memory.
+struct DgTables {
+  int N;
+  double xi[DG_NMAX + 1], w[DG_NMAX + 1], invw[DG_NMAX + 1];
+  double D[(DG_NMAX + 1) * (DG_NMAX + 1)];     // D[i*n+m] = l_m'(xi_i)
+  double Vinv[(DG_NMAX + 1) * (DG_NMAX + 1)];  // inverse orthonormal-Legendre Vandermonde
+  double xh[DG_NMAX + 2];                      // FV subcell interfaces -1 + cumulative weights
+};
+
+// Plain view of a context's device state, passed by value to every kernel.
+struct DgDevice {
+  int N, nE, nF;
+  int equations, vflux, sflux, precision, shock_capturing;
+  double gamma, R, mu, kappa, alpha_min, alpha_max, sharpness, alpha_fixed;
+  // geometry (built at init)
+  const double *xyz;   // [nE][3][n^3]  (init only)
+  double *Ja;          // [nE][3 d][3 c][n^3]
+  double *J;           // [nE][n^3]
+  double *invJ;        // [nE][n^3]
+  float *Jaf;          // FP32 copy of Ja for the FP32-bulk path (or null)
+  double *nrm;         // [nF][4][n^2]: unit normal (x,y,z) outward from L, area factor s
+  const int *face;     // [nF][5]
+  int *ef;             // [nE][6][4]: neighbour element, neighbour local face, orientation own->nb, face id
+  // per-stage work buffers
+  double *Fsurf;       // [nE][6][5][n^2] outward advective surface flux, own face-point order
+  double *Wsurf;       // [nE][6][4][n^2] BR1 lifting jump (w* - w_own), own order
+  double *Fv;          // [nE][3 d][4][n^3] contravariant viscous flux (momentum x,y,z, energy)
+  float *Fsurf_f, *Wsurf_f, *Fv_f;  // FP32-bulk versions
+  double *alpha_raw;   // [nE]
+  double *alpha;       // [nE]
+  double *red;         // reduction partials
+  int *flag;           // bit 0: non-physical state met; bit 1: J <= 0 at init
+};
+
+// Kernel entry points compiled for one polynomial degree (one translation unit per N).
+struct DgKernelTable {
+  int N;
+  cudaError_t (*upload)(const DgTables &t);
+  void (*metrics)(const DgDevice &d, cudaStream_t s);
+  void (*face_normals)(const DgDevice &d, cudaStream_t s);
+  void (*face)(const DgDevice &d, const double *U, cudaStream_t s);
+  void (*lift)(const DgDevice &d, const double *U, cudaStream_t s);
+  // mode 0: out = Ut. mode 1: LSERK stage in place on out (== U): g = first ? dt*Ut : A g + dt*Ut;
+  // U += B g.
+  void (*volume)(const DgDevice &d, const double *U, double *out, double *g, int mode, int first, double dt,
+                 double A, double B, cudaStream_t s);
+  void (*indicator)(const DgDevice &d, const double *U, cudaStream_t s);
+  void (*spread)(const DgDevice &d, double *alpha_out, cudaStream_t s);
+  void (*invariants)(const DgDevice &d, const double *U, const double *Ut, double *out8_dev, cudaStream_t s);
+  void (*max_dt)(const DgDevice &d, const double *U, double *out_dev, cudaStream_t s);
+};
+
+extern const DgKernelTable dg_kernels_n1, dg_kernels_n2, dg_kernels_n3, dg_kernels_n4, dg_kernels_n5,
+    dg_kernels_n6, dg_kernels_n7;
+
+// Host-side basis construction (dg_basis.cpp): returns 0 on success.
+int dg_build_tables(int N, DgTables *t);
+
+// Reduction buffer size (doubles) the kernels may use in DgDevice::red.
+#define DG_RED_BLOCKS 1024
+#define DG_RED_DOUBLES (DG_RED_BLOCKS * 8 + 8)

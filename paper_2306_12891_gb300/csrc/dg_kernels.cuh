@@ -1,0 +1,1006 @@
+// dg_kernels.cuh -- sm_103a kernels of the split-form DGSEM right-hand side for ONE polynomial
+// degree. Included by dg_kernels_nN.cu with DG_N defined; everything lives in an anonymous
+// namespace so each translation unit has its own constant-memory tables.
+//
+// Per RK stage (Sec. 2; Sec. 4.1):
+//   [indicator -> spread]   modified Persson indicator on rho*p (Sec. 4.1, Eq. (4)), alpha per element
+//   face                    Riemann flux s F*(U_L, U_R, n) once per face point (Roe / LLF / EC),
+//                           BR1 face jumps w* - w for the lifting (Navier-Stokes)
+//   [lift]                  BR1 gradients of (u, v, w, T) and the contravariant viscous flux
+//   volume                  split-form flux differencing along the three line families, viscous
+//                           divergence, surface terms, FV subcell operator + blend (Sec. 4.1,
+//                           Eq. (3)), Jacobian, and the fused LSERK(5,4) stage update
+//
+// Algebra used by the volume kernel (exact identities of the LGL/SBP operator): with
+// D_00 = -1/(2 w_0), D_NN = 1/(2 w_N) and zero interior diagonal, the diagonal volume term
+// 2 D_ii F(U_i) cancels the -F(U_i)/w_b part of the strong-form surface term, so the kernel
+// sums off-diagonal pairs only and adds (1/w_b) F*_out at boundary nodes; for the viscous
+// (BR1 central) flux the same cancellation leaves -(1/(2 w_b)) phi_nb, the neighbour's outward
+// normal viscous flux. Pair symmetry F#(U_i,U_m) = F#(U_m,U_i) halves the two-point fluxes.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "dg_internal.h"
+
+#ifndef DG_N
+#error "define DG_N before including dg_kernels.cuh"
+#endif
+
+namespace {
+
+constexpr int N = DG_N;
+constexpr int n = N + 1;
+constexpr int nn = n * n;
+constexpr int nnn = nn * n;
+constexpr int PS = n * (n + 1) * n;  // padded stride of one staged node quantity
+constexpr int NP = 7;                // staged quantities per node
+
+__constant__ double c_D[nn];      // D_im
+__constant__ double c_D2[nn];     // 2 D_im, zero diagonal
+__constant__ double c_Dq[nn];     // D_im / 4 (scaled mass flux), zero diagonal
+__constant__ double c_De[nn];     // D_im / 8 (scaled momentum / energy flux), zero diagonal
+__constant__ double c_w[n], c_invw[n], c_xi[n], c_xh[n + 1];
+__constant__ double c_Vinv[nn];
+
+enum { VF_KG = 0, VF_PIR = 1, VF_EC = 2, VF_CEN = 3 };
+enum { SF_LLF = 0, SF_ROE = 1, SF_EC = 2 };
+
+__host__ __device__ constexpr int round32(int x) { return (x + 31) / 32 * 32; }
+// elements per CTA of the volume kernel: make 3 n^2 line threads x EPB fill whole warps
+__host__ __device__ constexpr int vol_epb() {
+  return N == 1 ? 8 : N == 2 ? 4 : N == 3 ? 2 : N == 4 ? 3 : N == 5 ? 2 : 1;
+}
+constexpr int VOL_EPB = vol_epb();
+constexpr int VOL_THREADS = round32(3 * nn * VOL_EPB);
+// lifting kernel: whole elements per CTA, a thread per node (looped above 256 threads)
+__host__ __device__ constexpr int lift_epb() { return nnn >= 128 ? 1 : (128 + nnn - 1) / nnn; }
+constexpr int LIFT_EPB = lift_epb();
+constexpr int LIFT_THREADS = round32(LIFT_EPB * nnn) > 256 ? 256 : round32(LIFT_EPB * nnn);
+
+__device__ __forceinline__ int pidx(int node) {  // padded staging index of node (i,j,k)
+  const int i = node % n, j = (node / n) % n, k = node / nn;
+  return i + (n + 1) * (j + n * k);
+}
+
+__device__ __forceinline__ int face_node(int f, int p, int q) {
+  const int b = (f & 1) ? N : 0;
+  switch (f >> 1) {
+    case 0: return b + n * (p + n * q);
+    case 1: return p + n * (b + n * q);
+    default: return p + n * (q + n * b);
+  }
+}
+
+__device__ __forceinline__ void orient_map(int o, int p, int q, int &p2, int &q2) {
+  int a = p, b = q;
+  if (o & 4) { a = q; b = p; }
+  if (o & 1) a = N - a;
+  if (o & 2) b = N - b;
+  p2 = a;
+  q2 = b;
+}
+
+__device__ __forceinline__ void flag_set(int *flag, int bit) { atomicOr(flag, bit); }
+
+// ---------------------------------------------------------------------------------------------
+// pointwise physics
+// ---------------------------------------------------------------------------------------------
+
+// Euler flux through the (unit or metric) vector a
+__device__ __forceinline__ void euler_flux_n(const double U[5], double gam, const double a[3], double F[5],
+                                             double &un, double &p) {
+  const double ir = 1.0 / U[0];
+  const double u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
+  p = (gam - 1.0) * (U[4] - 0.5 * (U[1] * u + U[2] * v + U[3] * w));
+  un = u * a[0] + v * a[1] + w * a[2];
+  F[0] = U[0] * un;
+  F[1] = U[1] * un + p * a[0];
+  F[2] = U[2] * un + p * a[1];
+  F[3] = U[3] * un + p * a[2];
+  F[4] = (U[4] + p) * un;
+}
+
+__device__ __forceinline__ double logmean(double a, double b) {
+  // (a - b) / ln(a/b); Ismail-Roe series where the ratio is close to 1
+  const double z = a / b;
+  const double f = (z - 1.0) / (z + 1.0);
+  const double u = f * f;
+  if (u < 1e-4) return (a + b) / (2.0 * (1.0 + u * (1.0 / 3.0 + u * (0.2 + u * (1.0 / 7.0)))));
+  return (a - b) / log(z);
+}
+
+// Chandrashekar's entropy-conservative two-point flux through the vector a
+__device__ __forceinline__ void ec_flux(double rL, double uL, double vL, double wL, double pL, double rR, double uR,
+                                        double vR, double wR, double pR, const double a[3], double gam, double F[5]) {
+  const double bL = 0.5 * rL / pL, bR = 0.5 * rR / pR;
+  const double rln = logmean(rL, rR), bln = logmean(bL, bR);
+  const double um = 0.5 * (uL + uR), vm = 0.5 * (vL + vR), wm = 0.5 * (wL + wR);
+  const double phat = 0.5 * (rL + rR) / (bL + bR);
+  const double q2 = 0.5 * (uL * uL + vL * vL + wL * wL + uR * uR + vR * vR + wR * wR);
+  const double V = um * a[0] + vm * a[1] + wm * a[2];
+  F[0] = rln * V;
+  F[1] = F[0] * um + phat * a[0];
+  F[2] = F[0] * vm + phat * a[1];
+  F[3] = F[0] * wm + phat * a[2];
+  F[4] = F[0] * (0.5 / ((gam - 1.0) * bln) - 0.5 * q2) + um * F[1] + vm * F[2] + wm * F[3];
+}
+
+// Riemann flux F*(UL, UR, nv) for a unit normal nv
+__device__ __forceinline__ void riemann(int sf, const double UL[5], const double UR[5], const double nv[3], double gam,
+                                        double F[5]) {
+  if (sf == SF_EC) {
+    const double irL = 1.0 / UL[0], irR = 1.0 / UR[0];
+    const double uL = UL[1] * irL, vL = UL[2] * irL, wL = UL[3] * irL;
+    const double uR = UR[1] * irR, vR = UR[2] * irR, wR = UR[3] * irR;
+    const double pL = (gam - 1.0) * (UL[4] - 0.5 * (UL[1] * uL + UL[2] * vL + UL[3] * wL));
+    const double pR = (gam - 1.0) * (UR[4] - 0.5 * (UR[1] * uR + UR[2] * vR + UR[3] * wR));
+    ec_flux(UL[0], uL, vL, wL, pL, UR[0], uR, vR, wR, pR, nv, gam, F);
+    return;
+  }
+  double FL[5], FR[5], unL, unR, pL, pR;
+  euler_flux_n(UL, gam, nv, FL, unL, pL);
+  euler_flux_n(UR, gam, nv, FR, unR, pR);
+  if (sf == SF_LLF) {
+    const double cL = sqrt(gam * pL / UL[0]), cR = sqrt(gam * pR / UR[0]);
+    const double lam = fmax(fabs(unL) + cL, fabs(unR) + cR);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) F[v] = 0.5 * (FL[v] + FR[v] - lam * (UR[v] - UL[v]));
+    return;
+  }
+  // Roe: sqrt(rho)-weighted average state, three wave families, no entropy fix
+  const double sL = sqrt(UL[0]), sR = sqrt(UR[0]);
+  const double iw = 1.0 / (sL + sR);
+  const double irL = 1.0 / UL[0], irR = 1.0 / UR[0];
+  const double uL = UL[1] * irL, vL = UL[2] * irL, wL = UL[3] * irL;
+  const double uR = UR[1] * irR, vR = UR[2] * irR, wR = UR[3] * irR;
+  const double ut = (sL * uL + sR * uR) * iw, vt = (sL * vL + sR * vR) * iw, wt = (sL * wL + sR * wR) * iw;
+  const double Ht = (sL * (UL[4] + pL) * irL + sR * (UR[4] + pR) * irR) * iw;
+  const double q2 = ut * ut + vt * vt + wt * wt;
+  const double c2 = (gam - 1.0) * (Ht - 0.5 * q2);
+  const double ct = sqrt(c2), ic2 = 1.0 / c2;
+  const double rt = sL * sR;
+  const double unt = ut * nv[0] + vt * nv[1] + wt * nv[2];
+  const double dr = UR[0] - UL[0], dp = pR - pL;
+  const double du = uR - uL, dv = vR - vL, dw = wR - wL;
+  const double dun = du * nv[0] + dv * nv[1] + dw * nv[2];
+  const double a1 = 0.5 * (dp - rt * ct * dun) * ic2;
+  const double a5 = 0.5 * (dp + rt * ct * dun) * ic2;
+  const double a2 = dr - dp * ic2;
+  const double dut = du - dun * nv[0], dvt = dv - dun * nv[1], dwt = dw - dun * nv[2];
+  const double l1a1 = fabs(unt - ct) * a1, l5a5 = fabs(unt + ct) * a5, l2 = fabs(unt);
+  const double l2a2 = l2 * a2, l2r = l2 * rt;
+  double D[5];
+  D[0] = l1a1 + l5a5 + l2a2;
+  D[1] = l1a1 * (ut - ct * nv[0]) + l5a5 * (ut + ct * nv[0]) + l2a2 * ut + l2r * dut;
+  D[2] = l1a1 * (vt - ct * nv[1]) + l5a5 * (vt + ct * nv[1]) + l2a2 * vt + l2r * dvt;
+  D[3] = l1a1 * (wt - ct * nv[2]) + l5a5 * (wt + ct * nv[2]) + l2a2 * wt + l2r * dwt;
+  D[4] = l1a1 * (Ht - unt * ct) + l5a5 * (Ht + unt * ct) + l2a2 * 0.5 * q2 + l2r * (ut * dut + vt * dvt + wt * dwt);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) F[v] = 0.5 * (FL[v] + FR[v] - D[v]);
+}
+
+// ---------------------------------------------------------------------------------------------
+// init: curl-form metrics, Jacobian, face normals
+// ---------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ double dsweep(const double *f, int node, int d) {
+  const int i = node % n, j = (node / n) % n, k = node / nn;
+  const int id = d == 0 ? i : d == 1 ? j : k;
+  const int st = d == 0 ? 1 : d == 1 ? n : nn;
+  const int base = node - id * st;
+  double s = 0.0;
+#pragma unroll
+  for (int m = 0; m < n; ++m) s += c_D[id * n + m] * f[base + m * st];
+  return s;
+}
+
+// One CTA per element. Ja^d_c = D_k(X_l D_j X_m) - D_j(X_l D_k X_m), (d,j,k), (c,m,l) cyclic;
+// J = det(D-derivatives of X). X is taken relative to the element's first node: the metric
+// terms are translation invariant, and absolute coordinates (|x| >> h) would make the
+// products X_l D_j X_m cancel to O(|x|/h) of rounding.
+__global__ void __launch_bounds__(256) k_metrics(const DgDevice d) {
+  extern __shared__ double sm[];
+  double *X = sm;              // [3][nnn]
+  double *dX = X + 3 * nnn;    // [c][dd][nnn]
+  double *T1 = dX + 9 * nnn;   // [nnn]
+  double *T2 = T1 + nnn;       // [nnn]
+  const int e = blockIdx.x;
+  const double *xe = d.xyz + (size_t)e * 3 * nnn;
+  for (int t = threadIdx.x; t < 3 * nnn; t += blockDim.x) X[t] = xe[t] - xe[(t / nnn) * nnn];
+  __syncthreads();
+  for (int t = threadIdx.x; t < 9 * nnn; t += blockDim.x) {
+    const int node = t % nnn, cd = t / nnn, c = cd / 3, dd = cd % 3;
+    dX[cd * nnn + node] = dsweep(X + c * nnn, node, dd);
+  }
+  __syncthreads();
+  for (int dir = 0; dir < 3; ++dir) {
+    const int j = (dir + 1) % 3, k = (dir + 2) % 3;
+    for (int c = 0; c < 3; ++c) {
+      const int m = (c + 1) % 3, l = (c + 2) % 3;
+      for (int node = threadIdx.x; node < nnn; node += blockDim.x) {
+        T1[node] = X[l * nnn + node] * dX[(m * 3 + j) * nnn + node];
+        T2[node] = X[l * nnn + node] * dX[(m * 3 + k) * nnn + node];
+      }
+      __syncthreads();
+      for (int node = threadIdx.x; node < nnn; node += blockDim.x)
+        d.Ja[(((size_t)e * 3 + dir) * 3 + c) * nnn + node] = dsweep(T1, node, k) - dsweep(T2, node, j);
+      __syncthreads();
+    }
+  }
+  for (int node = threadIdx.x; node < nnn; node += blockDim.x) {
+    double a[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int dd = 0; dd < 3; ++dd) a[c][dd] = dX[(c * 3 + dd) * nnn + node];
+    const double J = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) - a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
+                     a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+    d.J[(size_t)e * nnn + node] = J;
+    d.invJ[(size_t)e * nnn + node] = 1.0 / J;
+    if (!(J > 0.0) || !isfinite(J)) flag_set(d.flag, 2);
+  }
+}
+
+// One thread per face point: unit normal and area factor from the L element's metric.
+__global__ void __launch_bounds__(256) k_face_normals(const DgDevice d) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)d.nF * nn) return;
+  const int f = (int)(t / nn), pq = (int)(t % nn), p = pq % n, q = pq / n;
+  const int eL = d.face[5 * f + 0], fL = d.face[5 * f + 1];
+  const int dL = fL >> 1;
+  const double sg = (fL & 1) ? 1.0 : -1.0;
+  const int node = face_node(fL, p, q);
+  double a[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) a[c] = sg * d.Ja[(((size_t)eL * 3 + dL) * 3 + c) * nnn + node];
+  const double s = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+  const double is = 1.0 / s;
+  double *o = d.nrm + (size_t)f * 4 * nn + pq;
+  o[0] = a[0] * is;
+  o[nn] = a[1] * is;
+  o[2 * nn] = a[2] * is;
+  o[3 * nn] = s;
+}
+
+// ---------------------------------------------------------------------------------------------
+// face kernel: Riemann flux once per face point, stored outward for both sides
+// ---------------------------------------------------------------------------------------------
+template <int SF>
+__global__ void __launch_bounds__(256) k_face(const DgDevice d, const double *__restrict__ U) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)d.nF * nn) return;
+  const int f = (int)(t / nn), pq = (int)(t % nn), p = pq % n, q = pq / n;
+  const int *F5 = d.face + 5 * f;
+  const int eL = F5[0], fL = F5[1], eR = F5[2], fR = F5[3], o = F5[4];
+  int p2, q2;
+  orient_map(o, p, q, p2, q2);
+  const int nodeL = face_node(fL, p, q), nodeR = face_node(fR, p2, q2);
+  const int pqR = p2 + n * q2;
+  double UL[5], UR[5], nv[3];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    UL[v] = U[((size_t)eL * 5 + v) * nnn + nodeL];
+    UR[v] = U[((size_t)eR * 5 + v) * nnn + nodeR];
+  }
+  const double *nr = d.nrm + (size_t)f * 4 * nn + pq;
+  nv[0] = nr[0];
+  nv[1] = nr[nn];
+  nv[2] = nr[2 * nn];
+  const double s = nr[3 * nn];
+  double Fs[5];
+  riemann(SF, UL, UR, nv, d.gamma, Fs);
+  double *oL = d.Fsurf + ((size_t)eL * 6 + fL) * 5 * nn;
+  double *oR = d.Fsurf + ((size_t)eR * 6 + fR) * 5 * nn;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    oL[v * nn + pq] = s * Fs[v];
+    oR[v * nn + pqR] = -s * Fs[v];
+  }
+  if (d.equations == 1) {
+    const double irL = 1.0 / UL[0], irR = 1.0 / UR[0];
+    const double wL[3] = {UL[1] * irL, UL[2] * irL, UL[3] * irL};
+    const double wR[3] = {UR[1] * irR, UR[2] * irR, UR[3] * irR};
+    const double pL = (d.gamma - 1.0) * (UL[4] - 0.5 * (UL[1] * wL[0] + UL[2] * wL[1] + UL[3] * wL[2]));
+    const double pR = (d.gamma - 1.0) * (UR[4] - 0.5 * (UR[1] * wR[0] + UR[2] * wR[1] + UR[3] * wR[2]));
+    const double iR = 1.0 / d.R;
+    const double jump[4] = {0.5 * (wR[0] - wL[0]), 0.5 * (wR[1] - wL[1]), 0.5 * (wR[2] - wL[2]),
+                            0.5 * (pR * irR - pL * irL) * iR};
+    double *jL = d.Wsurf + ((size_t)eL * 6 + fL) * 4 * nn;
+    double *jR = d.Wsurf + ((size_t)eR * 6 + fR) * 4 * nn;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      jL[c * nn + pq] = jump[c];
+      jR[c * nn + pqR] = -jump[c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// BR1 lifting + viscous flux: grad w = (1/J)[sum_d Ja^d D_d w + sum_faces (1/w_b) s n_out (w* - w)],
+// then Fv^d = sum_c Ja^d_c Fv_c(U, grad w) stored per node (4 components: momentum, energy).
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(LIFT_THREADS) k_lift(const DgDevice d, const double *__restrict__ U) {
+  __shared__ double W[LIFT_EPB][4][nnn];
+  const int e0 = blockIdx.x * LIFT_EPB;
+  const double gm1 = d.gamma - 1.0, iR = 1.0 / d.R;
+  for (int t = threadIdx.x; t < LIFT_EPB * nnn; t += blockDim.x) {
+    const int le = t / nnn, node = t % nnn, e = e0 + le;
+    if (e >= d.nE) continue;
+    const double *Ue = U + (size_t)e * 5 * nnn + node;
+    const double r = Ue[0], ir = 1.0 / r;
+    const double u = Ue[nnn] * ir, v = Ue[2 * nnn] * ir, w = Ue[3 * nnn] * ir;
+    const double p = gm1 * (Ue[4 * nnn] - 0.5 * r * (u * u + v * v + w * w));
+    W[le][0][node] = u;
+    W[le][1][node] = v;
+    W[le][2][node] = w;
+    W[le][3][node] = p * ir * iR;
+  }
+  __syncthreads();
+  const double mu = d.mu, kappa = d.kappa;
+  for (int t = threadIdx.x; t < LIFT_EPB * nnn; t += blockDim.x) {
+    const int le = t / nnn, node = t % nnn, e = e0 + le;
+    if (e >= d.nE) continue;
+    const int ijk[3] = {node % n, (node / n) % n, node / nn};
+    double Ja[3][3];
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Ja[dd][c] = d.Ja[(((size_t)e * 3 + dd) * 3 + c) * nnn + node];
+    double g[4][3];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) g[q][0] = g[q][1] = g[q][2] = 0.0;
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) {
+      const int id = ijk[dd];
+      const int st = dd == 0 ? 1 : dd == 1 ? n : nn;
+      const int base = node - id * st;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        double s = 0.0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) s += c_D[id * n + m] * W[le][q][base + m * st];
+        g[q][0] += Ja[dd][0] * s;
+        g[q][1] += Ja[dd][1] * s;
+        g[q][2] += Ja[dd][2] * s;
+      }
+      // surface terms on the faces of direction dd through this node
+      if (id == 0 || id == N) {
+        const int f = 2 * dd + (id == N ? 1 : 0);
+        const double sc = (id == N ? 1.0 : -1.0) * c_invw[id];
+        const int pp = dd == 0 ? ijk[1] : ijk[0];
+        const int qq = dd == 2 ? ijk[1] : ijk[2];
+        const double *js = d.Wsurf + ((size_t)e * 6 + f) * 4 * nn + pp + n * qq;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const double jq = sc * js[q * nn];
+          g[q][0] += Ja[dd][0] * jq;
+          g[q][1] += Ja[dd][1] * jq;
+          g[q][2] += Ja[dd][2] * jq;
+        }
+      }
+    }
+    const double iJ = d.invJ[(size_t)e * nnn + node];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { g[q][0] *= iJ; g[q][1] *= iJ; g[q][2] *= iJ; }
+    // Navier-Stokes-Fourier flux in Cartesian direction c: (tau_xc, tau_yc, tau_zc, u.tau_c + kappa dT/dx_c)
+    const double u = W[le][0][node], v = W[le][1][node], w = W[le][2][node];
+    const double div = g[0][0] + g[1][1] + g[2][2];
+    const double t23 = (2.0 / 3.0) * mu * div;
+    const double txx = 2.0 * mu * g[0][0] - t23, tyy = 2.0 * mu * g[1][1] - t23, tzz = 2.0 * mu * g[2][2] - t23;
+    const double txy = mu * (g[0][1] + g[1][0]), txz = mu * (g[0][2] + g[2][0]), tyz = mu * (g[1][2] + g[2][1]);
+    double Fc[3][4];
+    Fc[0][0] = txx; Fc[0][1] = txy; Fc[0][2] = txz; Fc[0][3] = u * txx + v * txy + w * txz + kappa * g[3][0];
+    Fc[1][0] = txy; Fc[1][1] = tyy; Fc[1][2] = tyz; Fc[1][3] = u * txy + v * tyy + w * tyz + kappa * g[3][1];
+    Fc[2][0] = txz; Fc[2][1] = tyz; Fc[2][2] = tzz; Fc[2][3] = u * txz + v * tyz + w * tzz + kappa * g[3][2];
+    double *out = d.Fv + (size_t)e * 12 * nnn + node;
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        out[(dd * 4 + q) * nnn] = Ja[dd][0] * Fc[0][q] + Ja[dd][1] * Fc[1][q] + Ja[dd][2] * Fc[2][q];
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// volume kernel
+// ---------------------------------------------------------------------------------------------
+
+// Flux differencing along one line of n nodes: acc_i = sum_{m != i} 2 D_im F#(U_i, U_m) with
+// the metric average {Ja}. For Kennedy-Gruber and Pirozzoli the flux is formed from plain sums
+// S = x_i + x_m and the 1/2 factors are folded into the coefficients (D/4 for mass, D/8 otherwise).
+// Node i's sums stay in registers while m runs over i+1..N; node m's share of each pair goes
+// straight to the line's accumulator in shared memory (the line belongs to this thread alone).
+// Ac points at the direction's accumulator [5][PS] of this element, indexed like P.
+template <int VF>
+__device__ __forceinline__ void line_fluxdiff(const double *__restrict__ P, int pb, int ps,
+                                              const double *__restrict__ Jd, int gb, int gs, double gam,
+                                              double *__restrict__ Ac) {
+#pragma unroll 1
+  for (int i = 0; i < n; ++i) {
+    const int ai = pb + i * ps, gi = gb + i * gs;
+    const double ri = P[ai], ui = P[PS + ai], vi = P[2 * PS + ai], wi = P[3 * PS + ai];
+    const double p4i = P[4 * PS + ai], xi_ = P[5 * PS + ai], yi = P[6 * PS + ai];
+    const double jxi = __ldg(Jd + gi), jyi = __ldg(Jd + nnn + gi), jzi = __ldg(Jd + 2 * nnn + gi);
+    double ac[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) ac[v] = (i == 0) ? 0.0 : Ac[v * PS + ai];
+#pragma unroll
+    for (int m = i + 1; m < n; ++m) {
+      const int am = pb + m * ps, gm = gb + m * gs;
+      const double rm = P[am], um = P[PS + am], vm = P[2 * PS + am], wm = P[3 * PS + am];
+      const double p4m = P[4 * PS + am], xm = P[5 * PS + am], ym = P[6 * PS + am];
+      const double jxm = __ldg(Jd + gm), jym = __ldg(Jd + nnn + gm), jzm = __ldg(Jd + 2 * nnn + gm);
+      double F[5], ci[5], cm[5];
+      if (VF == VF_PIR || VF == VF_KG) {
+        const double Sjx = jxi + jxm, Sjy = jyi + jym, Sjz = jzi + jzm;
+        const double Su = ui + um, Sv = vi + vm, Sw = wi + wm;
+        const double Vp = Su * Sjx + Sv * Sjy + Sw * Sjz;  // 4 {u}.{Ja}
+        F[0] = (ri + rm) * Vp;                             // 8 F_rho
+        const double Sp = p4i + p4m;                       // 4 (p_i + p_m)
+        F[1] = F[0] * Su + Sp * Sjx;                       // 16 F_rho u
+        F[2] = F[0] * Sv + Sp * Sjy;
+        F[3] = F[0] * Sw + Sp * Sjz;
+        if (VF == VF_PIR) F[4] = F[0] * (xi_ + xm);               // 16 {rho}V{h}
+        else F[4] = F[0] * (xi_ + xm) + (yi + ym) * Vp;           // 16 ({rho}V{e} + {p}V)
+        ci[0] = c_Dq[i * n + m]; cm[0] = c_Dq[m * n + i];
+#pragma unroll
+        for (int v = 1; v < 5; ++v) { ci[v] = c_De[i * n + m]; cm[v] = c_De[m * n + i]; }
+      } else {
+        const double a[3] = {0.5 * (jxi + jxm), 0.5 * (jyi + jym), 0.5 * (jzi + jzm)};
+        if (VF == VF_EC) {
+          ec_flux(ri, ui, vi, wi, 0.25 * p4i, rm, um, vm, wm, 0.25 * p4m, a, gam, F);
+        } else {  // central: mean of the two Euler fluxes through {Ja}; slot 5 = E + p
+          const double Vi = ui * a[0] + vi * a[1] + wi * a[2], Vm = um * a[0] + vm * a[1] + wm * a[2];
+          const double pm2 = 0.125 * (p4i + p4m);
+          F[0] = 0.5 * (ri * Vi + rm * Vm);
+          F[1] = 0.5 * (ri * ui * Vi + rm * um * Vm) + pm2 * a[0];
+          F[2] = 0.5 * (ri * vi * Vi + rm * vm * Vm) + pm2 * a[1];
+          F[3] = 0.5 * (ri * wi * Vi + rm * wm * Vm) + pm2 * a[2];
+          F[4] = 0.5 * (xi_ * Vi + xm * Vm);
+        }
+#pragma unroll
+        for (int v = 0; v < 5; ++v) { ci[v] = c_D2[i * n + m]; cm[v] = c_D2[m * n + i]; }
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        ac[v] += ci[v] * F[v];
+        if (i == 0) Ac[v * PS + am] = cm[v] * F[v];
+        else Ac[v * PS + am] += cm[v] * F[v];
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Ac[v * PS + ai] = ac[v];
+  }
+}
+
+// primitive state (rho, u, v, w, p) of staged node a
+__device__ __forceinline__ void staged_prim(const double *__restrict__ P, int a, double q[5]) {
+  q[0] = P[a]; q[1] = P[PS + a]; q[2] = P[2 * PS + a]; q[3] = P[3 * PS + a]; q[4] = 0.25 * P[4 * PS + a];
+}
+
+// reconstructed left/right interface states of subcell i (minmod slopes in primitive variables;
+// first order in the outer subcells and wherever the reconstruction loses positivity)
+__device__ __forceinline__ void subcell_states(const double *__restrict__ P, int pb, int ps, int i, double qL[5],
+                                               double qR[5]) {
+  double q[5];
+  staged_prim(P, pb + i * ps, q);
+  double sg[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (i > 0 && i < N) {
+    double qb[5], qf[5];
+    staged_prim(P, pb + (i - 1) * ps, qb);
+    staged_prim(P, pb + (i + 1) * ps, qf);
+    const double hb = 1.0 / (c_xi[i] - c_xi[i - 1]), hf = 1.0 / (c_xi[i + 1] - c_xi[i]);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const double sb = (q[v] - qb[v]) * hb, sf_ = (qf[v] - q[v]) * hf;
+      sg[v] = (sb * sf_ <= 0.0) ? 0.0 : (fabs(sb) < fabs(sf_) ? sb : sf_);
+    }
+  }
+  const double dl = c_xh[i] - c_xi[i], dr = c_xh[i + 1] - c_xi[i];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) { qL[v] = q[v] + sg[v] * dl; qR[v] = q[v] + sg[v] * dr; }
+  if (qL[0] <= 0.0 || qL[4] <= 0.0 || qR[0] <= 0.0 || qR[4] <= 0.0) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) { qL[v] = q[v]; qR[v] = q[v]; }
+  }
+}
+
+__device__ __forceinline__ void cons_of(const double q[5], double gm1, double U[5]) {
+  U[0] = q[0]; U[1] = q[0] * q[1]; U[2] = q[0] * q[2]; U[3] = q[0] * q[3];
+  U[4] = q[4] / gm1 + 0.5 * q[0] * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+}
+
+// FV subcell operator along one line (Sec. 4.1): Riemann fluxes at the N interior subcell
+// interfaces with telescoped interface metrics a_{i+1/2} = a_{i-1/2} + w_i (D Ja)_i, the DG surface
+// fluxes at the element faces, and Ac_i = (f_{i+1/2} - f_{i-1/2}) / w_i written to shared memory.
+__device__ __forceinline__ void line_fv(const double *__restrict__ P, int pb, int ps, const double *__restrict__ Jd,
+                                        int gb, int gs, const double *Fm, const double *Fp, int sf, double gam,
+                                        double *__restrict__ Ac) {
+  const double gm1 = gam - 1.0;
+  double fl[5];  // flux at the left interface of the current subcell, +xi direction
+#pragma unroll
+  for (int v = 0; v < 5; ++v) fl[v] = -Fm[v * nn];
+  double a[3] = {__ldg(Jd + gb), __ldg(Jd + nnn + gb), __ldg(Jd + 2 * nnn + gb)};
+  double qLn[5], qRn[5];
+  subcell_states(P, pb, ps, 0, qLn, qRn);
+#pragma unroll 1
+  for (int i = 0; i < n; ++i) {
+    double fr[5];
+    const double qRi[5] = {qRn[0], qRn[1], qRn[2], qRn[3], qRn[4]};
+    if (i < N) {
+      subcell_states(P, pb, ps, i + 1, qLn, qRn);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double dj = 0.0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) dj += c_D[i * n + m] * __ldg(Jd + c * nnn + gb + m * gs);
+        a[c] += c_w[i] * dj;
+      }
+      const double s = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+      const double is = 1.0 / s;
+      const double nv[3] = {a[0] * is, a[1] * is, a[2] * is};
+      double UL[5], UR[5], Fs[5];
+      cons_of(qRi, gm1, UL);
+      cons_of(qLn, gm1, UR);
+      riemann(sf, UL, UR, nv, gam, Fs);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) fr[v] = s * Fs[v];
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) fr[v] = Fp[v * nn];
+    }
+    const double iw = c_invw[i];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) { Ac[v * PS + pb + i * ps] = (fr[v] - fl[v]) * iw; fl[v] = fr[v]; }
+  }
+}
+
+// line geometry of line `line` of direction `dir`: staging base/stride (padded) and global base/stride
+__device__ __forceinline__ void line_geom(int dir, int line, int &pb, int &ps, int &gb, int &gs, int &a, int &b) {
+  a = line % n;
+  b = line / n;
+  if (dir == 0) { pb = (n + 1) * (a + n * b); ps = 1; gb = n * (a + n * b); gs = 1; }
+  else if (dir == 1) { pb = a + (n + 1) * n * b; ps = n + 1; gb = a + nn * b; gs = n; }
+  else { pb = a + (n + 1) * b; ps = (n + 1) * n; gb = a + n * b; gs = nn; }
+}
+
+template <int VF, bool SC>
+__global__ void __launch_bounds__(VOL_THREADS, 2) k_volume(const DgDevice d, const double *U, double *out,
+                                                        double *__restrict__ g, int mode, int first, double dt,
+                                                        double A, double B) {
+  extern __shared__ double sm[];
+  double *P = sm;                              // [EPB][NP][PS]
+  double *Acc = P + VOL_EPB * NP * PS;         // [EPB][3][5][PS]
+  double *AccT = Acc + VOL_EPB * 15 * PS;      // [EPB][5][nnn] (SC only)
+  const int e0 = blockIdx.x * VOL_EPB;
+  const double gam = d.gamma, gm1 = gam - 1.0;
+  const int vf = VF;
+  // phase A: stage primitive quantities
+  for (int t = threadIdx.x; t < VOL_EPB * nnn; t += blockDim.x) {
+    const int le = t / nnn, node = t % nnn, e = e0 + le;
+    if (e >= d.nE) continue;
+    const double *Ue = U + (size_t)e * 5 * nnn + node;
+    const double r = Ue[0], m1 = Ue[nnn], m2 = Ue[2 * nnn], m3 = Ue[3 * nnn], E = Ue[4 * nnn];
+    const double ir = 1.0 / r;
+    const double u = m1 * ir, v = m2 * ir, w = m3 * ir;
+    const double p = gm1 * (E - 0.5 * (m1 * u + m2 * v + m3 * w));
+    if (!(r > 0.0) || !(p > 0.0) || !isfinite(E)) flag_set(d.flag, 1);
+    double *Pe = P + le * NP * PS + pidx(node);
+    Pe[0] = r; Pe[PS] = u; Pe[2 * PS] = v; Pe[3 * PS] = w; Pe[4 * PS] = 4.0 * p;
+    if (vf == VF_PIR) Pe[5 * PS] = (E + p) * ir;
+    else if (vf == VF_KG) { Pe[5 * PS] = E * ir; Pe[6 * PS] = 2.0 * p; }
+    else if (vf == VF_CEN) Pe[5 * PS] = E + p;
+  }
+  __syncthreads();
+  // phase B: flux differencing, one thread per line, the three line families at once
+  for (int t = threadIdx.x; t < VOL_EPB * 3 * nn; t += blockDim.x) {
+    const int le = t / (3 * nn), r = t % (3 * nn), dir = r / nn, line = r % nn, e = e0 + le;
+    if (e >= d.nE) continue;
+    int pb, ps, gb, gs, a, b;
+    line_geom(dir, line, pb, ps, gb, gs, a, b);
+    line_fluxdiff<VF>(P + le * NP * PS, pb, ps, d.Ja + ((size_t)e * 3 + dir) * 3 * nnn, gb, gs, gam,
+                      Acc + (le * 3 + dir) * 5 * PS);
+  }
+  __syncthreads();
+  if (SC) {
+    // DG total (volume + surface) per node into AccT, then the FV operator into Acc
+    for (int t = threadIdx.x; t < VOL_EPB * nnn; t += blockDim.x) {
+      const int le = t / nnn, node = t % nnn, e = e0 + le;
+      if (e >= d.nE) continue;
+      const int ijk[3] = {node % n, (node / n) % n, node / nn};
+      const int pn = pidx(node);
+      double s[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v)
+        s[v] = Acc[(le * 3 + 0) * 5 * PS + v * PS + pn] + Acc[(le * 3 + 1) * 5 * PS + v * PS + pn] +
+               Acc[(le * 3 + 2) * 5 * PS + v * PS + pn];
+#pragma unroll
+      for (int dd = 0; dd < 3; ++dd) {
+        const int id = ijk[dd];
+        if (id != 0 && id != N) continue;
+        const int f = 2 * dd + (id == N ? 1 : 0);
+        const int pp = dd == 0 ? ijk[1] : ijk[0], qq = dd == 2 ? ijk[1] : ijk[2];
+        const double *fs = d.Fsurf + ((size_t)e * 6 + f) * 5 * nn + pp + n * qq;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) s[v] += c_invw[id] * fs[v * nn];
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) AccT[(le * 5 + v) * nnn + node] = s[v];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < VOL_EPB * 3 * nn; t += blockDim.x) {
+      const int le = t / (3 * nn), r = t % (3 * nn), dir = r / nn, line = r % nn, e = e0 + le;
+      if (e >= d.nE) continue;
+      if (!(d.alpha[e] > 0.0)) continue;
+      int pb, ps, gb, gs, a, b;
+      line_geom(dir, line, pb, ps, gb, gs, a, b);
+      const double *Fm = d.Fsurf + ((size_t)e * 6 + 2 * dir) * 5 * nn + a + n * b;
+      const double *Fp = d.Fsurf + ((size_t)e * 6 + 2 * dir + 1) * 5 * nn + a + n * b;
+      line_fv(P + le * NP * PS, pb, ps, d.Ja + ((size_t)e * 3 + dir) * 3 * nnn, gb, gs, Fm, Fp, d.sflux, gam,
+              Acc + (le * 3 + dir) * 5 * PS);
+    }
+    __syncthreads();
+  }
+  // phase C: per node -- surface terms, viscous divergence, blend, Jacobian, output / LSERK
+  const bool ns = d.equations == 1;
+  for (int t = threadIdx.x; t < VOL_EPB * nnn; t += blockDim.x) {
+    const int le = t / nnn, node = t % nnn, e = e0 + le;
+    if (e >= d.nE) continue;
+    const int ijk[3] = {node % n, (node / n) % n, node / nn};
+    const int pn = pidx(node);
+    double s[5];
+    if (SC) {
+      const double al = d.alpha[e];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) s[v] = AccT[(le * 5 + v) * nnn + node];
+      if (al > 0.0) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          const double fv = Acc[(le * 3 + 0) * 5 * PS + v * PS + pn] + Acc[(le * 3 + 1) * 5 * PS + v * PS + pn] +
+                            Acc[(le * 3 + 2) * 5 * PS + v * PS + pn];
+          s[v] = al * fv + (1.0 - al) * s[v];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v)
+        s[v] = Acc[(le * 3 + 0) * 5 * PS + v * PS + pn] + Acc[(le * 3 + 1) * 5 * PS + v * PS + pn] +
+               Acc[(le * 3 + 2) * 5 * PS + v * PS + pn];
+#pragma unroll
+      for (int dd = 0; dd < 3; ++dd) {
+        const int id = ijk[dd];
+        if (id != 0 && id != N) continue;
+        const int f = 2 * dd + (id == N ? 1 : 0);
+        const int pp = dd == 0 ? ijk[1] : ijk[0], qq = dd == 2 ? ijk[1] : ijk[2];
+        const double *fs = d.Fsurf + ((size_t)e * 6 + f) * 5 * nn + pp + n * qq;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) s[v] += c_invw[id] * fs[v * nn];
+      }
+    }
+    if (ns) {
+      const double *Fve = d.Fv + (size_t)e * 12 * nnn;
+      double vis[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int dd = 0; dd < 3; ++dd) {
+        const int id = ijk[dd];
+        const int st = dd == 0 ? 1 : dd == 1 ? n : nn;
+        const int base = node - id * st;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          double acc = 0.0;
+#pragma unroll
+          for (int m = 0; m < n; ++m)
+            if (m != id) acc += c_D[id * n + m] * Fve[(dd * 4 + q) * nnn + base + m * st];
+          vis[q] += acc;
+        }
+        if (id == 0 || id == N) {  // -(1/(2 w_b)) phi_nb, phi_nb = neighbour's outward normal viscous flux
+          const int f = 2 * dd + (id == N ? 1 : 0);
+          const int pp = dd == 0 ? ijk[1] : ijk[0], qq = dd == 2 ? ijk[1] : ijk[2];
+          const int *ef = d.ef + ((size_t)e * 6 + f) * 4;
+          const int nb = ef[0], fnb = ef[1], o = ef[2];
+          int p2, q2;
+          orient_map(o, pp, qq, p2, q2);
+          const int nbnode = face_node(fnb, p2, q2);
+          const double sg = (fnb & 1) ? 0.5 : -0.5;
+          const double *Fvn = d.Fv + ((size_t)nb * 12 + (fnb >> 1) * 4) * nnn + nbnode;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) vis[q] -= c_invw[id] * sg * Fvn[q * nnn];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s[1 + q] -= vis[q];
+    }
+    const double miJ = -d.invJ[(size_t)e * nnn + node];
+    const size_t gi = (size_t)e * 5 * nnn + node;
+    if (mode == 0) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) out[gi + v * nnn] = miJ * s[v];
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double ut = miJ * s[v];
+        const double gv = first ? dt * ut : A * g[gi + v * nnn] + dt * ut;
+        g[gi + v * nnn] = gv;
+        out[gi + v * nnn] = U[gi + v * nnn] + B * gv;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// modified Persson indicator (Sec. 4.1, Eq. (4)) and the neighbour extension
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_indicator(const DgDevice d, const double *__restrict__ U) {
+  __shared__ double q[nnn], t1[nnn];
+  __shared__ double red[3][128];
+  const int e = blockIdx.x;
+  const double gm1 = d.gamma - 1.0;
+  for (int node = threadIdx.x; node < nnn; node += blockDim.x) {
+    const double *Ue = U + (size_t)e * 5 * nnn + node;
+    const double r = Ue[0];
+    const double p = gm1 * (Ue[4 * nnn] - 0.5 * (Ue[nnn] * Ue[nnn] + Ue[2 * nnn] * Ue[2 * nnn] + Ue[3 * nnn] * Ue[3 * nnn]) / r);
+    q[node] = r * p;
+  }
+  __syncthreads();
+  // modal coefficients: three tensor-product passes with the inverse Vandermonde
+  for (int node = threadIdx.x; node < nnn; node += blockDim.x) {  // xi: (i,j,k) -> (a,j,k)
+    const int a = node % n, base = node - a;
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < n; ++i) s += c_Vinv[a * n + i] * q[base + i];
+    t1[node] = s;
+  }
+  __syncthreads();
+  for (int node = threadIdx.x; node < nnn; node += blockDim.x) {  // eta
+    const int b = (node / n) % n, base = node - b * n;
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < n; ++j) s += c_Vinv[b * n + j] * t1[base + j * n];
+    q[node] = s;
+  }
+  __syncthreads();
+  double all = 0.0, shN = 0.0, shN1 = 0.0;
+  for (int node = threadIdx.x; node < nnn; node += blockDim.x) {  // zeta, then the shell energies
+    const int a = node % n, b = (node / n) % n, c = node / nn, base = node - c * nn;
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < n; ++k) s += c_Vinv[c * n + k] * q[base + k * nn];
+    const int M = max(a, max(b, c));
+    const double m2 = s * s;
+    all += m2;
+    if (M == N) shN += m2;
+    if (M == N - 1) shN1 += m2;
+  }
+  red[0][threadIdx.x] = all;
+  red[1][threadIdx.x] = shN;
+  red[2][threadIdx.x] = shN1;
+  __syncthreads();
+  for (int w = 64; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double tot = red[0][0], sN = red[1][0], sN1 = red[2][0];
+    double E = tot > 1e-300 ? sN / tot : 0.0;
+    if (N >= 2) {
+      const double tot1 = tot - sN;
+      const double E1 = tot1 > 1e-300 ? sN1 / tot1 : 0.0;
+      E = fmax(E, E1);
+    }
+    const double T = 0.5 * pow(10.0, -1.8 * pow((double)(N + 1), 0.25));
+    double al = 1.0 / (1.0 + exp(-d.sharpness / T * (E - T)));
+    if (al < d.alpha_min) al = 0.0;
+    if (al > d.alpha_max) al = d.alpha_max;
+    d.alpha_raw[e] = al;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_spread(const DgDevice d, double *alpha_out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.nE) return;
+  double a = d.alpha_raw[e];
+#pragma unroll
+  for (int f = 0; f < 6; ++f) a = fmax(a, 0.5 * d.alpha_raw[d.ef[(e * 6 + f) * 4]]);
+  alpha_out[e] = a;
+}
+
+// ---------------------------------------------------------------------------------------------
+// reductions: integral invariants and the time-step estimate (deterministic two-pass)
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_invariants(const DgDevice d, const double *__restrict__ U,
+                                                    const double *__restrict__ Ut) {
+  __shared__ double red[8][256];
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const long long total = (long long)d.nE * nnn;
+  const double gam = d.gamma;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const int e = (int)(t / nnn), node = (int)(t % nnn);
+    const int i = node % n, j = (node / n) % n, k = node / nn;
+    const double wq = c_w[i] * c_w[j] * c_w[k] * d.J[t];
+    const size_t b = (size_t)e * 5 * nnn + node;
+    double Uv[5], Tv[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) { Uv[v] = U[b + v * nnn]; Tv[v] = Ut[b + v * nnn]; }
+    const double r = Uv[0], ir = 1.0 / r;
+    const double u = Uv[1] * ir, v = Uv[2] * ir, w = Uv[3] * ir;
+    const double q2 = u * u + v * v + w * w;
+    const double p = (gam - 1.0) * (Uv[4] - 0.5 * r * q2);
+    const double s = log(p) - gam * log(r);
+    const double ip = 1.0 / p;
+    const double ev[5] = {(gam - s) / (gam - 1.0) - 0.5 * r * q2 * ip, r * u * ip, r * v * ip, r * w * ip, -r * ip};
+#pragma unroll
+    for (int m = 0; m < 5; ++m) acc[m] += wq * Tv[m];
+    acc[5] += wq * (ev[0] * Tv[0] + ev[1] * Tv[1] + ev[2] * Tv[2] + ev[3] * Tv[3] + ev[4] * Tv[4]);
+    acc[6] += wq * 0.5 * r * q2;
+    acc[7] += wq * (u * Tv[1] + v * Tv[2] + w * Tv[3] - 0.5 * q2 * Tv[0]);
+  }
+#pragma unroll
+  for (int m = 0; m < 8; ++m) red[m][threadIdx.x] = acc[m];
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+#pragma unroll
+      for (int m = 0; m < 8; ++m) red[m][threadIdx.x] += red[m][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < 8) d.red[blockIdx.x * 8 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void k_reduce_partials(const double *__restrict__ part, int nblocks, int width, int op_min, double *out) {
+  // one thread per output column, fixed summation order (deterministic)
+  const int c = threadIdx.x;
+  if (c >= width) return;
+  double s = op_min ? part[c] : 0.0;
+  for (int b = op_min ? 1 : 0; b < nblocks; ++b) {
+    const double x = part[b * width + c];
+    s = op_min ? fmin(s, x) : s + x;
+  }
+  out[c] = s;
+}
+
+__global__ void __launch_bounds__(256) k_max_dt(const DgDevice d, const double *__restrict__ U) {
+  __shared__ double red[256];
+  double best = 1e300;
+  const long long total = (long long)d.nE * nnn;
+  const double gam = d.gamma;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const int e = (int)(t / nnn), node = (int)(t % nnn);
+    const size_t b = (size_t)e * 5 * nnn + node;
+    const double r = U[b], ir = 1.0 / r;
+    const double u = U[b + nnn] * ir, v = U[b + 2 * nnn] * ir, w = U[b + 3 * nnn] * ir;
+    const double p = (gam - 1.0) * (U[b + 4 * nnn] - 0.5 * r * (u * u + v * v + w * w));
+    const double c = sqrt(gam * p * ir);
+    double lam = 0.0;
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) {
+      const double *Jd = d.Ja + ((size_t)e * 3 + dd) * 3 * nnn + node;
+      const double ax = Jd[0], ay = Jd[nnn], az = Jd[2 * nnn];
+      lam += fabs(u * ax + v * ay + w * az) + c * sqrt(ax * ax + ay * ay + az * az);
+    }
+    best = fmin(best, 2.0 * d.J[t] / ((2.0 * N + 1.0) * lam));
+  }
+  red[threadIdx.x] = best;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmin(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) d.red[blockIdx.x] = red[0];
+}
+
+// ---------------------------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------------------------
+cudaError_t upload(const DgTables &t) {
+  if (t.N != N) return cudaErrorInvalidValue;
+  double D2[nn], Dq[nn], De[nn];
+  for (int i = 0; i < n; ++i)
+    for (int m = 0; m < n; ++m) {
+      const double v = (i == m) ? 0.0 : t.D[i * n + m];
+      D2[i * n + m] = 2.0 * v;
+      Dq[i * n + m] = 0.25 * v;
+      De[i * n + m] = 0.125 * v;
+    }
+  cudaError_t err = cudaSuccess;
+  err = err ? err : cudaMemcpyToSymbol(c_D, t.D, sizeof(double) * nn);
+  err = err ? err : cudaMemcpyToSymbol(c_D2, D2, sizeof(double) * nn);
+  err = err ? err : cudaMemcpyToSymbol(c_Dq, Dq, sizeof(double) * nn);
+  err = err ? err : cudaMemcpyToSymbol(c_De, De, sizeof(double) * nn);
+  err = err ? err : cudaMemcpyToSymbol(c_w, t.w, sizeof(double) * n);
+  err = err ? err : cudaMemcpyToSymbol(c_invw, t.invw, sizeof(double) * n);
+  err = err ? err : cudaMemcpyToSymbol(c_xi, t.xi, sizeof(double) * n);
+  err = err ? err : cudaMemcpyToSymbol(c_xh, t.xh, sizeof(double) * (n + 1));
+  err = err ? err : cudaMemcpyToSymbol(c_Vinv, t.Vinv, sizeof(double) * nn);
+  return err;
+}
+
+void launch_metrics(const DgDevice &d, cudaStream_t s) {
+  const size_t smem = sizeof(double) * 14 * nnn;
+  cudaFuncSetAttribute(k_metrics, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_metrics<<<d.nE, 256, smem, s>>>(d);
+}
+
+void launch_face_normals(const DgDevice &d, cudaStream_t s) {
+  const long long pts = (long long)d.nF * nn;
+  k_face_normals<<<(unsigned)((pts + 255) / 256), 256, 0, s>>>(d);
+}
+
+void launch_face(const DgDevice &d, const double *U, cudaStream_t s) {
+  const long long pts = (long long)d.nF * nn;
+  const unsigned grid = (unsigned)((pts + 255) / 256);
+  switch (d.sflux) {
+    case SF_LLF: k_face<SF_LLF><<<grid, 256, 0, s>>>(d, U); break;
+    case SF_ROE: k_face<SF_ROE><<<grid, 256, 0, s>>>(d, U); break;
+    default: k_face<SF_EC><<<grid, 256, 0, s>>>(d, U); break;
+  }
+}
+
+void launch_lift(const DgDevice &d, const double *U, cudaStream_t s) {
+  k_lift<<<(d.nE + LIFT_EPB - 1) / LIFT_EPB, LIFT_THREADS, 0, s>>>(d, U);
+}
+
+template <int VF, bool SC>
+void launch_volume_t(const DgDevice &d, const double *U, double *out, double *g, int mode, int first, double dt,
+                     double A, double B, cudaStream_t s) {
+  const size_t smem = sizeof(double) * (VOL_EPB * NP * PS + VOL_EPB * 15 * PS + (SC ? VOL_EPB * 5 * nnn : 0));
+  static bool attr_set = false;  // per instantiation; setting it twice is harmless
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_volume<VF, SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
+  k_volume<VF, SC><<<(d.nE + VOL_EPB - 1) / VOL_EPB, VOL_THREADS, smem, s>>>(d, U, out, g, mode, first, dt, A, B);
+}
+
+void launch_volume(const DgDevice &d, const double *U, double *out, double *g, int mode, int first, double dt,
+                   double A, double B, cudaStream_t s) {
+  const bool sc = d.shock_capturing != 0;
+  switch (d.vflux) {
+    case VF_KG:
+      if (sc) launch_volume_t<VF_KG, true>(d, U, out, g, mode, first, dt, A, B, s);
+      else launch_volume_t<VF_KG, false>(d, U, out, g, mode, first, dt, A, B, s);
+      break;
+    case VF_PIR:
+      if (sc) launch_volume_t<VF_PIR, true>(d, U, out, g, mode, first, dt, A, B, s);
+      else launch_volume_t<VF_PIR, false>(d, U, out, g, mode, first, dt, A, B, s);
+      break;
+    case VF_EC:
+      if (sc) launch_volume_t<VF_EC, true>(d, U, out, g, mode, first, dt, A, B, s);
+      else launch_volume_t<VF_EC, false>(d, U, out, g, mode, first, dt, A, B, s);
+      break;
+    default:
+      if (sc) launch_volume_t<VF_CEN, true>(d, U, out, g, mode, first, dt, A, B, s);
+      else launch_volume_t<VF_CEN, false>(d, U, out, g, mode, first, dt, A, B, s);
+      break;
+  }
+}
+
+void launch_indicator(const DgDevice &d, const double *U, cudaStream_t s) { k_indicator<<<d.nE, 128, 0, s>>>(d, U); }
+
+void launch_spread(const DgDevice &d, double *alpha_out, cudaStream_t s) {
+  k_spread<<<(d.nE + 255) / 256, 256, 0, s>>>(d, alpha_out);
+}
+
+void launch_invariants(const DgDevice &d, const double *U, const double *Ut, double *out8, cudaStream_t s) {
+  const long long total = (long long)d.nE * nnn;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > DG_RED_BLOCKS) blocks = DG_RED_BLOCKS;
+  k_invariants<<<blocks, 256, 0, s>>>(d, U, Ut);
+  k_reduce_partials<<<1, 32, 0, s>>>(d.red, blocks, 8, 0, out8);
+}
+
+void launch_max_dt(const DgDevice &d, const double *U, double *out, cudaStream_t s) {
+  const long long total = (long long)d.nE * nnn;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > DG_RED_BLOCKS) blocks = DG_RED_BLOCKS;
+  k_max_dt<<<blocks, 256, 0, s>>>(d, U);
+  k_reduce_partials<<<1, 32, 0, s>>>(d.red, blocks, 1, 1, out);
+}
+
+}  // namespace
+
+#define DG_CAT2(a, b) a##b
+#define DG_CAT(a, b) DG_CAT2(a, b)
+const DgKernelTable DG_CAT(dg_kernels_n, DG_N) = {
+    N,           upload,           launch_metrics, launch_face_normals, launch_face,  launch_lift,
+    launch_volume, launch_indicator, launch_spread,  launch_invariants,   launch_max_dt};

@@ -1,0 +1,247 @@
+"""Thin Python binding of libdg (include/dg.h): argument marshalling only.
+
+Every step of the solver runs in the library's CUDA kernels; PyTorch provides device memory
+and the stream. There is no CPU fallback: if libdg.so cannot be loaded, or a call fails, an
+exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdg.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "dg.h")
+
+DG_OK = 0
+STATUS = {0: "DG_OK", -1: "DG_ERR_ARG", -2: "DG_ERR_MESH", -3: "DG_ERR_JACOBIAN", -4: "DG_ERR_CUDA",
+          -5: "DG_ERR_NONPHYSICAL", -6: "DG_ERR_UNSUPPORTED", -7: "DG_ERR_OOM"}
+EQUATIONS = {"euler": 0, "ns": 1, "navier_stokes": 1}
+VFLUX = {"kg": 0, "pirozzoli": 1, "ec": 2, "central": 3}
+SFLUX = {"llf": 0, "roe": 1, "ec": 2}
+PRECISION = {"fp64": 0, "fp32_bulk": 1}
+DEFAULT_SHARPNESS = float(np.log((1.0 - 1e-4) / 1e-4))
+
+
+class DGError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Mesh(ctypes.Structure):
+    _fields_ = [("n_elems", ctypes.c_int), ("n_geo", ctypes.c_int), ("xyz", ctypes.c_void_p),
+                ("n_faces", ctypes.c_int), ("face", ctypes.c_void_p)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("equations", ctypes.c_int), ("volume_flux", ctypes.c_int), ("surface_flux", ctypes.c_int),
+                ("precision", ctypes.c_int), ("gamma", ctypes.c_double), ("R", ctypes.c_double),
+                ("mu", ctypes.c_double), ("Pr", ctypes.c_double), ("shock_capturing", ctypes.c_int),
+                ("alpha_min", ctypes.c_double), ("alpha_max", ctypes.c_double), ("sharpness", ctypes.c_double),
+                ("alpha_fixed", ctypes.c_double)]
+
+
+_lib = None
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/dg.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dg_[a-z_0-9]+)\s*\(", text)))
+
+
+def lib() -> ctypes.CDLL:
+    """Load libdg.so (built by paper_2306_12891_gb300.build). Raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libdg.so not built ({LIB_PATH}); run paper_2306_12891_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        sig = {
+            "dg_init": (i, [ctypes.POINTER(_Mesh), i, i, ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)]),
+            "dg_rhs": (i, [vp, vp, vp, d]),
+            "dg_lserk_step": (i, [vp, vp, d, d]),
+            "dg_lserk_steps": (i, [vp, vp, d, d, i]),
+            "dg_lserk_step_host": (i, [vp, vp, d, d]),
+            "dg_indicator": (i, [vp, vp, vp]),
+            "dg_invariants": (i, [vp, vp, vp, vp]),
+            "dg_max_dt": (i, [vp, vp, d, vp]),
+            "dg_check": (i, [vp]),
+            "dg_get_metrics": (i, [vp, vp, vp]),
+            "dg_timing_enable": (i, [vp, i]),
+            "dg_timing_get": (i, [vp, vp, vp, vp, i]),
+            "dg_launch_count": (ctypes.c_longlong, [vp]),
+            "dg_free": (None, [vp]),
+            "dg_last_error": (ctypes.c_char_p, [vp]),
+            "dg_status_string": (ctypes.c_char_p, [i]),
+            "dg_basis": (i, [i, vp, vp, vp]),
+            "dg_probe_fma": (i, [i, vp, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def basis(N: int):
+    """(xi, w, D) tables the kernels use (host computation, no GPU)."""
+    n = N + 1
+    xi, w, D = np.zeros(n), np.zeros(n), np.zeros((n, n))
+    st = lib().dg_basis(N, xi.ctypes.data, w.ctypes.data, D.ctypes.data)
+    if st != DG_OK:
+        raise DGError(st, "dg_basis")
+    return xi, w, D
+
+
+def _stream_ptr(stream):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def probe_fma(kind: str = "fp64", stream=None) -> float:
+    """Measured FMA throughput in FLOP/s (kind 'fp64' or 'fp32')."""
+    out = ctypes.c_double(0.0)
+    st = lib().dg_probe_fma(0 if kind == "fp64" else 1, _stream_ptr(stream), ctypes.byref(out))
+    if st != DG_OK:
+        raise DGError(st, "dg_probe_fma")
+    return out.value
+
+
+class DG:
+    """A solver context: mesh, degree N, physics and the CUDA stream its calls are queued on."""
+
+    def __init__(self, N, xyz, faces, equations="euler", vflux="kg", sflux="llf", precision="fp64", gamma=1.4,
+                 R=1.0, mu=0.0, Pr=0.72, shock_capturing=False, alpha_min=0.01, alpha_max=0.7,
+                 sharpness=DEFAULT_SHARPNESS, alpha_fixed=-1.0, stream=None):
+        import torch
+
+        self.torch = torch
+        self.N, self.n = int(N), int(N) + 1
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        faces = np.ascontiguousarray(faces, dtype=np.int32)
+        self.nE = xyz.shape[0]
+        self.shape = (self.nE, 5, self.n, self.n, self.n)
+        self.numel = int(np.prod(self.shape))
+        mesh = _Mesh(self.nE, self.N, xyz.ctypes.data, faces.shape[0], faces.ctypes.data)
+        prm = _Params(EQUATIONS[equations], VFLUX[vflux], SFLUX[sflux], PRECISION[precision], gamma, R, mu, Pr,
+                      int(bool(shock_capturing)), alpha_min, alpha_max, sharpness, float(alpha_fixed))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        ctx = ctypes.c_void_p(None)
+        st = lib().dg_init(ctypes.byref(mesh), self.N, 0, ctypes.byref(prm), ctypes.c_void_p(self.stream.cuda_stream),
+                           ctypes.byref(ctx))
+        if st != DG_OK:
+            raise DGError(st, "dg_init")
+        self._ctx = ctx
+
+    # ------------------------------------------------------------------ helpers
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            lib().dg_free(self._ctx)
+            self._ctx = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != DG_OK:
+            msg = lib().dg_last_error(self._ctx)
+            raise DGError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def _state(self, U, name="U"):
+        t = self.torch
+        if not isinstance(U, t.Tensor) or U.dtype != t.float64 or not U.is_cuda or not U.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+        if U.numel() != self.numel:
+            raise ValueError(f"{name} must have {self.numel} elements")
+        return ctypes.c_void_p(U.data_ptr())
+
+    # ------------------------------------------------------------------ solver calls
+    def rhs(self, U, Ut=None, t=0.0):
+        if Ut is None:
+            Ut = self.torch.empty_like(U)
+        self._check(lib().dg_rhs(self._ctx, self._state(U), self._state(Ut, "Ut"), float(t)), "dg_rhs")
+        return Ut
+
+    def lserk_step(self, U, dt, t=0.0):
+        self._check(lib().dg_lserk_step(self._ctx, self._state(U), float(dt), float(t)), "dg_lserk_step")
+        return U
+
+    def lserk_steps(self, U, dt, n_steps, t=0.0):
+        self._check(lib().dg_lserk_steps(self._ctx, self._state(U), float(dt), float(t), int(n_steps)),
+                    "dg_lserk_steps")
+        return U
+
+    def lserk_step_host(self, U_host, dt, t=0.0):
+        """One step on a host array (numpy float64 or a CPU torch tensor, ideally pinned)."""
+        if isinstance(U_host, np.ndarray):
+            if U_host.dtype != np.float64 or not U_host.flags.c_contiguous or U_host.size != self.numel:
+                raise ValueError("U_host must be a contiguous float64 array of the state's size")
+            ptr = U_host.ctypes.data
+        else:
+            if U_host.dtype != self.torch.float64 or U_host.is_cuda or not U_host.is_contiguous() or \
+                    U_host.numel() != self.numel:
+                raise ValueError("U_host must be a contiguous float64 CPU tensor of the state's size")
+            ptr = U_host.data_ptr()
+        self._check(lib().dg_lserk_step_host(self._ctx, ctypes.c_void_p(ptr), float(dt), float(t)),
+                    "dg_lserk_step_host")
+        return U_host
+
+    def indicator(self, U, alpha=None):
+        if alpha is None:
+            alpha = self.torch.empty(self.nE, dtype=self.torch.float64, device=U.device)
+        if alpha.dtype != self.torch.float64 or not alpha.is_cuda or alpha.numel() != self.nE:
+            raise ValueError("alpha must be a float64 CUDA tensor of n_elems entries")
+        self._check(lib().dg_indicator(self._ctx, self._state(U), ctypes.c_void_p(alpha.data_ptr())), "dg_indicator")
+        return alpha
+
+    def invariants(self, U, Ut):
+        out = np.zeros(8)
+        self._check(lib().dg_invariants(self._ctx, self._state(U), self._state(Ut, "Ut"), out.ctypes.data),
+                    "dg_invariants")
+        return out
+
+    def max_dt(self, U, cfl):
+        out = ctypes.c_double(0.0)
+        self._check(lib().dg_max_dt(self._ctx, self._state(U), float(cfl), ctypes.byref(out)), "dg_max_dt")
+        return out.value
+
+    def check(self):
+        self._check(lib().dg_check(self._ctx), "dg_check")
+
+    def metrics(self):
+        t = self.torch
+        n = self.n
+        Ja = t.empty((self.nE, 3, 3, n, n, n), dtype=t.float64, device="cuda")
+        J = t.empty((self.nE, n, n, n), dtype=t.float64, device="cuda")
+        self._check(lib().dg_get_metrics(self._ctx, ctypes.c_void_p(Ja.data_ptr()), ctypes.c_void_p(J.data_ptr())),
+                    "dg_get_metrics")
+        return Ja, J
+
+    def timing_enable(self, on=True):
+        self._check(lib().dg_timing_enable(self._ctx, int(bool(on))), "dg_timing_enable")
+
+    def timing_get(self) -> dict:
+        cap = 16
+        names = (ctypes.c_char_p * cap)()
+        ms = (ctypes.c_double * cap)()
+        cnt = (ctypes.c_longlong * cap)()
+        k = lib().dg_timing_get(self._ctx, names, ms, cnt, cap)
+        if k < 0:
+            raise DGError(-1, "dg_timing_get")
+        return {names[i].decode(): (ms[i], cnt[i]) for i in range(k)}
+
+    def launch_count(self) -> int:
+        return int(lib().dg_launch_count(self._ctx))

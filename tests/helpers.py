@@ -3,17 +3,20 @@ import numpy as np
 
 
 def euler_flux_magnitude(U, Ja, gamma=1.4):
-    """Per node and variable: sum_d |F^d_v(U)| with F^d the contravariant Euler flux, a magnitude
-    estimate of the terms the right-hand side differences (numpy, vectorised)."""
+    """Per node and variable: sum_d (|F^d_v(U)| + c |Ja^d| |U_v|) with F^d the contravariant Euler
+    flux and c the sound speed -- the size of the advective and dissipative flux terms the
+    right-hand side differences (numpy, vectorised)."""
     rho = U[:, 0]
     u = U[:, 1:4] / rho[:, None]
     p = (gamma - 1.0) * (U[:, 4] - 0.5 * rho * (u * u).sum(1))
+    c = np.sqrt(gamma * np.abs(p) / np.abs(rho))
     out = np.zeros(U.shape)
     for d in range(3):
         V = (u * Ja[:, d]).sum(1)  # u . Ja^d
-        F = [rho * V] + [U[:, 1 + c] * V + p * Ja[:, d, c] for c in range(3)] + [(U[:, 4] + p) * V]
+        s = np.sqrt((Ja[:, d] ** 2).sum(1))
+        F = [rho * V] + [U[:, 1 + c_] * V + p * Ja[:, d, c_] for c_ in range(3)] + [(U[:, 4] + p) * V]
         for v in range(5):
-            out[:, v] += np.abs(F[v])
+            out[:, v] += np.abs(F[v]) + c * s * np.abs(U[:, v])
     return out
 
 
