@@ -4,7 +4,7 @@
  * (arXiv 2306.12891): the right-hand side of the compressible Euler / Navier-Stokes-Fourier
  * equations on curved hexahedra with Legendre-Gauss-Lobatto nodes (Sec. 2), its explicit
  * low-storage Runge-Kutta stage update (Sec. 2, Eq. (1)), and the DG/FV subcell blend with the
- * modified Persson indicator (Sec. 4.1, Eqs. (3)-(4)).
+ * modified Persson indicator (Sec. 4.1, Eqs. (6)-(7)).
  *
  * Conventions
  *  - n = N+1; node index = i + n*(j + n*k), i along xi.
@@ -68,10 +68,10 @@ typedef struct {
   int surface_flux;   /* DG_SFLUX_* */
   int precision;      /* DG_FP64 | DG_FP32_BULK */
   double gamma, R, mu, Pr; /* ideal gas, constant viscosity, Prandtl number */
-  int shock_capturing;     /* 1: DG/FV subcell blend (Sec. 4.1, Eq. (3)) */
+  int shock_capturing;     /* 1: DG/FV subcell blend (Sec. 4.1, Eq. (6)) */
   double alpha_min;        /* alpha < alpha_min -> pure DG (Sec. 4.2: 0.01) */
   double alpha_max;        /* alpha clipped to alpha_max (Sec. 4.2: 0.7) */
-  double sharpness;        /* s of the indicator sigmoid (Sec. 4.1, Eq. (4)) */
+  double sharpness;        /* s of the indicator sigmoid (Sec. 4.1, Eq. (7)) */
   double alpha_fixed;      /* >= 0: use this blending coefficient on every element; < 0: indicator */
 } dg_params;
 
@@ -82,7 +82,7 @@ typedef struct {
 dg_status dg_init(const dg_mesh *mesh, int N, int nodes, const dg_params *params, void *cuda_stream,
                   dg_ctx **out);
 
-/* Ut = L(U): the DGSEM time derivative at time t (Sec. 2; Sec. 4.1, Eq. (3) when shock capturing
+/* Ut = L(U): the DGSEM time derivative at time t (Sec. 2; Sec. 4.1, Eq. (6) when shock capturing
  * is on). U and Ut are device arrays [n_elems][5][n]^3 and must not overlap. */
 dg_status dg_rhs(dg_ctx *ctx, const double *U, double *Ut, double t);
 
@@ -97,7 +97,7 @@ dg_status dg_lserk_steps(dg_ctx *ctx, double *U, double dt, double t, int n_step
  * copies the result back; synchronising. U_host should be pinned for full copy bandwidth. */
 dg_status dg_lserk_step_host(dg_ctx *ctx, double *U_host, double dt, double t);
 
-/* alpha[e] = blending coefficient of element e (Sec. 4.1, Eq. (4): modified Persson indicator on
+/* alpha[e] = blending coefficient of element e (Sec. 4.1, Eq. (7): modified Persson indicator on
  * rho*p, clipped to [alpha_min, alpha_max] (Sec. 4.2), extended to face neighbours by 1/2).
  * alpha: device array [n_elems]. */
 dg_status dg_indicator(dg_ctx *ctx, const double *U, double *alpha);

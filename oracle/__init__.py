@@ -3,7 +3,7 @@
 A plain, slow restatement (``dgsem_oracle.c``) of what arXiv 2306.12891's solver
 computes: the split-form DGSEM right-hand side on curved hexahedra (Sec. 2, Sec. 4.1),
 its explicit Runge-Kutta step (Sec. 2, Eq. (1)), the modified Persson indicator
-(Sec. 4.1, Eq. (4)) and the DG/FV blend (Sec. 4.1, Eq. (3)).
+(Sec. 4.1, Eq. (7)) and the DG/FV blend (Sec. 4.1, Eq. (6)).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
 may import this package. The CUDA path never does, and this package never imports the

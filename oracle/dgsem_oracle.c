@@ -11,10 +11,10 @@
  *   - BR1 lifting of the primitive gradients (u, v, w, T) for the Navier-Stokes-Fourier
  *     viscous fluxes (Sec. 4: "Navier--Stokes--Fourier equations");
  *   - curvilinear metric terms in Kopriva's discrete curl form;
- *   - the hybrid DG/FV convex blend U_t = a U_t^FV + (1-a) U_t^DG (Sec. 4.1, Eq. (3)) with a
+ *   - the hybrid DG/FV convex blend U_t = a U_t^FV + (1-a) U_t^DG (Sec. 4.1, Eq. (6)) with a
  *     second-order minmod FV scheme in the interior subcells and first order in the outer
  *     subcells (Sec. 4.1), blending coefficient from the modified Persson indicator
- *     (Sec. 4.1, Eq. (4)), clipped to [alpha_min, alpha_max] (Sec. 4.2) and extended to face
+ *     (Sec. 4.1, Eq. (7)), clipped to [alpha_min, alpha_max] (Sec. 4.2) and extended to face
  *     neighbours by a factor 1/2 (Sec. 4.1);
  *   - the explicit low-storage Runge-Kutta scheme LSERK(5,4) of Carpenter and Kennedy
  *     (the "explicit Runge--Kutta scheme" of Sec. 2).
@@ -557,7 +557,7 @@ static void lift_element(orc_state *s, const double *U, int e) {
 }
 
 /* ======================================================================= */
-/* 7. Modified Persson indicator (Sec. 4.1, Eq. (4))                         */
+/* 7. Modified Persson indicator (Sec. 4.1, Eq. (7))                         */
 /* ======================================================================= */
 
 static double indicator_element(const orc_state *s, const double *U, int e) {

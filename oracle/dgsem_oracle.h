@@ -7,7 +7,7 @@
  * equations on curved hexahedra (split-form flux differencing on Legendre-Gauss-Lobatto
  * nodes, Sec. 2 "Performance" and Sec. 4.1 "Hybrid DGSE/FV subcell scheme"), its
  * explicit Runge-Kutta time step (Sec. 2, Eq. (1) counts its stages), the modified
- * Persson indicator (Sec. 4.1, Eq. (4)) and the DG/FV convex blend (Sec. 4.1, Eq. (3)).
+ * Persson indicator (Sec. 4.1, Eq. (7)) and the DG/FV convex blend (Sec. 4.1, Eq. (6)).
  *
  * Only the tests, the smoke check and the CPU-baseline leg of the benchmark may load
  * this library. It shares no code with the CUDA path. Every routine uses plain loops

@@ -3,13 +3,13 @@
 // namespace so each translation unit has its own constant-memory tables.
 //
 // Per RK stage (Sec. 2; Sec. 4.1):
-//   [indicator -> spread]   modified Persson indicator on rho*p (Sec. 4.1, Eq. (4)), alpha per element
+//   [indicator -> spread]   modified Persson indicator on rho*p (Sec. 4.1, Eq. (7)), alpha per element
 //   face                    Riemann flux s F*(U_L, U_R, n) once per face point (Roe / LLF / EC),
 //                           BR1 face jumps w* - w for the lifting (Navier-Stokes)
 //   [lift]                  BR1 gradients of (u, v, w, T) and the contravariant viscous flux
 //   volume                  split-form flux differencing along the three line families, viscous
 //                           divergence, surface terms, FV subcell operator + blend (Sec. 4.1,
-//                           Eq. (3)), Jacobian, and the fused LSERK(5,4) stage update
+//                           Eq. (6)), Jacobian, and the fused LSERK(5,4) stage update
 //
 // Algebra used by the volume kernel (exact identities of the LGL/SBP operator): with
 // D_00 = -1/(2 w_0), D_NN = 1/(2 w_N) and zero interior diagonal, the diagonal volume term
@@ -728,7 +728,7 @@ __global__ void __launch_bounds__(VOL_THREADS, 2) k_volume(const DgDevice d, con
 }
 
 // ---------------------------------------------------------------------------------------------
-// modified Persson indicator (Sec. 4.1, Eq. (4)) and the neighbour extension
+// modified Persson indicator (Sec. 4.1, Eq. (7)) and the neighbour extension
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_indicator(const DgDevice d, const double *__restrict__ U) {
   __shared__ double q[nnn], t1[nnn];

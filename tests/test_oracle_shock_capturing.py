@@ -1,7 +1,7 @@
-"""Pins of the oracle's shock-capturing pieces: the modified Persson indicator (Sec. 4.1, Eq. (4))
+"""Pins of the oracle's shock-capturing pieces: the modified Persson indicator (Sec. 4.1, Eq. (7))
 on states of known modal content, the clipping to [0.01, 0.7] (Sec. 4.2), the factor-1/2
 extension to neighbours (Sec. 4.1), and the FV subcell operator (freestream, conservation,
-no new extrema at a discontinuity, consistency) and the DG/FV blend (Sec. 4.1, Eq. (3))."""
+no new extrema at a discontinuity, consistency) and the DG/FV blend (Sec. 4.1, Eq. (6))."""
 import math
 
 import numpy as np
