@@ -107,6 +107,25 @@ dg_status dg_indicator(dg_ctx *ctx, const double *U, double *alpha);
  * out[6] = sum J w rho|u|^2/2; out[7] = sum J w d/dt(rho|u|^2/2). */
 dg_status dg_invariants(dg_ctx *ctx, const double *U, const double *Ut, double out[8]);
 
+/* The same eight integrals as dg_invariants, for callers that cannot allocate device memory where
+ * they need them: a stream being captured into a CUDA graph (cudaMalloc is not allowed during
+ * capture), a host callback, or a host framework whose memory pool holds nearly all of the device
+ * memory. (The paper has no counterpart; this is a service of the library.)
+ *  - Needs no context and allocates nothing: every input and output belongs to the caller.
+ *    U, Ut: device [n_elems][5][N+1]^3; J: device Jacobian [n_elems][N+1]^3 (e.g. from
+ *    dg_get_metrics); out8: device double[8], written asynchronously on `cuda_stream`
+ *    (no synchronisation; read it after the stream has reached this work).
+ *  - Partial sums live in one fixed device array of 2048 x 8 doubles (128 KiB) inside the library,
+ *    which every GPU that loads the library keeps until exit. At most 33,554,432 nodes
+ *    (n_elems * (N+1)^3) fit; larger problems return DG_ERR_UNSUPPORTED before any launch.
+ *    Bad arguments return DG_ERR_ARG, launch failures DG_ERR_CUDA.
+ *  - The first call on each device looks up the array's device address (with that device
+ *    current); make that first call before any stream capture.
+ *  - All calls share the array and it keeps the last call's partial sums; calls whose kernels
+ *    overlap on the GPU (different streams, several host threads) race on it -- serialise them. */
+dg_status dg_invariants_noalloc(int N, int n_elems, double gamma, const double *U, const double *Ut,
+                                const double *J, double *out8, void *cuda_stream);
+
 /* *dt = cfl * min over nodes of 2J / ((2N+1) sum_d (|u.Ja^d| + c|Ja^d|)) (synchronising). */
 dg_status dg_max_dt(dg_ctx *ctx, const double *U, double cfl, double *dt);
 

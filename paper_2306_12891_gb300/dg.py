@@ -82,6 +82,7 @@ def lib() -> ctypes.CDLL:
             "dg_status_string": (ctypes.c_char_p, [i]),
             "dg_basis": (i, [i, vp, vp, vp]),
             "dg_probe_fma": (i, [i, vp, vp]),
+            "dg_invariants_noalloc": (i, [i, i, d, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
