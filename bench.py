@@ -34,6 +34,11 @@ WORKLOAD = "tgv_ns_n7_32x32x32_curved"
 METRIC = "DOF-stage updates/s (1/PID), N=7 split-form Navier-Stokes, FP64"
 UNIT = "DOF-stage/s"
 STAGES = 5
+# DRAM bytes per element of one volume-kernel launch (dram__bytes_read.sum + dram__bytes_write.sum),
+# from an ncu capture of the current kernel on the 16^3 case (profiles/k_volume_tgv_ns_n7_16x16x16.md),
+# scaled to a launch by the element count (the kernel's traffic is per element). None once the kernel
+# has changed since that capture.
+VOLUME_DRAM_BYTES_PER_ELEMENT = 745.4e6 / 16 ** 3
 
 
 def volume_kernel_flops_per_element(N: int, navier_stokes: bool) -> float:
@@ -267,7 +272,9 @@ def run_gpu(args):
         "pid_s_per_dof_stage": 1.0 / (value / world),
         "roofline": {"bound": "alu", "kernel": "volume (split-form flux differencing, FP64 pipe)",
                      "achieved": achieved / 1e12 if achieved else None, "peak": peak_fp64 / 1e12,
-                     "unit": "TFLOP/s", "frac": (achieved / peak_fp64) if achieved else None, "traffic": None,
+                     "unit": "TFLOP/s", "frac": (achieved / peak_fp64) if achieved else None,
+                     "traffic": (VOLUME_DRAM_BYTES_PER_ELEMENT * w.n_elems
+                                 if VOLUME_DRAM_BYTES_PER_ELEMENT else None),
                      "flops_per_launch": flops_launch, "peak_source": "measured FP64 FMA probe (dg_probe_fma), live"},
         "kernels": breakdown,
         "gpu_launches": launches,
