@@ -34,6 +34,7 @@ WORKLOAD = "tgv_ns_n7_32x32x32_curved"
 METRIC = "DOF-stage updates/s (1/PID), N=7 split-form Navier-Stokes, FP64"
 UNIT = "DOF-stage/s"
 STAGES = 5
+P0_TGV = 1.0 / (1.4 * 0.1 ** 2)  # background pressure of the Ma 0.1 Taylor-Green vortex
 # DRAM bytes per element of one volume-kernel launch (dram__bytes_read.sum + dram__bytes_write.sum),
 # from an ncu capture of the current kernel on the 16^3 case (profiles/k_volume_tgv_ns_n7_16x16x16.md),
 # scaled to a launch by the element count (the kernel's traffic is per element). None once the kernel
@@ -248,6 +249,37 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(world, time.perf_counter() - t0)
 
+    # the FP32-bulk form on the same workload: throughput and its error against the FP64 state
+    fp32 = None
+    if args.fp32:
+        U64 = U.clone()  # FP64 state after warmup + steps (the e2e steps ran on a host copy)
+        n_done = args.warmup + args.steps
+        del solver
+        s32 = dg.DG(w.N, xyz, faces, stream=stream, precision="fp32_bulk", p_ref=P0_TGV, **w.physics())
+        V = torch.from_numpy(U0).cuda()
+        s32.lserk_steps(V, dt, args.warmup)
+        torch.cuda.synchronize()
+        barrier(world)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        s32.lserk_steps(V, dt, args.steps)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms32 = max_over_ranks(world, f0.elapsed_time(f1))
+        s32.lserk_steps(V, dt, n_done - args.warmup - args.steps)
+        s32.check()
+        d = (V - U64).abs().amax(dim=(0, 2, 3, 4))
+        change = (U64 - torch.from_numpy(U0).cuda()).abs().amax(dim=(0, 2, 3, 4))
+        scale = U64.abs().amax(dim=(0, 2, 3, 4))
+        value32 = world * w.dofs * STAGES * args.steps / (ms32 * 1e-3)
+        fp32 = {"value": value32, "unit": UNIT, "ms_per_step": ms32 / args.steps,
+                "speedup_vs_fp64": value32 / (world * w.dofs * STAGES * args.steps / (ms * 1e-3)),
+                "steps_compared": n_done,
+                "linf_err_rel_to_state": (d / scale).tolist(),
+                "linf_err_rel_to_change": (d / change).tolist(),
+                "p_ref": P0_TGV}
+        del s32
+
     dofs = w.dofs
     total_updates = world * dofs * STAGES * args.steps
     value = total_updates / (ms * 1e-3)
@@ -282,6 +314,8 @@ def run_gpu(args):
         "e2e": {"value": world * dofs * STAGES * e2e_steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
     }
+    if fp32:
+        line["fp32_bulk"] = fp32
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -294,6 +328,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-fp32", dest="fp32", action="store_false", help="skip the FP32-bulk comparison")
     ap.add_argument("--nel", type=int, default=None, help="elements per direction (default: the workload's 32)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -73,6 +73,10 @@ typedef struct {
   double alpha_max;        /* alpha clipped to alpha_max (Sec. 4.2: 0.7) */
   double sharpness;        /* s of the indicator sigmoid (Sec. 4.1, Eq. (7)) */
   double alpha_fixed;      /* >= 0: use this blending coefficient on every element; < 0: indicator */
+  double p_ref;            /* DG_FP32_BULK only (ignored in DG_FP64): reference pressure removed from the
+                              pressure term of the momentum flux. Exact: its contribution is p_ref times the
+                              discrete metric identity, zero. Set it near the mean pressure (e.g. p0 of a
+                              low-Mach flow) so FP32 forms p - p_ref from O(1) numbers; 0 disables it. */
 } dg_params;
 
 /* Build a solver for `mesh` at polynomial degree N (1..7) with `nodes` = DG_NODES_LGL.

@@ -194,7 +194,7 @@ dg_status dg_init(const dg_mesh *mesh, int N, int nodes, const dg_params *prm, v
       prm->surface_flux < 0 || prm->surface_flux > 2 || prm->precision < 0 || prm->precision > 1)
     return DG_ERR_ARG;
   if (!(prm->gamma > 1.0) || !(prm->R > 0.0) || !(prm->mu >= 0.0) || !(prm->Pr > 0.0)) return DG_ERR_ARG;
-  if (prm->precision != DG_FP64) return DG_ERR_UNSUPPORTED;
+  if (!std::isfinite(prm->p_ref) || prm->p_ref < 0.0) return DG_ERR_ARG;
   const int nE = mesh->n_elems, nF = mesh->n_faces, n = N + 1, nn = n * n, nnn = nn * n;
   if ((long long)nF * 2 != (long long)nE * 6) return DG_ERR_MESH;
 
@@ -239,7 +239,9 @@ dg_status dg_init(const dg_mesh *mesh, int N, int nodes, const dg_params *prm, v
   d.kappa = prm->mu * prm->gamma * prm->R / ((prm->gamma - 1.0) * prm->Pr);
   d.alpha_min = prm->alpha_min; d.alpha_max = prm->alpha_max; d.sharpness = prm->sharpness;
   d.alpha_fixed = prm->alpha_fixed;
+  d.p_ref = prm->precision == DG_FP32_BULK ? prm->p_ref : 0.0;
   c->n_state = (size_t)nE * 5 * nnn;
+  const bool fp32 = prm->precision == DG_FP32_BULK;
 
   double *xyz = nullptr;
   int *face = nullptr;
@@ -252,10 +254,20 @@ dg_status dg_init(const dg_mesh *mesh, int N, int nodes, const dg_params *prm, v
   DG_ALLOC(d.J, (size_t)nE * nnn);
   DG_ALLOC(d.invJ, (size_t)nE * nnn);
   DG_ALLOC(d.nrm, (size_t)nF * 4 * nn);
-  DG_ALLOC(d.Fsurf, (size_t)nE * 6 * 5 * nn);
-  if (prm->equations == DG_NAVIER_STOKES) {
-    DG_ALLOC(d.Wsurf, (size_t)nE * 6 * 4 * nn);
-    DG_ALLOC(d.Fv, (size_t)nE * 12 * nnn);
+  if (fp32) {  // FP32-bulk: FP32 copies of the geometry and FP32 work buffers
+    DG_ALLOC(d.Jaf, (size_t)nE * 9 * nnn);
+    DG_ALLOC(d.nrm_f, (size_t)nF * 4 * nn);
+    DG_ALLOC(d.Fsurf_f, (size_t)nE * 6 * 5 * nn);
+    if (prm->equations == DG_NAVIER_STOKES) {
+      DG_ALLOC(d.Wsurf_f, (size_t)nE * 6 * 4 * nn);
+      DG_ALLOC(d.Fv_f, (size_t)nE * 12 * nnn);
+    }
+  } else {
+    DG_ALLOC(d.Fsurf, (size_t)nE * 6 * 5 * nn);
+    if (prm->equations == DG_NAVIER_STOKES) {
+      DG_ALLOC(d.Wsurf, (size_t)nE * 6 * 4 * nn);
+      DG_ALLOC(d.Fv, (size_t)nE * 12 * nnn);
+    }
   }
   DG_ALLOC(d.alpha_raw, (size_t)nE);
   DG_ALLOC(d.alpha, (size_t)nE);

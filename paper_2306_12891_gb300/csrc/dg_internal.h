@@ -23,6 +23,7 @@ struct DgDevice {
   int N, nE, nF;
   int equations, vflux, sflux, precision, shock_capturing;
   double gamma, R, mu, kappa, alpha_min, alpha_max, sharpness, alpha_fixed;
+  double p_ref;        // reference pressure removed from the momentum flux (FP32-bulk only; 0 in FP64)
   // geometry (built at init)
   const double *xyz;   // [nE][3][n^3]  (init only)
   double *Ja;          // [nE][3 d][3 c][n^3]
@@ -30,6 +31,7 @@ struct DgDevice {
   double *invJ;        // [nE][n^3]
   float *Jaf;          // FP32 copy of Ja for the FP32-bulk path (or null)
   double *nrm;         // [nF][4][n^2]: unit normal (x,y,z) outward from L, area factor s
+  float *nrm_f;        // FP32 copy of nrm for the FP32-bulk path (or null)
   const int *face;     // [nF][5]
   int *ef;             // [nE][6][4]: neighbour element, neighbour local face, orientation own->nb, face id
   // per-stage work buffers

@@ -17,8 +17,18 @@
 // sums off-diagonal pairs only and adds (1/w_b) F*_out at boundary nodes; for the viscous
 // (BR1 central) flux the same cancellation leaves -(1/(2 w_b)) phi_nb, the neighbour's outward
 // normal viscous flux. Pair symmetry F#(U_i,U_m) = F#(U_m,U_i) halves the two-point fluxes.
+//
+// Arithmetic type R: double for the FP64 path; float for the FP32-bulk path, where the flux,
+// lifting and accumulation arithmetic is FP32 while U is read as FP64, metrics and Jacobian are
+// computed in FP64 (the kernels read an FP32 rounding of Ja), and the 1/J scaling and the LSERK
+// update stay FP64. In FP32 the state is carried with E' = E - p_ref/(gamma-1) so that the
+// pressure p' = p - p_ref is formed from O(1) numbers; the momentum flux uses p' throughout
+// (volume, surface and subcell fluxes). The constant p_ref part of that flux contributes
+// p_ref times the discrete metric identity sum_d D_d Ja^d, which is zero, so the shift is exact.
 #pragma once
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "dg_internal.h"
 
@@ -33,7 +43,6 @@ constexpr int n = N + 1;
 constexpr int nn = n * n;
 constexpr int nnn = nn * n;
 constexpr int PS = n * (n + 1) * n;  // padded stride of one staged node quantity
-constexpr int NP = 7;                // staged quantities per node
 
 __constant__ double c_D[nn];      // D_im
 __constant__ double c_D2[nn];     // 2 D_im, zero diagonal
@@ -41,6 +50,51 @@ __constant__ double c_Dq[nn];     // D_im / 4 (scaled mass flux), zero diagonal
 __constant__ double c_De[nn];     // D_im / 8 (scaled momentum / energy flux), zero diagonal
 __constant__ double c_w[n], c_invw[n], c_xi[n], c_xh[n + 1];
 __constant__ double c_Vinv[nn];
+__constant__ float f_D[nn], f_D2[nn], f_Dq[nn], f_De[nn];
+__constant__ float f_w[n], f_invw[n], f_xi[n], f_xh[n + 1];
+
+// basis tables in the arithmetic type
+template <typename R> struct Tab;
+template <> struct Tab<double> {
+  static __device__ __forceinline__ double D(int k) { return c_D[k]; }
+  static __device__ __forceinline__ double D2(int k) { return c_D2[k]; }
+  static __device__ __forceinline__ double Dq(int k) { return c_Dq[k]; }
+  static __device__ __forceinline__ double De(int k) { return c_De[k]; }
+  static __device__ __forceinline__ double w(int k) { return c_w[k]; }
+  static __device__ __forceinline__ double invw(int k) { return c_invw[k]; }
+  static __device__ __forceinline__ double xi(int k) { return c_xi[k]; }
+  static __device__ __forceinline__ double xh(int k) { return c_xh[k]; }
+};
+template <> struct Tab<float> {
+  static __device__ __forceinline__ float D(int k) { return f_D[k]; }
+  static __device__ __forceinline__ float D2(int k) { return f_D2[k]; }
+  static __device__ __forceinline__ float Dq(int k) { return f_Dq[k]; }
+  static __device__ __forceinline__ float De(int k) { return f_De[k]; }
+  static __device__ __forceinline__ float w(int k) { return f_w[k]; }
+  static __device__ __forceinline__ float invw(int k) { return f_invw[k]; }
+  static __device__ __forceinline__ float xi(int k) { return f_xi[k]; }
+  static __device__ __forceinline__ float xh(int k) { return f_xh[k]; }
+};
+
+// per-stage buffers and metric copies in the arithmetic type
+template <typename R> struct Buf;
+template <> struct Buf<double> {
+  static __device__ __forceinline__ double *Fsurf(const DgDevice &d) { return d.Fsurf; }
+  static __device__ __forceinline__ double *Wsurf(const DgDevice &d) { return d.Wsurf; }
+  static __device__ __forceinline__ double *Fv(const DgDevice &d) { return d.Fv; }
+  static __device__ __forceinline__ const double *Ja(const DgDevice &d) { return d.Ja; }
+  static __device__ __forceinline__ const double *nrm(const DgDevice &d) { return d.nrm; }
+};
+template <> struct Buf<float> {
+  static __device__ __forceinline__ float *Fsurf(const DgDevice &d) { return d.Fsurf_f; }
+  static __device__ __forceinline__ float *Wsurf(const DgDevice &d) { return d.Wsurf_f; }
+  static __device__ __forceinline__ float *Fv(const DgDevice &d) { return d.Fv_f; }
+  static __device__ __forceinline__ const float *Ja(const DgDevice &d) { return d.Jaf; }
+  static __device__ __forceinline__ const float *nrm(const DgDevice &d) { return d.nrm_f; }
+};
+
+// whether the state is carried shifted by the reference pressure (FP32 only)
+template <typename R> constexpr bool kShift = std::is_same<R, float>::value;
 
 enum { VF_KG = 0, VF_PIR = 1, VF_EC = 2, VF_CEN = 3 };
 enum { SF_LLF = 0, SF_ROE = 1, SF_EC = 2 };
@@ -52,6 +106,8 @@ __host__ __device__ constexpr int vol_epb() {
 }
 constexpr int VOL_EPB = vol_epb();
 constexpr int VOL_THREADS = round32(3 * nn * VOL_EPB);
+// staged quantities per node: rho, u, v, w, 4 p_m, X, Y (+ p' for the FV operator)
+template <bool SC> __host__ __device__ constexpr int vol_np() { return SC ? 8 : 7; }
 // lifting kernel: whole elements per CTA, a thread per node (looped above 256 threads)
 __host__ __device__ constexpr int lift_epb() { return nnn >= 128 ? 1 : (128 + nnn - 1) / nnn; }
 constexpr int LIFT_EPB = lift_epb();
@@ -82,105 +138,129 @@ __device__ __forceinline__ void orient_map(int o, int p, int q, int &p2, int &q2
 
 __device__ __forceinline__ void flag_set(int *flag, int bit) { atomicOr(flag, bit); }
 
-// ---------------------------------------------------------------------------------------------
-// pointwise physics
-// ---------------------------------------------------------------------------------------------
-
-// Euler flux through the (unit or metric) vector a
-__device__ __forceinline__ void euler_flux_n(const double U[5], double gam, const double a[3], double F[5],
-                                             double &un, double &p) {
-  const double ir = 1.0 / U[0];
-  const double u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
-  p = (gam - 1.0) * (U[4] - 0.5 * (U[1] * u + U[2] * v + U[3] * w));
-  un = u * a[0] + v * a[1] + w * a[2];
-  F[0] = U[0] * un;
-  F[1] = U[1] * un + p * a[0];
-  F[2] = U[2] * un + p * a[1];
-  F[3] = U[3] * un + p * a[2];
-  F[4] = (U[4] + p) * un;
+// five conservative values of node `node` of element e, in the arithmetic type; FP32 carries E'
+template <typename R>
+__device__ __forceinline__ void load_state(const double *__restrict__ U, size_t e, int node, double eref, R out[5]) {
+  const double *Ue = U + e * 5 * nnn + node;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) out[v] = (R)Ue[v * nnn];
+  out[4] = kShift<R> ? (R)(Ue[4 * nnn] - eref) : (R)Ue[4 * nnn];
 }
 
-__device__ __forceinline__ double logmean(double a, double b) {
+// ---------------------------------------------------------------------------------------------
+// pointwise physics (pressure p' = p - p_ref enters the momentum flux; p_ref = 0 in FP64)
+// ---------------------------------------------------------------------------------------------
+
+// Euler flux through the (unit or metric) vector a; returns u.a and the true pressure p
+template <typename R>
+__device__ __forceinline__ void euler_flux_n(const R U[5], R gam, R pref, R href, const R a[3], R F[5], R &un, R &p) {
+  const R ir = R(1) / U[0];
+  const R u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
+  const R pm = (gam - R(1)) * (U[4] - R(0.5) * (U[1] * u + U[2] * v + U[3] * w));  // p'
+  un = u * a[0] + v * a[1] + w * a[2];
+  F[0] = U[0] * un;
+  F[1] = U[1] * un + pm * a[0];
+  F[2] = U[2] * un + pm * a[1];
+  F[3] = U[3] * un + pm * a[2];
+  if (kShift<R>) {
+    p = pm + pref;
+    F[4] = (U[4] + pm + href) * un;  // E + p = E' + p' + gamma p_ref/(gamma-1)
+  } else {
+    p = pm;
+    F[4] = (U[4] + pm) * un;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ R logmean(R a, R b) {
   // (a - b) / ln(a/b); Ismail-Roe series where the ratio is close to 1
-  const double z = a / b;
-  const double f = (z - 1.0) / (z + 1.0);
-  const double u = f * f;
-  if (u < 1e-4) return (a + b) / (2.0 * (1.0 + u * (1.0 / 3.0 + u * (0.2 + u * (1.0 / 7.0)))));
+  const R z = a / b;
+  const R f = (z - R(1)) / (z + R(1));
+  const R u = f * f;
+  const R cut = kShift<R> ? R(1e-2) : R(1e-4);
+  if (u < cut) return (a + b) / (R(2) * (R(1) + u * (R(1.0 / 3.0) + u * (R(0.2) + u * R(1.0 / 7.0)))));
   return (a - b) / log(z);
 }
 
-// Chandrashekar's entropy-conservative two-point flux through the vector a
-__device__ __forceinline__ void ec_flux(double rL, double uL, double vL, double wL, double pL, double rR, double uR,
-                                        double vR, double wR, double pR, const double a[3], double gam, double F[5]) {
-  const double bL = 0.5 * rL / pL, bR = 0.5 * rR / pR;
-  const double rln = logmean(rL, rR), bln = logmean(bL, bR);
-  const double um = 0.5 * (uL + uR), vm = 0.5 * (vL + vR), wm = 0.5 * (wL + wR);
-  const double phat = 0.5 * (rL + rR) / (bL + bR);
-  const double q2 = 0.5 * (uL * uL + vL * vL + wL * wL + uR * uR + vR * vR + wR * wR);
-  const double V = um * a[0] + vm * a[1] + wm * a[2];
+// Chandrashekar's entropy-conservative two-point flux through the vector a (true pressures)
+template <typename R>
+__device__ __forceinline__ void ec_flux(R rL, R uL, R vL, R wL, R pL, R rR, R uR, R vR, R wR, R pR, const R a[3], R gam,
+                                        R pref, R F[5]) {
+  const R bL = R(0.5) * rL / pL, bR = R(0.5) * rR / pR;
+  const R rln = logmean(rL, rR), bln = logmean(bL, bR);
+  const R um = R(0.5) * (uL + uR), vm = R(0.5) * (vL + vR), wm = R(0.5) * (wL + wR);
+  const R phat = R(0.5) * (rL + rR) / (bL + bR) - pref;
+  const R q2 = R(0.5) * (uL * uL + vL * vL + wL * wL + uR * uR + vR * vR + wR * wR);
+  const R V = um * a[0] + vm * a[1] + wm * a[2];
   F[0] = rln * V;
   F[1] = F[0] * um + phat * a[0];
   F[2] = F[0] * vm + phat * a[1];
   F[3] = F[0] * wm + phat * a[2];
-  F[4] = F[0] * (0.5 / ((gam - 1.0) * bln) - 0.5 * q2) + um * F[1] + vm * F[2] + wm * F[3];
+  // energy: uses the true p-hat
+  F[4] = F[0] * (R(0.5) / ((gam - R(1)) * bln) - R(0.5) * q2) + um * F[1] + vm * F[2] + wm * F[3] +
+         pref * (um * a[0] + vm * a[1] + wm * a[2]);
 }
 
 // Riemann flux F*(UL, UR, nv) for a unit normal nv
-__device__ __forceinline__ void riemann(int sf, const double UL[5], const double UR[5], const double nv[3], double gam,
-                                        double F[5]) {
+template <typename R>
+__device__ __forceinline__ void riemann(int sf, const R UL[5], const R UR[5], const R nv[3], R gam, R pref, R href,
+                                        R F[5]) {
+  const R gm1 = gam - R(1);
   if (sf == SF_EC) {
-    const double irL = 1.0 / UL[0], irR = 1.0 / UR[0];
-    const double uL = UL[1] * irL, vL = UL[2] * irL, wL = UL[3] * irL;
-    const double uR = UR[1] * irR, vR = UR[2] * irR, wR = UR[3] * irR;
-    const double pL = (gam - 1.0) * (UL[4] - 0.5 * (UL[1] * uL + UL[2] * vL + UL[3] * wL));
-    const double pR = (gam - 1.0) * (UR[4] - 0.5 * (UR[1] * uR + UR[2] * vR + UR[3] * wR));
-    ec_flux(UL[0], uL, vL, wL, pL, UR[0], uR, vR, wR, pR, nv, gam, F);
+    const R irL = R(1) / UL[0], irR = R(1) / UR[0];
+    const R uL = UL[1] * irL, vL = UL[2] * irL, wL = UL[3] * irL;
+    const R uR = UR[1] * irR, vR = UR[2] * irR, wR = UR[3] * irR;
+    const R pL = gm1 * (UL[4] - R(0.5) * (UL[1] * uL + UL[2] * vL + UL[3] * wL)) + (kShift<R> ? pref : R(0));
+    const R pR = gm1 * (UR[4] - R(0.5) * (UR[1] * uR + UR[2] * vR + UR[3] * wR)) + (kShift<R> ? pref : R(0));
+    ec_flux<R>(UL[0], uL, vL, wL, pL, UR[0], uR, vR, wR, pR, nv, gam, kShift<R> ? pref : R(0), F);
     return;
   }
-  double FL[5], FR[5], unL, unR, pL, pR;
-  euler_flux_n(UL, gam, nv, FL, unL, pL);
-  euler_flux_n(UR, gam, nv, FR, unR, pR);
+  R FL[5], FR[5], unL, unR, pL, pR;
+  euler_flux_n<R>(UL, gam, pref, href, nv, FL, unL, pL);
+  euler_flux_n<R>(UR, gam, pref, href, nv, FR, unR, pR);
   if (sf == SF_LLF) {
-    const double cL = sqrt(gam * pL / UL[0]), cR = sqrt(gam * pR / UR[0]);
-    const double lam = fmax(fabs(unL) + cL, fabs(unR) + cR);
+    const R cL = sqrt(gam * pL / UL[0]), cR = sqrt(gam * pR / UR[0]);
+    const R lam = fmax(fabs(unL) + cL, fabs(unR) + cR);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) F[v] = 0.5 * (FL[v] + FR[v] - lam * (UR[v] - UL[v]));
+    for (int v = 0; v < 5; ++v) F[v] = R(0.5) * (FL[v] + FR[v] - lam * (UR[v] - UL[v]));
     return;
   }
   // Roe: sqrt(rho)-weighted average state, three wave families, no entropy fix
-  const double sL = sqrt(UL[0]), sR = sqrt(UR[0]);
-  const double iw = 1.0 / (sL + sR);
-  const double irL = 1.0 / UL[0], irR = 1.0 / UR[0];
-  const double uL = UL[1] * irL, vL = UL[2] * irL, wL = UL[3] * irL;
-  const double uR = UR[1] * irR, vR = UR[2] * irR, wR = UR[3] * irR;
-  const double ut = (sL * uL + sR * uR) * iw, vt = (sL * vL + sR * vR) * iw, wt = (sL * wL + sR * wR) * iw;
-  const double Ht = (sL * (UL[4] + pL) * irL + sR * (UR[4] + pR) * irR) * iw;
-  const double q2 = ut * ut + vt * vt + wt * wt;
-  const double c2 = (gam - 1.0) * (Ht - 0.5 * q2);
-  const double ct = sqrt(c2), ic2 = 1.0 / c2;
-  const double rt = sL * sR;
-  const double unt = ut * nv[0] + vt * nv[1] + wt * nv[2];
-  const double dr = UR[0] - UL[0], dp = pR - pL;
-  const double du = uR - uL, dv = vR - vL, dw = wR - wL;
-  const double dun = du * nv[0] + dv * nv[1] + dw * nv[2];
-  const double a1 = 0.5 * (dp - rt * ct * dun) * ic2;
-  const double a5 = 0.5 * (dp + rt * ct * dun) * ic2;
-  const double a2 = dr - dp * ic2;
-  const double dut = du - dun * nv[0], dvt = dv - dun * nv[1], dwt = dw - dun * nv[2];
-  const double l1a1 = fabs(unt - ct) * a1, l5a5 = fabs(unt + ct) * a5, l2 = fabs(unt);
-  const double l2a2 = l2 * a2, l2r = l2 * rt;
-  double D[5];
+  const R sL = sqrt(UL[0]), sR = sqrt(UR[0]);
+  const R iw = R(1) / (sL + sR);
+  const R irL = R(1) / UL[0], irR = R(1) / UR[0];
+  const R uL = UL[1] * irL, vL = UL[2] * irL, wL = UL[3] * irL;
+  const R uR = UR[1] * irR, vR = UR[2] * irR, wR = UR[3] * irR;
+  const R ut = (sL * uL + sR * uR) * iw, vt = (sL * vL + sR * vR) * iw, wt = (sL * wL + sR * wR) * iw;
+  const R EpL = kShift<R> ? UL[4] + pL - pref + href : UL[4] + pL;  // E + p
+  const R EpR = kShift<R> ? UR[4] + pR - pref + href : UR[4] + pR;
+  const R Ht = (sL * EpL * irL + sR * EpR * irR) * iw;
+  const R q2 = ut * ut + vt * vt + wt * wt;
+  const R c2 = gm1 * (Ht - R(0.5) * q2);
+  const R ct = sqrt(c2), ic2 = R(1) / c2;
+  const R rt = sL * sR;
+  const R unt = ut * nv[0] + vt * nv[1] + wt * nv[2];
+  const R dr = UR[0] - UL[0], dp = pR - pL;
+  const R du = uR - uL, dv = vR - vL, dw = wR - wL;
+  const R dun = du * nv[0] + dv * nv[1] + dw * nv[2];
+  const R a1 = R(0.5) * (dp - rt * ct * dun) * ic2;
+  const R a5 = R(0.5) * (dp + rt * ct * dun) * ic2;
+  const R a2 = dr - dp * ic2;
+  const R dut = du - dun * nv[0], dvt = dv - dun * nv[1], dwt = dw - dun * nv[2];
+  const R l1a1 = fabs(unt - ct) * a1, l5a5 = fabs(unt + ct) * a5, l2 = fabs(unt);
+  const R l2a2 = l2 * a2, l2r = l2 * rt;
+  R D[5];
   D[0] = l1a1 + l5a5 + l2a2;
   D[1] = l1a1 * (ut - ct * nv[0]) + l5a5 * (ut + ct * nv[0]) + l2a2 * ut + l2r * dut;
   D[2] = l1a1 * (vt - ct * nv[1]) + l5a5 * (vt + ct * nv[1]) + l2a2 * vt + l2r * dvt;
   D[3] = l1a1 * (wt - ct * nv[2]) + l5a5 * (wt + ct * nv[2]) + l2a2 * wt + l2r * dwt;
-  D[4] = l1a1 * (Ht - unt * ct) + l5a5 * (Ht + unt * ct) + l2a2 * 0.5 * q2 + l2r * (ut * dut + vt * dvt + wt * dwt);
+  D[4] = l1a1 * (Ht - unt * ct) + l5a5 * (Ht + unt * ct) + l2a2 * R(0.5) * q2 + l2r * (ut * dut + vt * dvt + wt * dwt);
 #pragma unroll
-  for (int v = 0; v < 5; ++v) F[v] = 0.5 * (FL[v] + FR[v] - D[v]);
+  for (int v = 0; v < 5; ++v) F[v] = R(0.5) * (FL[v] + FR[v] - D[v]);
 }
 
 // ---------------------------------------------------------------------------------------------
-// init: curl-form metrics, Jacobian, face normals
+// init: curl-form metrics, Jacobian, face normals (FP64), FP32 copies
 // ---------------------------------------------------------------------------------------------
 
 __device__ __forceinline__ double dsweep(const double *f, int node, int d) {
@@ -262,10 +342,20 @@ __global__ void __launch_bounds__(256) k_face_normals(const DgDevice d) {
   o[3 * nn] = s;
 }
 
+// FP32 roundings of the FP64 metric terms and face normals (FP32-bulk path)
+__global__ void __launch_bounds__(256) k_round_geometry(const DgDevice d) {
+  const long long nja = (long long)d.nE * 9 * nnn, nnr = (long long)d.nF * 4 * nn;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nja + nnr;
+       t += (long long)gridDim.x * blockDim.x) {
+    if (t < nja) d.Jaf[t] = (float)d.Ja[t];
+    else d.nrm_f[t - nja] = (float)d.nrm[t - nja];
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // face kernel: Riemann flux once per face point, stored outward for both sides
 // ---------------------------------------------------------------------------------------------
-template <int SF>
+template <typename R, int SF>
 __global__ void __launch_bounds__(256) k_face(const DgDevice d, const double *__restrict__ U) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)d.nF * nn) return;
@@ -276,37 +366,38 @@ __global__ void __launch_bounds__(256) k_face(const DgDevice d, const double *__
   orient_map(o, p, q, p2, q2);
   const int nodeL = face_node(fL, p, q), nodeR = face_node(fR, p2, q2);
   const int pqR = p2 + n * q2;
-  double UL[5], UR[5], nv[3];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    UL[v] = U[((size_t)eL * 5 + v) * nnn + nodeL];
-    UR[v] = U[((size_t)eR * 5 + v) * nnn + nodeR];
-  }
-  const double *nr = d.nrm + (size_t)f * 4 * nn + pq;
+  const double eref = d.p_ref / (d.gamma - 1.0);
+  const R pref = (R)d.p_ref, href = (R)(d.p_ref * d.gamma / (d.gamma - 1.0)), gam = (R)d.gamma;
+  R UL[5], UR[5], nv[3];
+  load_state<R>(U, eL, nodeL, eref, UL);
+  load_state<R>(U, eR, nodeR, eref, UR);
+  const R *nr = Buf<R>::nrm(d) + (size_t)f * 4 * nn + pq;
   nv[0] = nr[0];
   nv[1] = nr[nn];
   nv[2] = nr[2 * nn];
-  const double s = nr[3 * nn];
-  double Fs[5];
-  riemann(SF, UL, UR, nv, d.gamma, Fs);
-  double *oL = d.Fsurf + ((size_t)eL * 6 + fL) * 5 * nn;
-  double *oR = d.Fsurf + ((size_t)eR * 6 + fR) * 5 * nn;
+  const R s = nr[3 * nn];
+  R Fs[5];
+  riemann<R>(SF, UL, UR, nv, gam, pref, href, Fs);
+  R *oL = Buf<R>::Fsurf(d) + ((size_t)eL * 6 + fL) * 5 * nn;
+  R *oR = Buf<R>::Fsurf(d) + ((size_t)eR * 6 + fR) * 5 * nn;
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     oL[v * nn + pq] = s * Fs[v];
     oR[v * nn + pqR] = -s * Fs[v];
   }
   if (d.equations == 1) {
-    const double irL = 1.0 / UL[0], irR = 1.0 / UR[0];
-    const double wL[3] = {UL[1] * irL, UL[2] * irL, UL[3] * irL};
-    const double wR[3] = {UR[1] * irR, UR[2] * irR, UR[3] * irR};
-    const double pL = (d.gamma - 1.0) * (UL[4] - 0.5 * (UL[1] * wL[0] + UL[2] * wL[1] + UL[3] * wL[2]));
-    const double pR = (d.gamma - 1.0) * (UR[4] - 0.5 * (UR[1] * wR[0] + UR[2] * wR[1] + UR[3] * wR[2]));
-    const double iR = 1.0 / d.R;
-    const double jump[4] = {0.5 * (wR[0] - wL[0]), 0.5 * (wR[1] - wL[1]), 0.5 * (wR[2] - wL[2]),
-                            0.5 * (pR * irR - pL * irL) * iR};
-    double *jL = d.Wsurf + ((size_t)eL * 6 + fL) * 4 * nn;
-    double *jR = d.Wsurf + ((size_t)eR * 6 + fR) * 4 * nn;
+    const R irL = R(1) / UL[0], irR = R(1) / UR[0];
+    const R wL[3] = {UL[1] * irL, UL[2] * irL, UL[3] * irL};
+    const R wR[3] = {UR[1] * irR, UR[2] * irR, UR[3] * irR};
+    const R gm1 = gam - R(1);
+    R pL = gm1 * (UL[4] - R(0.5) * (UL[1] * wL[0] + UL[2] * wL[1] + UL[3] * wL[2]));
+    R pR = gm1 * (UR[4] - R(0.5) * (UR[1] * wR[0] + UR[2] * wR[1] + UR[3] * wR[2]));
+    if (kShift<R>) { pL += pref; pR += pref; }
+    const R iR = R(1) / (R)d.R;
+    const R jump[4] = {R(0.5) * (wR[0] - wL[0]), R(0.5) * (wR[1] - wL[1]), R(0.5) * (wR[2] - wL[2]),
+                       R(0.5) * (pR * irR - pL * irL) * iR};
+    R *jL = Buf<R>::Wsurf(d) + ((size_t)eL * 6 + fL) * 4 * nn;
+    R *jR = Buf<R>::Wsurf(d) + ((size_t)eR * 6 + fR) * 4 * nn;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       jL[c * nn + pq] = jump[c];
@@ -319,36 +410,42 @@ __global__ void __launch_bounds__(256) k_face(const DgDevice d, const double *__
 // BR1 lifting + viscous flux: grad w = (1/J)[sum_d Ja^d D_d w + sum_faces (1/w_b) s n_out (w* - w)],
 // then Fv^d = sum_c Ja^d_c Fv_c(U, grad w) stored per node (4 components: momentum, energy).
 // ---------------------------------------------------------------------------------------------
+template <typename R>
 __global__ void __launch_bounds__(LIFT_THREADS) k_lift(const DgDevice d, const double *__restrict__ U) {
-  __shared__ double W[LIFT_EPB][4][nnn];
+  __shared__ R W[LIFT_EPB][4][nnn];
   const int e0 = blockIdx.x * LIFT_EPB;
-  const double gm1 = d.gamma - 1.0, iR = 1.0 / d.R;
+  const R gm1 = (R)(d.gamma - 1.0), iR = R(1) / (R)d.R;
+  const double eref = d.p_ref / (d.gamma - 1.0);
+  const R pref = (R)d.p_ref;
+  const R *Jab = Buf<R>::Ja(d);
   for (int t = threadIdx.x; t < LIFT_EPB * nnn; t += blockDim.x) {
     const int le = t / nnn, node = t % nnn, e = e0 + le;
     if (e >= d.nE) continue;
-    const double *Ue = U + (size_t)e * 5 * nnn + node;
-    const double r = Ue[0], ir = 1.0 / r;
-    const double u = Ue[nnn] * ir, v = Ue[2 * nnn] * ir, w = Ue[3 * nnn] * ir;
-    const double p = gm1 * (Ue[4 * nnn] - 0.5 * r * (u * u + v * v + w * w));
+    R Uv[5];
+    load_state<R>(U, e, node, eref, Uv);
+    const R r = Uv[0], ir = R(1) / r;
+    const R u = Uv[1] * ir, v = Uv[2] * ir, w = Uv[3] * ir;
+    R p = gm1 * (Uv[4] - R(0.5) * r * (u * u + v * v + w * w));
+    if (kShift<R>) p += pref;
     W[le][0][node] = u;
     W[le][1][node] = v;
     W[le][2][node] = w;
     W[le][3][node] = p * ir * iR;
   }
   __syncthreads();
-  const double mu = d.mu, kappa = d.kappa;
+  const R mu = (R)d.mu, kappa = (R)d.kappa;
   for (int t = threadIdx.x; t < LIFT_EPB * nnn; t += blockDim.x) {
     const int le = t / nnn, node = t % nnn, e = e0 + le;
     if (e >= d.nE) continue;
     const int ijk[3] = {node % n, (node / n) % n, node / nn};
-    double Ja[3][3];
+    R Ja[3][3];
 #pragma unroll
     for (int dd = 0; dd < 3; ++dd)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) Ja[dd][c] = d.Ja[(((size_t)e * 3 + dd) * 3 + c) * nnn + node];
-    double g[4][3];
+      for (int c = 0; c < 3; ++c) Ja[dd][c] = Jab[(((size_t)e * 3 + dd) * 3 + c) * nnn + node];
+    R g[4][3];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) g[q][0] = g[q][1] = g[q][2] = 0.0;
+    for (int q = 0; q < 4; ++q) g[q][0] = g[q][1] = g[q][2] = R(0);
 #pragma unroll
     for (int dd = 0; dd < 3; ++dd) {
       const int id = ijk[dd];
@@ -356,9 +453,9 @@ __global__ void __launch_bounds__(LIFT_THREADS) k_lift(const DgDevice d, const d
       const int base = node - id * st;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        double s = 0.0;
+        R s = R(0);
 #pragma unroll
-        for (int m = 0; m < n; ++m) s += c_D[id * n + m] * W[le][q][base + m * st];
+        for (int m = 0; m < n; ++m) s += Tab<R>::D(id * n + m) * W[le][q][base + m * st];
         g[q][0] += Ja[dd][0] * s;
         g[q][1] += Ja[dd][1] * s;
         g[q][2] += Ja[dd][2] * s;
@@ -366,33 +463,33 @@ __global__ void __launch_bounds__(LIFT_THREADS) k_lift(const DgDevice d, const d
       // surface terms on the faces of direction dd through this node
       if (id == 0 || id == N) {
         const int f = 2 * dd + (id == N ? 1 : 0);
-        const double sc = (id == N ? 1.0 : -1.0) * c_invw[id];
+        const R sc = (id == N ? R(1) : R(-1)) * Tab<R>::invw(id);
         const int pp = dd == 0 ? ijk[1] : ijk[0];
         const int qq = dd == 2 ? ijk[1] : ijk[2];
-        const double *js = d.Wsurf + ((size_t)e * 6 + f) * 4 * nn + pp + n * qq;
+        const R *js = Buf<R>::Wsurf(d) + ((size_t)e * 6 + f) * 4 * nn + pp + n * qq;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const double jq = sc * js[q * nn];
+          const R jq = sc * js[q * nn];
           g[q][0] += Ja[dd][0] * jq;
           g[q][1] += Ja[dd][1] * jq;
           g[q][2] += Ja[dd][2] * jq;
         }
       }
     }
-    const double iJ = d.invJ[(size_t)e * nnn + node];
+    const R iJ = (R)d.invJ[(size_t)e * nnn + node];
 #pragma unroll
     for (int q = 0; q < 4; ++q) { g[q][0] *= iJ; g[q][1] *= iJ; g[q][2] *= iJ; }
     // Navier-Stokes-Fourier flux in Cartesian direction c: (tau_xc, tau_yc, tau_zc, u.tau_c + kappa dT/dx_c)
-    const double u = W[le][0][node], v = W[le][1][node], w = W[le][2][node];
-    const double div = g[0][0] + g[1][1] + g[2][2];
-    const double t23 = (2.0 / 3.0) * mu * div;
-    const double txx = 2.0 * mu * g[0][0] - t23, tyy = 2.0 * mu * g[1][1] - t23, tzz = 2.0 * mu * g[2][2] - t23;
-    const double txy = mu * (g[0][1] + g[1][0]), txz = mu * (g[0][2] + g[2][0]), tyz = mu * (g[1][2] + g[2][1]);
-    double Fc[3][4];
+    const R u = W[le][0][node], v = W[le][1][node], w = W[le][2][node];
+    const R div = g[0][0] + g[1][1] + g[2][2];
+    const R t23 = R(2.0 / 3.0) * mu * div;
+    const R txx = R(2) * mu * g[0][0] - t23, tyy = R(2) * mu * g[1][1] - t23, tzz = R(2) * mu * g[2][2] - t23;
+    const R txy = mu * (g[0][1] + g[1][0]), txz = mu * (g[0][2] + g[2][0]), tyz = mu * (g[1][2] + g[2][1]);
+    R Fc[3][4];
     Fc[0][0] = txx; Fc[0][1] = txy; Fc[0][2] = txz; Fc[0][3] = u * txx + v * txy + w * txz + kappa * g[3][0];
     Fc[1][0] = txy; Fc[1][1] = tyy; Fc[1][2] = tyz; Fc[1][3] = u * txy + v * tyy + w * tyz + kappa * g[3][1];
     Fc[2][0] = txz; Fc[2][1] = tyz; Fc[2][2] = tzz; Fc[2][3] = u * txz + v * tyz + w * tzz + kappa * g[3][2];
-    double *out = d.Fv + (size_t)e * 12 * nnn + node;
+    R *out = Buf<R>::Fv(d) + (size_t)e * 12 * nnn + node;
 #pragma unroll
     for (int dd = 0; dd < 3; ++dd)
 #pragma unroll
@@ -411,55 +508,56 @@ __global__ void __launch_bounds__(LIFT_THREADS) k_lift(const DgDevice d, const d
 // Node i's sums stay in registers while m runs over i+1..N; node m's share of each pair goes
 // straight to the line's accumulator in shared memory (the line belongs to this thread alone).
 // Ac points at the direction's accumulator [5][PS] of this element, indexed like P.
-template <int VF>
-__device__ __forceinline__ void line_fluxdiff(const double *__restrict__ P, int pb, int ps,
-                                              const double *__restrict__ Jd, int gb, int gs, double gam,
-                                              double *__restrict__ Ac) {
+// Staged slots: 0 rho, 1 u, 2 v, 3 w, 4 4 p' (momentum pressure), 5 X, 6 Y with
+// PIR: X = h; KG: X = e = E/rho, Y = 2p; EC: Y = p; central: X = E + p.
+template <typename R, int VF>
+__device__ __forceinline__ void line_fluxdiff(const R *__restrict__ P, int pb, int ps, const R *__restrict__ Jd,
+                                              int gb, int gs, R gam, R pref, R *__restrict__ Ac) {
 #pragma unroll 1
   for (int i = 0; i < n; ++i) {
     const int ai = pb + i * ps, gi = gb + i * gs;
-    const double ri = P[ai], ui = P[PS + ai], vi = P[2 * PS + ai], wi = P[3 * PS + ai];
-    const double p4i = P[4 * PS + ai], xi_ = P[5 * PS + ai], yi = P[6 * PS + ai];
-    const double jxi = __ldg(Jd + gi), jyi = __ldg(Jd + nnn + gi), jzi = __ldg(Jd + 2 * nnn + gi);
-    double ac[5];
+    const R ri = P[ai], ui = P[PS + ai], vi = P[2 * PS + ai], wi = P[3 * PS + ai];
+    const R p4i = P[4 * PS + ai], xi_ = P[5 * PS + ai], yi = P[6 * PS + ai];
+    const R jxi = __ldg(Jd + gi), jyi = __ldg(Jd + nnn + gi), jzi = __ldg(Jd + 2 * nnn + gi);
+    R ac[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) ac[v] = (i == 0) ? 0.0 : Ac[v * PS + ai];
+    for (int v = 0; v < 5; ++v) ac[v] = (i == 0) ? R(0) : Ac[v * PS + ai];
 #pragma unroll
     for (int m = i + 1; m < n; ++m) {
       const int am = pb + m * ps, gm = gb + m * gs;
-      const double rm = P[am], um = P[PS + am], vm = P[2 * PS + am], wm = P[3 * PS + am];
-      const double p4m = P[4 * PS + am], xm = P[5 * PS + am], ym = P[6 * PS + am];
-      const double jxm = __ldg(Jd + gm), jym = __ldg(Jd + nnn + gm), jzm = __ldg(Jd + 2 * nnn + gm);
-      double F[5], ci[5], cm[5];
+      const R rm = P[am], um = P[PS + am], vm = P[2 * PS + am], wm = P[3 * PS + am];
+      const R p4m = P[4 * PS + am], xm = P[5 * PS + am], ym = P[6 * PS + am];
+      const R jxm = __ldg(Jd + gm), jym = __ldg(Jd + nnn + gm), jzm = __ldg(Jd + 2 * nnn + gm);
+      R F[5], ci[5], cm[5];
       if (VF == VF_PIR || VF == VF_KG) {
-        const double Sjx = jxi + jxm, Sjy = jyi + jym, Sjz = jzi + jzm;
-        const double Su = ui + um, Sv = vi + vm, Sw = wi + wm;
-        const double Vp = Su * Sjx + Sv * Sjy + Sw * Sjz;  // 4 {u}.{Ja}
-        F[0] = (ri + rm) * Vp;                             // 8 F_rho
-        const double Sp = p4i + p4m;                       // 4 (p_i + p_m)
-        F[1] = F[0] * Su + Sp * Sjx;                       // 16 F_rho u
+        const R Sjx = jxi + jxm, Sjy = jyi + jym, Sjz = jzi + jzm;
+        const R Su = ui + um, Sv = vi + vm, Sw = wi + wm;
+        const R Vp = Su * Sjx + Sv * Sjy + Sw * Sjz;  // 4 {u}.{Ja}
+        F[0] = (ri + rm) * Vp;                        // 8 F_rho
+        const R Sp = p4i + p4m;                       // 4 (p'_i + p'_m)
+        F[1] = F[0] * Su + Sp * Sjx;                  // 16 F_rho u
         F[2] = F[0] * Sv + Sp * Sjy;
         F[3] = F[0] * Sw + Sp * Sjz;
-        if (VF == VF_PIR) F[4] = F[0] * (xi_ + xm);               // 16 {rho}V{h}
-        else F[4] = F[0] * (xi_ + xm) + (yi + ym) * Vp;           // 16 ({rho}V{e} + {p}V)
-        ci[0] = c_Dq[i * n + m]; cm[0] = c_Dq[m * n + i];
+        if (VF == VF_PIR) F[4] = F[0] * (xi_ + xm);            // 16 {rho}V{h}
+        else F[4] = F[0] * (xi_ + xm) + (yi + ym) * Vp;        // 16 ({rho}V{e} + {p}V)
+        ci[0] = Tab<R>::Dq(i * n + m); cm[0] = Tab<R>::Dq(m * n + i);
 #pragma unroll
-        for (int v = 1; v < 5; ++v) { ci[v] = c_De[i * n + m]; cm[v] = c_De[m * n + i]; }
+        for (int v = 1; v < 5; ++v) { ci[v] = Tab<R>::De(i * n + m); cm[v] = Tab<R>::De(m * n + i); }
       } else {
-        const double a[3] = {0.5 * (jxi + jxm), 0.5 * (jyi + jym), 0.5 * (jzi + jzm)};
+        const R a[3] = {R(0.5) * (jxi + jxm), R(0.5) * (jyi + jym), R(0.5) * (jzi + jzm)};
         if (VF == VF_EC) {
-          ec_flux(ri, ui, vi, wi, 0.25 * p4i, rm, um, vm, wm, 0.25 * p4m, a, gam, F);
+          ec_flux<R>(ri, ui, vi, wi, yi, rm, um, vm, wm, ym, a, gam, kShift<R> ? pref : R(0), F);
         } else {  // central: mean of the two Euler fluxes through {Ja}; slot 5 = E + p
-          const double Vi = ui * a[0] + vi * a[1] + wi * a[2], Vm = um * a[0] + vm * a[1] + wm * a[2];
-          const double pm2 = 0.125 * (p4i + p4m);
-          F[0] = 0.5 * (ri * Vi + rm * Vm);
-          F[1] = 0.5 * (ri * ui * Vi + rm * um * Vm) + pm2 * a[0];
-          F[2] = 0.5 * (ri * vi * Vi + rm * vm * Vm) + pm2 * a[1];
-          F[3] = 0.5 * (ri * wi * Vi + rm * wm * Vm) + pm2 * a[2];
-          F[4] = 0.5 * (xi_ * Vi + xm * Vm);
+          const R Vi = ui * a[0] + vi * a[1] + wi * a[2], Vm = um * a[0] + vm * a[1] + wm * a[2];
+          const R pm2 = R(0.125) * (p4i + p4m);
+          F[0] = R(0.5) * (ri * Vi + rm * Vm);
+          F[1] = R(0.5) * (ri * ui * Vi + rm * um * Vm) + pm2 * a[0];
+          F[2] = R(0.5) * (ri * vi * Vi + rm * vm * Vm) + pm2 * a[1];
+          F[3] = R(0.5) * (ri * wi * Vi + rm * wm * Vm) + pm2 * a[2];
+          F[4] = R(0.5) * (xi_ * Vi + xm * Vm);
         }
 #pragma unroll
-        for (int v = 0; v < 5; ++v) { ci[v] = c_D2[i * n + m]; cm[v] = c_D2[m * n + i]; }
+        for (int v = 0; v < 5; ++v) { ci[v] = Tab<R>::D2(i * n + m); cm[v] = Tab<R>::D2(m * n + i); }
       }
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
@@ -473,83 +571,89 @@ __device__ __forceinline__ void line_fluxdiff(const double *__restrict__ P, int 
   }
 }
 
-// primitive state (rho, u, v, w, p) of staged node a
-__device__ __forceinline__ void staged_prim(const double *__restrict__ P, int a, double q[5]) {
-  q[0] = P[a]; q[1] = P[PS + a]; q[2] = P[2 * PS + a]; q[3] = P[3 * PS + a]; q[4] = 0.25 * P[4 * PS + a];
+// (rho, u, v, w, p') of staged node a for the FV operator (slot 7 holds p')
+template <typename R>
+__device__ __forceinline__ void staged_prim(const R *__restrict__ P, int a, R q[5]) {
+  q[0] = P[a]; q[1] = P[PS + a]; q[2] = P[2 * PS + a]; q[3] = P[3 * PS + a]; q[4] = P[7 * PS + a];
 }
 
 // reconstructed left/right interface states of subcell i (minmod slopes in primitive variables;
 // first order in the outer subcells and wherever the reconstruction loses positivity)
-__device__ __forceinline__ void subcell_states(const double *__restrict__ P, int pb, int ps, int i, double qL[5],
-                                               double qR[5]) {
-  double q[5];
-  staged_prim(P, pb + i * ps, q);
-  double sg[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+template <typename R>
+__device__ __forceinline__ void subcell_states(const R *__restrict__ P, int pb, int ps, int i, R pref, R qL[5],
+                                               R qR[5]) {
+  R q[5];
+  staged_prim<R>(P, pb + i * ps, q);
+  R sg[5] = {R(0), R(0), R(0), R(0), R(0)};
   if (i > 0 && i < N) {
-    double qb[5], qf[5];
-    staged_prim(P, pb + (i - 1) * ps, qb);
-    staged_prim(P, pb + (i + 1) * ps, qf);
-    const double hb = 1.0 / (c_xi[i] - c_xi[i - 1]), hf = 1.0 / (c_xi[i + 1] - c_xi[i]);
+    R qb[5], qf[5];
+    staged_prim<R>(P, pb + (i - 1) * ps, qb);
+    staged_prim<R>(P, pb + (i + 1) * ps, qf);
+    const R hb = R(1) / (Tab<R>::xi(i) - Tab<R>::xi(i - 1)), hf = R(1) / (Tab<R>::xi(i + 1) - Tab<R>::xi(i));
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      const double sb = (q[v] - qb[v]) * hb, sf_ = (qf[v] - q[v]) * hf;
-      sg[v] = (sb * sf_ <= 0.0) ? 0.0 : (fabs(sb) < fabs(sf_) ? sb : sf_);
+      const R sb = (q[v] - qb[v]) * hb, sf_ = (qf[v] - q[v]) * hf;
+      sg[v] = (sb * sf_ <= R(0)) ? R(0) : (fabs(sb) < fabs(sf_) ? sb : sf_);
     }
   }
-  const double dl = c_xh[i] - c_xi[i], dr = c_xh[i + 1] - c_xi[i];
+  const R dl = Tab<R>::xh(i) - Tab<R>::xi(i), dr = Tab<R>::xh(i + 1) - Tab<R>::xi(i);
 #pragma unroll
   for (int v = 0; v < 5; ++v) { qL[v] = q[v] + sg[v] * dl; qR[v] = q[v] + sg[v] * dr; }
-  if (qL[0] <= 0.0 || qL[4] <= 0.0 || qR[0] <= 0.0 || qR[4] <= 0.0) {
+  const R pad = kShift<R> ? pref : R(0);
+  if (qL[0] <= R(0) || qL[4] + pad <= R(0) || qR[0] <= R(0) || qR[4] + pad <= R(0)) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) { qL[v] = q[v]; qR[v] = q[v]; }
   }
 }
 
-__device__ __forceinline__ void cons_of(const double q[5], double gm1, double U[5]) {
+// conservative state from (rho, u, v, w, p') in the kernel's representation (E' in FP32)
+template <typename R>
+__device__ __forceinline__ void cons_of(const R q[5], R gm1, R U[5]) {
   U[0] = q[0]; U[1] = q[0] * q[1]; U[2] = q[0] * q[2]; U[3] = q[0] * q[3];
-  U[4] = q[4] / gm1 + 0.5 * q[0] * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  U[4] = q[4] / gm1 + R(0.5) * q[0] * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
 }
 
 // FV subcell operator along one line (Sec. 4.1): Riemann fluxes at the N interior subcell
 // interfaces with telescoped interface metrics a_{i+1/2} = a_{i-1/2} + w_i (D Ja)_i, the DG surface
 // fluxes at the element faces, and Ac_i = (f_{i+1/2} - f_{i-1/2}) / w_i written to shared memory.
-__device__ __forceinline__ void line_fv(const double *__restrict__ P, int pb, int ps, const double *__restrict__ Jd,
-                                        int gb, int gs, const double *Fm, const double *Fp, int sf, double gam,
-                                        double *__restrict__ Ac) {
-  const double gm1 = gam - 1.0;
-  double fl[5];  // flux at the left interface of the current subcell, +xi direction
+template <typename R>
+__device__ __forceinline__ void line_fv(const R *__restrict__ P, int pb, int ps, const R *__restrict__ Jd, int gb,
+                                        int gs, const R *Fm, const R *Fp, int sf, R gam, R pref, R href,
+                                        R *__restrict__ Ac) {
+  const R gm1 = gam - R(1);
+  R fl[5];  // flux at the left interface of the current subcell, +xi direction
 #pragma unroll
   for (int v = 0; v < 5; ++v) fl[v] = -Fm[v * nn];
-  double a[3] = {__ldg(Jd + gb), __ldg(Jd + nnn + gb), __ldg(Jd + 2 * nnn + gb)};
-  double qLn[5], qRn[5];
-  subcell_states(P, pb, ps, 0, qLn, qRn);
+  R a[3] = {__ldg(Jd + gb), __ldg(Jd + nnn + gb), __ldg(Jd + 2 * nnn + gb)};
+  R qLn[5], qRn[5];
+  subcell_states<R>(P, pb, ps, 0, pref, qLn, qRn);
 #pragma unroll 1
   for (int i = 0; i < n; ++i) {
-    double fr[5];
-    const double qRi[5] = {qRn[0], qRn[1], qRn[2], qRn[3], qRn[4]};
+    R fr[5];
+    const R qRi[5] = {qRn[0], qRn[1], qRn[2], qRn[3], qRn[4]};
     if (i < N) {
-      subcell_states(P, pb, ps, i + 1, qLn, qRn);
+      subcell_states<R>(P, pb, ps, i + 1, pref, qLn, qRn);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        double dj = 0.0;
+        R dj = R(0);
 #pragma unroll
-        for (int m = 0; m < n; ++m) dj += c_D[i * n + m] * __ldg(Jd + c * nnn + gb + m * gs);
-        a[c] += c_w[i] * dj;
+        for (int m = 0; m < n; ++m) dj += Tab<R>::D(i * n + m) * __ldg(Jd + c * nnn + gb + m * gs);
+        a[c] += Tab<R>::w(i) * dj;
       }
-      const double s = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-      const double is = 1.0 / s;
-      const double nv[3] = {a[0] * is, a[1] * is, a[2] * is};
-      double UL[5], UR[5], Fs[5];
-      cons_of(qRi, gm1, UL);
-      cons_of(qLn, gm1, UR);
-      riemann(sf, UL, UR, nv, gam, Fs);
+      const R s = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+      const R is = R(1) / s;
+      const R nv[3] = {a[0] * is, a[1] * is, a[2] * is};
+      R UL[5], UR[5], Fs[5];
+      cons_of<R>(qRi, gm1, UL);
+      cons_of<R>(qLn, gm1, UR);
+      riemann<R>(sf, UL, UR, nv, gam, pref, href, Fs);
 #pragma unroll
       for (int v = 0; v < 5; ++v) fr[v] = s * Fs[v];
     } else {
 #pragma unroll
       for (int v = 0; v < 5; ++v) fr[v] = Fp[v * nn];
     }
-    const double iw = c_invw[i];
+    const R iw = Tab<R>::invw(i);
 #pragma unroll
     for (int v = 0; v < 5; ++v) { Ac[v * PS + pb + i * ps] = (fr[v] - fl[v]) * iw; fl[v] = fr[v]; }
   }
@@ -564,32 +668,41 @@ __device__ __forceinline__ void line_geom(int dir, int line, int &pb, int &ps, i
   else { pb = a + (n + 1) * b; ps = (n + 1) * n; gb = a + n * b; gs = nn; }
 }
 
-template <int VF, bool SC>
+template <typename R, int VF, bool SC>
 __global__ void __launch_bounds__(VOL_THREADS, 2) k_volume(const DgDevice d, const double *U, double *out,
                                                         double *__restrict__ g, int mode, int first, double dt,
                                                         double A, double B) {
-  extern __shared__ double sm[];
-  double *P = sm;                              // [EPB][NP][PS]
-  double *Acc = P + VOL_EPB * NP * PS;         // [EPB][3][5][PS]
-  double *AccT = Acc + VOL_EPB * 15 * PS;      // [EPB][5][nnn] (SC only)
+  constexpr int NP = vol_np<SC>();
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  R *P = reinterpret_cast<R *>(sm_raw);  // [EPB][NP][PS]
+  R *Acc = P + VOL_EPB * NP * PS;         // [EPB][3][5][PS]
+  R *AccT = Acc + VOL_EPB * 15 * PS;      // [EPB][5][nnn] (SC only)
   const int e0 = blockIdx.x * VOL_EPB;
-  const double gam = d.gamma, gm1 = gam - 1.0;
+  const R gam = (R)d.gamma, gm1 = gam - R(1);
+  const R pref = (R)d.p_ref, href = (R)(d.p_ref * d.gamma / (d.gamma - 1.0));
+  const double eref = d.p_ref / (d.gamma - 1.0);
+  const R *Jab = Buf<R>::Ja(d);
   const int vf = VF;
   // phase A: stage primitive quantities
   for (int t = threadIdx.x; t < VOL_EPB * nnn; t += blockDim.x) {
     const int le = t / nnn, node = t % nnn, e = e0 + le;
     if (e >= d.nE) continue;
-    const double *Ue = U + (size_t)e * 5 * nnn + node;
-    const double r = Ue[0], m1 = Ue[nnn], m2 = Ue[2 * nnn], m3 = Ue[3 * nnn], E = Ue[4 * nnn];
-    const double ir = 1.0 / r;
-    const double u = m1 * ir, v = m2 * ir, w = m3 * ir;
-    const double p = gm1 * (E - 0.5 * (m1 * u + m2 * v + m3 * w));
-    if (!(r > 0.0) || !(p > 0.0) || !isfinite(E)) flag_set(d.flag, 1);
-    double *Pe = P + le * NP * PS + pidx(node);
-    Pe[0] = r; Pe[PS] = u; Pe[2 * PS] = v; Pe[3 * PS] = w; Pe[4 * PS] = 4.0 * p;
-    if (vf == VF_PIR) Pe[5 * PS] = (E + p) * ir;
-    else if (vf == VF_KG) { Pe[5 * PS] = E * ir; Pe[6 * PS] = 2.0 * p; }
-    else if (vf == VF_CEN) Pe[5 * PS] = E + p;
+    R Uv[5];
+    load_state<R>(U, e, node, eref, Uv);
+    const R r = Uv[0], m1 = Uv[1], m2 = Uv[2], m3 = Uv[3], E = Uv[4];
+    const R ir = R(1) / r;
+    const R u = m1 * ir, v = m2 * ir, w = m3 * ir;
+    const R pm = gm1 * (E - R(0.5) * (m1 * u + m2 * v + m3 * w));  // p' (= p in FP64)
+    const R p = kShift<R> ? pm + pref : pm;
+    const R Et = kShift<R> ? E + (R)eref : E;
+    if (!(r > R(0)) || !(p > R(0)) || !isfinite(E)) flag_set(d.flag, 1);
+    R *Pe = P + le * NP * PS + pidx(node);
+    Pe[0] = r; Pe[PS] = u; Pe[2 * PS] = v; Pe[3 * PS] = w; Pe[4 * PS] = R(4) * pm;
+    if (vf == VF_PIR) Pe[5 * PS] = (Et + p) * ir;
+    else if (vf == VF_KG) { Pe[5 * PS] = Et * ir; Pe[6 * PS] = R(2) * p; }
+    else if (vf == VF_EC) Pe[6 * PS] = p;
+    else Pe[5 * PS] = Et + p;
+    if (SC) Pe[7 * PS] = pm;
   }
   __syncthreads();
   // phase B: flux differencing, one thread per line, the three line families at once
@@ -598,10 +711,11 @@ __global__ void __launch_bounds__(VOL_THREADS, 2) k_volume(const DgDevice d, con
     if (e >= d.nE) continue;
     int pb, ps, gb, gs, a, b;
     line_geom(dir, line, pb, ps, gb, gs, a, b);
-    line_fluxdiff<VF>(P + le * NP * PS, pb, ps, d.Ja + ((size_t)e * 3 + dir) * 3 * nnn, gb, gs, gam,
-                      Acc + (le * 3 + dir) * 5 * PS);
+    line_fluxdiff<R, VF>(P + le * NP * PS, pb, ps, Jab + ((size_t)e * 3 + dir) * 3 * nnn, gb, gs, gam, pref,
+                         Acc + (le * 3 + dir) * 5 * PS);
   }
   __syncthreads();
+  const R *Fsb = Buf<R>::Fsurf(d);
   if (SC) {
     // DG total (volume + surface) per node into AccT, then the FV operator into Acc
     for (int t = threadIdx.x; t < VOL_EPB * nnn; t += blockDim.x) {
@@ -609,7 +723,7 @@ __global__ void __launch_bounds__(VOL_THREADS, 2) k_volume(const DgDevice d, con
       if (e >= d.nE) continue;
       const int ijk[3] = {node % n, (node / n) % n, node / nn};
       const int pn = pidx(node);
-      double s[5];
+      R s[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v)
         s[v] = Acc[(le * 3 + 0) * 5 * PS + v * PS + pn] + Acc[(le * 3 + 1) * 5 * PS + v * PS + pn] +
@@ -620,9 +734,9 @@ __global__ void __launch_bounds__(VOL_THREADS, 2) k_volume(const DgDevice d, con
         if (id != 0 && id != N) continue;
         const int f = 2 * dd + (id == N ? 1 : 0);
         const int pp = dd == 0 ? ijk[1] : ijk[0], qq = dd == 2 ? ijk[1] : ijk[2];
-        const double *fs = d.Fsurf + ((size_t)e * 6 + f) * 5 * nn + pp + n * qq;
+        const R *fs = Fsb + ((size_t)e * 6 + f) * 5 * nn + pp + n * qq;
 #pragma unroll
-        for (int v = 0; v < 5; ++v) s[v] += c_invw[id] * fs[v * nn];
+        for (int v = 0; v < 5; ++v) s[v] += Tab<R>::invw(id) * fs[v * nn];
       }
 #pragma unroll
       for (int v = 0; v < 5; ++v) AccT[(le * 5 + v) * nnn + node] = s[v];
@@ -634,31 +748,32 @@ __global__ void __launch_bounds__(VOL_THREADS, 2) k_volume(const DgDevice d, con
       if (!(d.alpha[e] > 0.0)) continue;
       int pb, ps, gb, gs, a, b;
       line_geom(dir, line, pb, ps, gb, gs, a, b);
-      const double *Fm = d.Fsurf + ((size_t)e * 6 + 2 * dir) * 5 * nn + a + n * b;
-      const double *Fp = d.Fsurf + ((size_t)e * 6 + 2 * dir + 1) * 5 * nn + a + n * b;
-      line_fv(P + le * NP * PS, pb, ps, d.Ja + ((size_t)e * 3 + dir) * 3 * nnn, gb, gs, Fm, Fp, d.sflux, gam,
-              Acc + (le * 3 + dir) * 5 * PS);
+      const R *Fm = Fsb + ((size_t)e * 6 + 2 * dir) * 5 * nn + a + n * b;
+      const R *Fp = Fsb + ((size_t)e * 6 + 2 * dir + 1) * 5 * nn + a + n * b;
+      line_fv<R>(P + le * NP * PS, pb, ps, Jab + ((size_t)e * 3 + dir) * 3 * nnn, gb, gs, Fm, Fp, d.sflux, gam, pref,
+                 href, Acc + (le * 3 + dir) * 5 * PS);
     }
     __syncthreads();
   }
   // phase C: per node -- surface terms, viscous divergence, blend, Jacobian, output / LSERK
   const bool ns = d.equations == 1;
+  const R *Fvb = Buf<R>::Fv(d);
   for (int t = threadIdx.x; t < VOL_EPB * nnn; t += blockDim.x) {
     const int le = t / nnn, node = t % nnn, e = e0 + le;
     if (e >= d.nE) continue;
     const int ijk[3] = {node % n, (node / n) % n, node / nn};
     const int pn = pidx(node);
-    double s[5];
+    R s[5];
     if (SC) {
-      const double al = d.alpha[e];
+      const R al = (R)d.alpha[e];
 #pragma unroll
       for (int v = 0; v < 5; ++v) s[v] = AccT[(le * 5 + v) * nnn + node];
-      if (al > 0.0) {
+      if (al > R(0)) {
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          const double fv = Acc[(le * 3 + 0) * 5 * PS + v * PS + pn] + Acc[(le * 3 + 1) * 5 * PS + v * PS + pn] +
-                            Acc[(le * 3 + 2) * 5 * PS + v * PS + pn];
-          s[v] = al * fv + (1.0 - al) * s[v];
+          const R fv = Acc[(le * 3 + 0) * 5 * PS + v * PS + pn] + Acc[(le * 3 + 1) * 5 * PS + v * PS + pn] +
+                       Acc[(le * 3 + 2) * 5 * PS + v * PS + pn];
+          s[v] = al * fv + (R(1) - al) * s[v];
         }
       }
     } else {
@@ -672,14 +787,14 @@ __global__ void __launch_bounds__(VOL_THREADS, 2) k_volume(const DgDevice d, con
         if (id != 0 && id != N) continue;
         const int f = 2 * dd + (id == N ? 1 : 0);
         const int pp = dd == 0 ? ijk[1] : ijk[0], qq = dd == 2 ? ijk[1] : ijk[2];
-        const double *fs = d.Fsurf + ((size_t)e * 6 + f) * 5 * nn + pp + n * qq;
+        const R *fs = Fsb + ((size_t)e * 6 + f) * 5 * nn + pp + n * qq;
 #pragma unroll
-        for (int v = 0; v < 5; ++v) s[v] += c_invw[id] * fs[v * nn];
+        for (int v = 0; v < 5; ++v) s[v] += Tab<R>::invw(id) * fs[v * nn];
       }
     }
     if (ns) {
-      const double *Fve = d.Fv + (size_t)e * 12 * nnn;
-      double vis[4] = {0.0, 0.0, 0.0, 0.0};
+      const R *Fve = Fvb + (size_t)e * 12 * nnn;
+      R vis[4] = {R(0), R(0), R(0), R(0)};
 #pragma unroll
       for (int dd = 0; dd < 3; ++dd) {
         const int id = ijk[dd];
@@ -687,10 +802,10 @@ __global__ void __launch_bounds__(VOL_THREADS, 2) k_volume(const DgDevice d, con
         const int base = node - id * st;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          double acc = 0.0;
+          R acc = R(0);
 #pragma unroll
           for (int m = 0; m < n; ++m)
-            if (m != id) acc += c_D[id * n + m] * Fve[(dd * 4 + q) * nnn + base + m * st];
+            if (m != id) acc += Tab<R>::D(id * n + m) * Fve[(dd * 4 + q) * nnn + base + m * st];
           vis[q] += acc;
         }
         if (id == 0 || id == N) {  // -(1/(2 w_b)) phi_nb, phi_nb = neighbour's outward normal viscous flux
@@ -701,10 +816,10 @@ __global__ void __launch_bounds__(VOL_THREADS, 2) k_volume(const DgDevice d, con
           int p2, q2;
           orient_map(o, pp, qq, p2, q2);
           const int nbnode = face_node(fnb, p2, q2);
-          const double sg = (fnb & 1) ? 0.5 : -0.5;
-          const double *Fvn = d.Fv + ((size_t)nb * 12 + (fnb >> 1) * 4) * nnn + nbnode;
+          const R sg = (fnb & 1) ? R(0.5) : R(-0.5);
+          const R *Fvn = Fvb + ((size_t)nb * 12 + (fnb >> 1) * 4) * nnn + nbnode;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) vis[q] -= c_invw[id] * sg * Fvn[q * nnn];
+          for (int q = 0; q < 4; ++q) vis[q] -= Tab<R>::invw(id) * sg * Fvn[q * nnn];
         }
       }
 #pragma unroll
@@ -714,11 +829,11 @@ __global__ void __launch_bounds__(VOL_THREADS, 2) k_volume(const DgDevice d, con
     const size_t gi = (size_t)e * 5 * nnn + node;
     if (mode == 0) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) out[gi + v * nnn] = miJ * s[v];
+      for (int v = 0; v < 5; ++v) out[gi + v * nnn] = miJ * (double)s[v];
     } else {
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const double ut = miJ * s[v];
+        const double ut = miJ * (double)s[v];
         const double gv = first ? dt * ut : A * g[gi + v * nnn] + dt * ut;
         g[gi + v * nnn] = gv;
         out[gi + v * nnn] = U[gi + v * nnn] + B * gv;
@@ -728,7 +843,7 @@ __global__ void __launch_bounds__(VOL_THREADS, 2) k_volume(const DgDevice d, con
 }
 
 // ---------------------------------------------------------------------------------------------
-// modified Persson indicator (Sec. 4.1, Eq. (7)) and the neighbour extension
+// modified Persson indicator (Sec. 4.1, Eq. (7)) and the neighbour extension (FP64)
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_indicator(const DgDevice d, const double *__restrict__ U) {
   __shared__ double q[nnn], t1[nnn];
@@ -806,7 +921,7 @@ __global__ void __launch_bounds__(256) k_spread(const DgDevice d, double *alpha_
 }
 
 // ---------------------------------------------------------------------------------------------
-// reductions: integral invariants and the time-step estimate (deterministic two-pass)
+// reductions: integral invariants and the time-step estimate (deterministic two-pass, FP64)
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_invariants(const DgDevice d, const double *__restrict__ U,
                                                     const double *__restrict__ Ut) {
@@ -895,13 +1010,20 @@ __global__ void __launch_bounds__(256) k_max_dt(const DgDevice d, const double *
 cudaError_t upload(const DgTables &t) {
   if (t.N != N) return cudaErrorInvalidValue;
   double D2[nn], Dq[nn], De[nn];
+  float fD[nn], fD2[nn], fDq[nn], fDe[nn], fw[n], finvw[n], fxi[n], fxh[n + 1];
   for (int i = 0; i < n; ++i)
     for (int m = 0; m < n; ++m) {
       const double v = (i == m) ? 0.0 : t.D[i * n + m];
       D2[i * n + m] = 2.0 * v;
       Dq[i * n + m] = 0.25 * v;
       De[i * n + m] = 0.125 * v;
+      fD[i * n + m] = (float)t.D[i * n + m];
+      fD2[i * n + m] = (float)D2[i * n + m];
+      fDq[i * n + m] = (float)Dq[i * n + m];
+      fDe[i * n + m] = (float)De[i * n + m];
     }
+  for (int i = 0; i < n; ++i) { fw[i] = (float)t.w[i]; finvw[i] = (float)t.invw[i]; fxi[i] = (float)t.xi[i]; }
+  for (int i = 0; i <= n; ++i) fxh[i] = (float)t.xh[i];
   cudaError_t err = cudaSuccess;
   err = err ? err : cudaMemcpyToSymbol(c_D, t.D, sizeof(double) * nn);
   err = err ? err : cudaMemcpyToSymbol(c_D2, D2, sizeof(double) * nn);
@@ -912,6 +1034,14 @@ cudaError_t upload(const DgTables &t) {
   err = err ? err : cudaMemcpyToSymbol(c_xi, t.xi, sizeof(double) * n);
   err = err ? err : cudaMemcpyToSymbol(c_xh, t.xh, sizeof(double) * (n + 1));
   err = err ? err : cudaMemcpyToSymbol(c_Vinv, t.Vinv, sizeof(double) * nn);
+  err = err ? err : cudaMemcpyToSymbol(f_D, fD, sizeof(float) * nn);
+  err = err ? err : cudaMemcpyToSymbol(f_D2, fD2, sizeof(float) * nn);
+  err = err ? err : cudaMemcpyToSymbol(f_Dq, fDq, sizeof(float) * nn);
+  err = err ? err : cudaMemcpyToSymbol(f_De, fDe, sizeof(float) * nn);
+  err = err ? err : cudaMemcpyToSymbol(f_w, fw, sizeof(float) * n);
+  err = err ? err : cudaMemcpyToSymbol(f_invw, finvw, sizeof(float) * n);
+  err = err ? err : cudaMemcpyToSymbol(f_xi, fxi, sizeof(float) * n);
+  err = err ? err : cudaMemcpyToSymbol(f_xh, fxh, sizeof(float) * (n + 1));
   return err;
 }
 
@@ -924,55 +1054,72 @@ void launch_metrics(const DgDevice &d, cudaStream_t s) {
 void launch_face_normals(const DgDevice &d, cudaStream_t s) {
   const long long pts = (long long)d.nF * nn;
   k_face_normals<<<(unsigned)((pts + 255) / 256), 256, 0, s>>>(d);
+  if (d.precision == 1) k_round_geometry<<<4 * 152, 256, 0, s>>>(d);
 }
 
-void launch_face(const DgDevice &d, const double *U, cudaStream_t s) {
+template <typename R>
+void launch_face_t(const DgDevice &d, const double *U, cudaStream_t s) {
   const long long pts = (long long)d.nF * nn;
   const unsigned grid = (unsigned)((pts + 255) / 256);
   switch (d.sflux) {
-    case SF_LLF: k_face<SF_LLF><<<grid, 256, 0, s>>>(d, U); break;
-    case SF_ROE: k_face<SF_ROE><<<grid, 256, 0, s>>>(d, U); break;
-    default: k_face<SF_EC><<<grid, 256, 0, s>>>(d, U); break;
+    case SF_LLF: k_face<R, SF_LLF><<<grid, 256, 0, s>>>(d, U); break;
+    case SF_ROE: k_face<R, SF_ROE><<<grid, 256, 0, s>>>(d, U); break;
+    default: k_face<R, SF_EC><<<grid, 256, 0, s>>>(d, U); break;
   }
+}
+
+void launch_face(const DgDevice &d, const double *U, cudaStream_t s) {
+  if (d.precision == 1) launch_face_t<float>(d, U, s);
+  else launch_face_t<double>(d, U, s);
 }
 
 void launch_lift(const DgDevice &d, const double *U, cudaStream_t s) {
-  k_lift<<<(d.nE + LIFT_EPB - 1) / LIFT_EPB, LIFT_THREADS, 0, s>>>(d, U);
+  const unsigned grid = (d.nE + LIFT_EPB - 1) / LIFT_EPB;
+  if (d.precision == 1) k_lift<float><<<grid, LIFT_THREADS, 0, s>>>(d, U);
+  else k_lift<double><<<grid, LIFT_THREADS, 0, s>>>(d, U);
 }
 
-template <int VF, bool SC>
+template <typename R, int VF, bool SC>
 void launch_volume_t(const DgDevice &d, const double *U, double *out, double *g, int mode, int first, double dt,
                      double A, double B, cudaStream_t s) {
-  const size_t smem = sizeof(double) * (VOL_EPB * NP * PS + VOL_EPB * 15 * PS + (SC ? VOL_EPB * 5 * nnn : 0));
+  const size_t smem =
+      sizeof(R) * (VOL_EPB * vol_np<SC>() * PS + VOL_EPB * 15 * PS + (SC ? VOL_EPB * 5 * nnn : 0));
   static bool attr_set = false;  // per instantiation; setting it twice is harmless
   if (!attr_set) {
-    cudaFuncSetAttribute(k_volume<VF, SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_volume<R, VF, SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_set = true;
   }
-  k_volume<VF, SC><<<(d.nE + VOL_EPB - 1) / VOL_EPB, VOL_THREADS, smem, s>>>(d, U, out, g, mode, first, dt, A, B);
+  k_volume<R, VF, SC><<<(d.nE + VOL_EPB - 1) / VOL_EPB, VOL_THREADS, smem, s>>>(d, U, out, g, mode, first, dt, A, B);
+}
+
+template <typename R>
+void launch_volume_r(const DgDevice &d, const double *U, double *out, double *g, int mode, int first, double dt,
+                     double A, double B, cudaStream_t s) {
+  const bool sc = d.shock_capturing != 0;
+  switch (d.vflux) {
+    case VF_KG:
+      if (sc) launch_volume_t<R, VF_KG, true>(d, U, out, g, mode, first, dt, A, B, s);
+      else launch_volume_t<R, VF_KG, false>(d, U, out, g, mode, first, dt, A, B, s);
+      break;
+    case VF_PIR:
+      if (sc) launch_volume_t<R, VF_PIR, true>(d, U, out, g, mode, first, dt, A, B, s);
+      else launch_volume_t<R, VF_PIR, false>(d, U, out, g, mode, first, dt, A, B, s);
+      break;
+    case VF_EC:
+      if (sc) launch_volume_t<R, VF_EC, true>(d, U, out, g, mode, first, dt, A, B, s);
+      else launch_volume_t<R, VF_EC, false>(d, U, out, g, mode, first, dt, A, B, s);
+      break;
+    default:
+      if (sc) launch_volume_t<R, VF_CEN, true>(d, U, out, g, mode, first, dt, A, B, s);
+      else launch_volume_t<R, VF_CEN, false>(d, U, out, g, mode, first, dt, A, B, s);
+      break;
+  }
 }
 
 void launch_volume(const DgDevice &d, const double *U, double *out, double *g, int mode, int first, double dt,
                    double A, double B, cudaStream_t s) {
-  const bool sc = d.shock_capturing != 0;
-  switch (d.vflux) {
-    case VF_KG:
-      if (sc) launch_volume_t<VF_KG, true>(d, U, out, g, mode, first, dt, A, B, s);
-      else launch_volume_t<VF_KG, false>(d, U, out, g, mode, first, dt, A, B, s);
-      break;
-    case VF_PIR:
-      if (sc) launch_volume_t<VF_PIR, true>(d, U, out, g, mode, first, dt, A, B, s);
-      else launch_volume_t<VF_PIR, false>(d, U, out, g, mode, first, dt, A, B, s);
-      break;
-    case VF_EC:
-      if (sc) launch_volume_t<VF_EC, true>(d, U, out, g, mode, first, dt, A, B, s);
-      else launch_volume_t<VF_EC, false>(d, U, out, g, mode, first, dt, A, B, s);
-      break;
-    default:
-      if (sc) launch_volume_t<VF_CEN, true>(d, U, out, g, mode, first, dt, A, B, s);
-      else launch_volume_t<VF_CEN, false>(d, U, out, g, mode, first, dt, A, B, s);
-      break;
-  }
+  if (d.precision == 1) launch_volume_r<float>(d, U, out, g, mode, first, dt, A, B, s);
+  else launch_volume_r<double>(d, U, out, g, mode, first, dt, A, B, s);
 }
 
 void launch_indicator(const DgDevice &d, const double *U, cudaStream_t s) { k_indicator<<<d.nE, 128, 0, s>>>(d, U); }

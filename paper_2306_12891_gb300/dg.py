@@ -42,7 +42,7 @@ class _Params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("gamma", ctypes.c_double), ("R", ctypes.c_double),
                 ("mu", ctypes.c_double), ("Pr", ctypes.c_double), ("shock_capturing", ctypes.c_int),
                 ("alpha_min", ctypes.c_double), ("alpha_max", ctypes.c_double), ("sharpness", ctypes.c_double),
-                ("alpha_fixed", ctypes.c_double)]
+                ("alpha_fixed", ctypes.c_double), ("p_ref", ctypes.c_double)]
 
 
 _lib = None
@@ -123,7 +123,7 @@ class DG:
 
     def __init__(self, N, xyz, faces, equations="euler", vflux="kg", sflux="llf", precision="fp64", gamma=1.4,
                  R=1.0, mu=0.0, Pr=0.72, shock_capturing=False, alpha_min=0.01, alpha_max=0.7,
-                 sharpness=DEFAULT_SHARPNESS, alpha_fixed=-1.0, stream=None):
+                 sharpness=DEFAULT_SHARPNESS, alpha_fixed=-1.0, p_ref=0.0, stream=None):
         import torch
 
         self.torch = torch
@@ -135,7 +135,7 @@ class DG:
         self.numel = int(np.prod(self.shape))
         mesh = _Mesh(self.nE, self.N, xyz.ctypes.data, faces.shape[0], faces.ctypes.data)
         prm = _Params(EQUATIONS[equations], VFLUX[vflux], SFLUX[sflux], PRECISION[precision], gamma, R, mu, Pr,
-                      int(bool(shock_capturing)), alpha_min, alpha_max, sharpness, float(alpha_fixed))
+                      int(bool(shock_capturing)), alpha_min, alpha_max, sharpness, float(alpha_fixed), float(p_ref))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         ctx = ctypes.c_void_p(None)
         st = lib().dg_init(ctypes.byref(mesh), self.N, 0, ctypes.byref(prm), ctypes.c_void_p(self.stream.cuda_stream),
