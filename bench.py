@@ -59,6 +59,30 @@ def volume_kernel_flops_per_element(N: int, navier_stokes: bool) -> float:
     return 45.0 * pairs + per_node * n ** 3 + per_face_pt * 6 * n * n
 
 
+def volume_kernel_bytes_per_element(N: int, navier_stokes: bool, real_bytes: int) -> float:
+    """Algorithmic DRAM bytes of one volume-kernel launch per element in an LSERK stage after the
+    first: U and the LSERK register g read and written (FP64), the metric terms Ja (real type),
+    1/J (FP64), the element's six face slots of outward flux (real type) and, for Navier-Stokes,
+    the contravariant viscous flux (12 per node) plus the neighbours' face traces (4 per face point)."""
+    n = N + 1
+    nodes, fpts = n ** 3, 6 * n * n
+    b = nodes * (4 * 5 * 8 + 8) + nodes * 9 * real_bytes + fpts * 5 * real_bytes
+    if navier_stokes:
+        b += nodes * 12 * real_bytes + fpts * 4 * real_bytes
+    return float(b)
+
+
+def _measured_hbm_gbs() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0  # the profiling recipe's fallback
+
+
+HBM_GBS = _measured_hbm_gbs()
+
+
 def dist_setup(n_gpus: int):
     import torch
 
@@ -202,13 +226,16 @@ def run_gpu(args):
     if rank == 0 or not os.path.exists(dg.LIB_PATH):
         build.build()
     barrier(world)
-    w = WORKLOADS[WORKLOAD]
+    w = WORKLOADS[args.workload]
     if args.nel:  # a smaller mesh of the same workload (profiling runs)
         w = w.with_(nel=(args.nel,) * 3)
+    fp32_main = args.precision == "fp32_bulk"
     xyz, faces = w.mesh()
     U0 = w.initial_state(xyz)
     stream = torch.cuda.current_stream()
-    solver = dg.DG(w.N, xyz, faces, stream=stream, **w.physics())
+    p_ref = P0_TGV if w.initial == "tgv" else 0.0
+    prec = dict(precision="fp32_bulk", p_ref=p_ref) if fp32_main else {}
+    solver = dg.DG(w.N, xyz, faces, stream=stream, **prec, **w.physics())
     U = torch.from_numpy(U0).cuda()
     dt = solver.max_dt(U, w.cfl)
     peak_fp64 = dg.probe_fma("fp64", stream)
@@ -251,21 +278,25 @@ def run_gpu(args):
 
     # the FP32-bulk form on the same workload: throughput and its error against the FP64 state
     fp32 = None
-    if args.fp32:
+    if args.fp32 and not fp32_main:
         U64 = U.clone()  # FP64 state after warmup + steps (the e2e steps ran on a host copy)
         n_done = args.warmup + args.steps
         del solver
-        s32 = dg.DG(w.N, xyz, faces, stream=stream, precision="fp32_bulk", p_ref=P0_TGV, **w.physics())
+        s32 = dg.DG(w.N, xyz, faces, stream=stream, precision="fp32_bulk", p_ref=p_ref, **w.physics())
         V = torch.from_numpy(U0).cuda()
         s32.lserk_steps(V, dt, args.warmup)
         torch.cuda.synchronize()
         barrier(world)
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s32.timing_enable(True)
+        s32.timing_get()
         f0.record(stream)
         s32.lserk_steps(V, dt, args.steps)
         f1.record(stream)
         torch.cuda.synchronize()
         ms32 = max_over_ranks(world, f0.elapsed_time(f1))
+        kt32 = s32.timing_get()
+        s32.timing_enable(False)
         s32.lserk_steps(V, dt, n_done - args.warmup - args.steps)
         s32.check()
         d = (V - U64).abs().amax(dim=(0, 2, 3, 4))
@@ -277,15 +308,29 @@ def run_gpu(args):
                 "steps_compared": n_done,
                 "linf_err_rel_to_state": (d / scale).tolist(),
                 "linf_err_rel_to_change": (d / change).tolist(),
-                "p_ref": P0_TGV}
+                "p_ref": p_ref,
+                "kernels": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in kt32.items() if v[1]}}
         del s32
 
     dofs = w.dofs
     total_updates = world * dofs * STAGES * args.steps
     value = total_updates / (ms * 1e-3)
     vol_ms, vol_n = ktimes.get("volume", (0.0, 0))
-    flops_launch = volume_kernel_flops_per_element(w.N, True) * w.n_elems
-    achieved = flops_launch / (vol_ms / vol_n * 1e-3) if vol_n else None
+    vol_s = vol_ms / vol_n * 1e-3 if vol_n else None
+    if fp32_main:  # HBM-bound: algorithmic bytes of the volume kernel against the measured copy bandwidth
+        bytes_launch = volume_kernel_bytes_per_element(w.N, True, 4) * w.n_elems
+        roofline = {"bound": "hbm", "kernel": "volume (FP32-bulk)", "achieved": bytes_launch / vol_s / 1e9,
+                    "peak": HBM_GBS, "unit": "GB/s", "frac": bytes_launch / vol_s / 1e9 / HBM_GBS,
+                    "traffic": None, "bytes_per_launch": bytes_launch,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
+    else:
+        flops_launch = volume_kernel_flops_per_element(w.N, True) * w.n_elems
+        achieved = flops_launch / vol_s
+        roofline = {"bound": "alu", "kernel": "volume (split-form flux differencing, FP64 pipe)",
+                    "achieved": achieved / 1e12, "peak": peak_fp64 / 1e12, "unit": "TFLOP/s",
+                    "frac": achieved / peak_fp64,
+                    "traffic": (VOLUME_DRAM_BYTES_PER_ELEMENT * w.n_elems if VOLUME_DRAM_BYTES_PER_ELEMENT else None),
+                    "flops_per_launch": flops_launch, "peak_source": "measured FP64 FMA probe (dg_probe_fma), live"}
     state_bytes = U.numel() * 8
     if rank != 0:
         return
@@ -294,20 +339,15 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if not args.nel else f"{WORKLOAD} reduced to {args.nel}^3",
+        "vs_baseline": None, "dtype": "f32+f64" if fp32_main else "f64", "data": "synthetic",
+        "config": {"workload": args.workload if not args.nel else f"{args.workload} reduced to {args.nel}^3",
                    "N": w.N, "elements": w.n_elems, "dofs": dofs,
                    "physics": "Navier-Stokes, Pirozzoli split form, Roe, BR1, curved mesh, TGV Re 1600 Ma 0.1",
-                   "precision": "fp64", "dt": dt, "cfl": w.cfl,
+                   "precision": args.precision, "dt": dt, "cfl": w.cfl,
                    "l2": f"inputs larger than L2 (state {state_bytes / 1e6:.0f} MB, working set > 5 GB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "pid_s_per_dof_stage": 1.0 / (value / world),
-        "roofline": {"bound": "alu", "kernel": "volume (split-form flux differencing, FP64 pipe)",
-                     "achieved": achieved / 1e12 if achieved else None, "peak": peak_fp64 / 1e12,
-                     "unit": "TFLOP/s", "frac": (achieved / peak_fp64) if achieved else None,
-                     "traffic": (VOLUME_DRAM_BYTES_PER_ELEMENT * w.n_elems
-                                 if VOLUME_DRAM_BYTES_PER_ELEMENT else None),
-                     "flops_per_launch": flops_launch, "peak_source": "measured FP64 FMA probe (dg_probe_fma), live"},
+        "roofline": roofline,
         "kernels": breakdown,
         "gpu_launches": launches,
         "clocks": clk,
@@ -329,6 +369,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-fp32", dest="fp32", action="store_false", help="skip the FP32-bulk comparison")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk"])
     ap.add_argument("--nel", type=int, default=None, help="elements per direction (default: the workload's 32)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -257,6 +257,8 @@ dg_status dg_init(const dg_mesh *mesh, int N, int nodes, const dg_params *prm, v
   if (fp32) {  // FP32-bulk: FP32 copies of the geometry and FP32 work buffers
     DG_ALLOC(d.Jaf, (size_t)nE * 9 * nnn);
     DG_ALLOC(d.nrm_f, (size_t)nF * 4 * nn);
+    DG_ALLOC(d.invJf, (size_t)nE * nnn);
+    DG_ALLOC(d.Uf, (size_t)nE * 5 * nnn);
     DG_ALLOC(d.Fsurf_f, (size_t)nE * 6 * 5 * nn);
     if (prm->equations == DG_NAVIER_STOKES) {
       DG_ALLOC(d.Wsurf_f, (size_t)nE * 6 * 4 * nn);
@@ -307,23 +309,37 @@ dg_status dg_init(const dg_mesh *mesh, int N, int nodes, const dg_params *prm, v
   return DG_OK;
 }
 
+namespace {
+// FP32-bulk: refresh the FP32 shadow of a caller state (the volume kernel keeps it current afterwards)
+dg_status refresh_shadow(dg_ctx *c, const double *U) {
+  if (c->d.precision != DG_FP32_BULK) return DG_OK;
+  return launch(c, KC_OTHER, [&] { c->K->shadow(c->d, U, c->stream); });
+}
+dg_status steps_impl(dg_ctx *c, double *U, double dt, int n_steps) {
+  DG_TRY(refresh_shadow(c, U));
+  for (int k = 0; k < n_steps; ++k)
+    for (int st = 0; st < 5; ++st) DG_TRY(stage(c, U, U, 1, st, dt));
+  return DG_OK;
+}
+}  // namespace
+
 dg_status dg_rhs(dg_ctx *c, const double *U, double *Ut, double t) {
   (void)t;
   if (!c || !U || !Ut || U == Ut) return fail(c, DG_ERR_ARG, "dg_rhs: null or aliased arrays");
+  DG_TRY(refresh_shadow(c, U));
   return stage(c, U, Ut, 0, 0, 0.0);
 }
 
 dg_status dg_lserk_step(dg_ctx *c, double *U, double dt, double t) {
   (void)t;
   if (!c || !U || !std::isfinite(dt)) return fail(c, DG_ERR_ARG, "dg_lserk_step: bad argument");
-  for (int st = 0; st < 5; ++st) DG_TRY(stage(c, U, U, 1, st, dt));
-  return DG_OK;
+  return steps_impl(c, U, dt, 1);
 }
 
 dg_status dg_lserk_steps(dg_ctx *c, double *U, double dt, double t, int n_steps) {
-  if (!c || !U || n_steps < 0) return fail(c, DG_ERR_ARG, "dg_lserk_steps: bad argument");
-  for (int k = 0; k < n_steps; ++k) DG_TRY(dg_lserk_step(c, U, dt, t + k * dt));
-  return DG_OK;
+  (void)t;
+  if (!c || !U || n_steps < 0 || !std::isfinite(dt)) return fail(c, DG_ERR_ARG, "dg_lserk_steps: bad argument");
+  return steps_impl(c, U, dt, n_steps);
 }
 
 dg_status dg_lserk_step_host(dg_ctx *c, double *U_host, double dt, double t) {

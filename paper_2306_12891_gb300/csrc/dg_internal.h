@@ -39,6 +39,8 @@ struct DgDevice {
   double *Wsurf;       // [nE][6][4][n^2] BR1 lifting jump (w* - w_own), own order
   double *Fv;          // [nE][3 d][4][n^3] contravariant viscous flux (momentum x,y,z, energy)
   float *Fsurf_f, *Wsurf_f, *Fv_f;  // FP32-bulk versions
+  float *Uf;           // FP32-bulk: FP32 shadow of the state [nE][5][n^3], E shifted by p_ref/(gamma-1)
+  float *invJf;        // FP32-bulk: FP32 copy of 1/J for the lifting
   double *alpha_raw;   // [nE]
   double *alpha;       // [nE]
   double *red;         // reduction partials
@@ -61,6 +63,7 @@ struct DgKernelTable {
   void (*spread)(const DgDevice &d, double *alpha_out, cudaStream_t s);
   void (*invariants)(const DgDevice &d, const double *U, const double *Ut, double *out8_dev, cudaStream_t s);
   void (*max_dt)(const DgDevice &d, const double *U, double *out_dev, cudaStream_t s);
+  void (*shadow)(const DgDevice &d, const double *U, cudaStream_t s);  // FP32 shadow of U (FP32-bulk)
 };
 
 extern const DgKernelTable dg_kernels_n1, dg_kernels_n2, dg_kernels_n3, dg_kernels_n4, dg_kernels_n5,

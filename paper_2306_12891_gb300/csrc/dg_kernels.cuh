@@ -138,13 +138,30 @@ __device__ __forceinline__ void orient_map(int o, int p, int q, int &p2, int &q2
 
 __device__ __forceinline__ void flag_set(int *flag, int bit) { atomicOr(flag, bit); }
 
-// five conservative values of node `node` of element e, in the arithmetic type; FP32 carries E'
+// five conservative values of node `node` of element e, in the arithmetic type: the FP64 state,
+// or in FP32 its shadow copy (E' = E - p_ref/(gamma-1) already applied, rounded once)
 template <typename R>
-__device__ __forceinline__ void load_state(const double *__restrict__ U, size_t e, int node, double eref, R out[5]) {
-  const double *Ue = U + e * 5 * nnn + node;
+__device__ __forceinline__ void load_state(const DgDevice &d, const double *__restrict__ U, size_t e, int node,
+                                           R out[5]) {
+  if (kShift<R>) {
+    const float *Ue = d.Uf + e * 5 * nnn + node;
 #pragma unroll
-  for (int v = 0; v < 4; ++v) out[v] = (R)Ue[v * nnn];
-  out[4] = kShift<R> ? (R)(Ue[4 * nnn] - eref) : (R)Ue[4 * nnn];
+    for (int v = 0; v < 5; ++v) out[v] = (R)Ue[v * nnn];
+  } else {
+    const double *Ue = U + e * 5 * nnn + node;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) out[v] = (R)Ue[v * nnn];
+  }
+}
+
+// FP32 shadow of the state: Uf = float(U), with E' = E - p_ref/(gamma-1) formed in FP64 first
+__global__ void __launch_bounds__(256) k_shadow(const DgDevice d, const double *__restrict__ U) {
+  const long long total = (long long)d.nE * 5 * nnn;
+  const double eref = d.p_ref / (d.gamma - 1.0);
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)((t / nnn) % 5);
+    d.Uf[t] = v == 4 ? (float)(U[t] - eref) : (float)U[t];
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -344,11 +361,12 @@ __global__ void __launch_bounds__(256) k_face_normals(const DgDevice d) {
 
 // FP32 roundings of the FP64 metric terms and face normals (FP32-bulk path)
 __global__ void __launch_bounds__(256) k_round_geometry(const DgDevice d) {
-  const long long nja = (long long)d.nE * 9 * nnn, nnr = (long long)d.nF * 4 * nn;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nja + nnr;
+  const long long nja = (long long)d.nE * 9 * nnn, nnr = (long long)d.nF * 4 * nn, nij = (long long)d.nE * nnn;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nja + nnr + nij;
        t += (long long)gridDim.x * blockDim.x) {
     if (t < nja) d.Jaf[t] = (float)d.Ja[t];
-    else d.nrm_f[t - nja] = (float)d.nrm[t - nja];
+    else if (t < nja + nnr) d.nrm_f[t - nja] = (float)d.nrm[t - nja];
+    else d.invJf[t - nja - nnr] = (float)d.invJ[t - nja - nnr];
   }
 }
 
@@ -366,11 +384,10 @@ __global__ void __launch_bounds__(256) k_face(const DgDevice d, const double *__
   orient_map(o, p, q, p2, q2);
   const int nodeL = face_node(fL, p, q), nodeR = face_node(fR, p2, q2);
   const int pqR = p2 + n * q2;
-  const double eref = d.p_ref / (d.gamma - 1.0);
   const R pref = (R)d.p_ref, href = (R)(d.p_ref * d.gamma / (d.gamma - 1.0)), gam = (R)d.gamma;
   R UL[5], UR[5], nv[3];
-  load_state<R>(U, eL, nodeL, eref, UL);
-  load_state<R>(U, eR, nodeR, eref, UR);
+  load_state<R>(d, U, eL, nodeL, UL);
+  load_state<R>(d, U, eR, nodeR, UR);
   const R *nr = Buf<R>::nrm(d) + (size_t)f * 4 * nn + pq;
   nv[0] = nr[0];
   nv[1] = nr[nn];
@@ -413,16 +430,17 @@ __global__ void __launch_bounds__(256) k_face(const DgDevice d, const double *__
 template <typename R>
 __global__ void __launch_bounds__(LIFT_THREADS) k_lift(const DgDevice d, const double *__restrict__ U) {
   __shared__ R W[LIFT_EPB][4][nnn];
+  __shared__ R sD[n][n + 1];  // D, rows padded: lanes read different rows without bank conflicts
+  for (int t = threadIdx.x; t < nn; t += blockDim.x) sD[t / n][t % n] = Tab<R>::D(t);
   const int e0 = blockIdx.x * LIFT_EPB;
   const R gm1 = (R)(d.gamma - 1.0), iR = R(1) / (R)d.R;
-  const double eref = d.p_ref / (d.gamma - 1.0);
   const R pref = (R)d.p_ref;
   const R *Jab = Buf<R>::Ja(d);
   for (int t = threadIdx.x; t < LIFT_EPB * nnn; t += blockDim.x) {
     const int le = t / nnn, node = t % nnn, e = e0 + le;
     if (e >= d.nE) continue;
     R Uv[5];
-    load_state<R>(U, e, node, eref, Uv);
+    load_state<R>(d, U, e, node, Uv);
     const R r = Uv[0], ir = R(1) / r;
     const R u = Uv[1] * ir, v = Uv[2] * ir, w = Uv[3] * ir;
     R p = gm1 * (Uv[4] - R(0.5) * r * (u * u + v * v + w * w));
@@ -455,7 +473,7 @@ __global__ void __launch_bounds__(LIFT_THREADS) k_lift(const DgDevice d, const d
       for (int q = 0; q < 4; ++q) {
         R s = R(0);
 #pragma unroll
-        for (int m = 0; m < n; ++m) s += Tab<R>::D(id * n + m) * W[le][q][base + m * st];
+        for (int m = 0; m < n; ++m) s += sD[id][m] * W[le][q][base + m * st];
         g[q][0] += Ja[dd][0] * s;
         g[q][1] += Ja[dd][1] * s;
         g[q][2] += Ja[dd][2] * s;
@@ -476,7 +494,7 @@ __global__ void __launch_bounds__(LIFT_THREADS) k_lift(const DgDevice d, const d
         }
       }
     }
-    const R iJ = (R)d.invJ[(size_t)e * nnn + node];
+    const R iJ = kShift<R> ? (R)d.invJf[(size_t)e * nnn + node] : (R)d.invJ[(size_t)e * nnn + node];
 #pragma unroll
     for (int q = 0; q < 4; ++q) { g[q][0] *= iJ; g[q][1] *= iJ; g[q][2] *= iJ; }
     // Navier-Stokes-Fourier flux in Cartesian direction c: (tau_xc, tau_yc, tau_zc, u.tau_c + kappa dT/dx_c)
@@ -568,6 +586,28 @@ __device__ __forceinline__ void line_fluxdiff(const R *__restrict__ P, int pb, i
     }
 #pragma unroll
     for (int v = 0; v < 5; ++v) Ac[v * PS + ai] = ac[v];
+  }
+}
+
+// Viscous divergence along one line: Ac[1+q]_i -= sum_{m != i} D_im Fv^d_q(m) for the line's n
+// nodes (the diagonal cancels against the surface term, see the file header). Fvd points at the
+// element's contravariant viscous flux of this direction [4][nnn].
+template <typename R>
+__device__ __forceinline__ void line_viscous(const R *__restrict__ Fvd, int gb, int gs, int pb, int ps,
+                                             R *__restrict__ Ac) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    R f[n];
+#pragma unroll
+    for (int m = 0; m < n; ++m) f[m] = __ldg(Fvd + q * nnn + gb + m * gs);
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      R s = R(0);
+#pragma unroll
+      for (int m = 0; m < n; ++m)
+        if (m != i) s += Tab<R>::D(i * n + m) * f[m];
+      Ac[(1 + q) * PS + pb + i * ps] -= s;
+    }
   }
 }
 
@@ -669,7 +709,7 @@ __device__ __forceinline__ void line_geom(int dir, int line, int &pb, int &ps, i
 }
 
 template <typename R, int VF, bool SC>
-__global__ void __launch_bounds__(VOL_THREADS, 2) k_volume(const DgDevice d, const double *U, double *out,
+__global__ void __launch_bounds__(VOL_THREADS, kShift<R> ? 3 : 2) k_volume(const DgDevice d, const double *U, double *out,
                                                         double *__restrict__ g, int mode, int first, double dt,
                                                         double A, double B) {
   constexpr int NP = vol_np<SC>();
@@ -688,7 +728,7 @@ __global__ void __launch_bounds__(VOL_THREADS, 2) k_volume(const DgDevice d, con
     const int le = t / nnn, node = t % nnn, e = e0 + le;
     if (e >= d.nE) continue;
     R Uv[5];
-    load_state<R>(U, e, node, eref, Uv);
+    load_state<R>(d, U, e, node, Uv);
     const R r = Uv[0], m1 = Uv[1], m2 = Uv[2], m3 = Uv[3], E = Uv[4];
     const R ir = R(1) / r;
     const R u = m1 * ir, v = m2 * ir, w = m3 * ir;
@@ -713,6 +753,9 @@ __global__ void __launch_bounds__(VOL_THREADS, 2) k_volume(const DgDevice d, con
     line_geom(dir, line, pb, ps, gb, gs, a, b);
     line_fluxdiff<R, VF>(P + le * NP * PS, pb, ps, Jab + ((size_t)e * 3 + dir) * 3 * nnn, gb, gs, gam, pref,
                          Acc + (le * 3 + dir) * 5 * PS);
+    // viscous divergence joins the line sums, except under the blend (which must not weight it)
+    if (!SC && d.equations == 1)
+      line_viscous<R>(Buf<R>::Fv(d) + ((size_t)e * 12 + dir * 4) * nnn, gb, gs, pb, ps, Acc + (le * 3 + dir) * 5 * PS);
   }
   __syncthreads();
   const R *Fsb = Buf<R>::Fsurf(d);
@@ -798,15 +841,17 @@ __global__ void __launch_bounds__(VOL_THREADS, 2) k_volume(const DgDevice d, con
 #pragma unroll
       for (int dd = 0; dd < 3; ++dd) {
         const int id = ijk[dd];
-        const int st = dd == 0 ? 1 : dd == 1 ? n : nn;
-        const int base = node - id * st;
+        if (SC) {  // (without the blend the line threads of phase B already added this part)
+          const int st = dd == 0 ? 1 : dd == 1 ? n : nn;
+          const int base = node - id * st;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          R acc = R(0);
+          for (int q = 0; q < 4; ++q) {
+            R acc = R(0);
 #pragma unroll
-          for (int m = 0; m < n; ++m)
-            if (m != id) acc += Tab<R>::D(id * n + m) * Fve[(dd * 4 + q) * nnn + base + m * st];
-          vis[q] += acc;
+            for (int m = 0; m < n; ++m)
+              if (m != id) acc += Tab<R>::D(id * n + m) * Fve[(dd * 4 + q) * nnn + base + m * st];
+            vis[q] += acc;
+          }
         }
         if (id == 0 || id == N) {  // -(1/(2 w_b)) phi_nb, phi_nb = neighbour's outward normal viscous flux
           const int f = 2 * dd + (id == N ? 1 : 0);
@@ -836,7 +881,9 @@ __global__ void __launch_bounds__(VOL_THREADS, 2) k_volume(const DgDevice d, con
         const double ut = miJ * (double)s[v];
         const double gv = first ? dt * ut : A * g[gi + v * nnn] + dt * ut;
         g[gi + v * nnn] = gv;
-        out[gi + v * nnn] = U[gi + v * nnn] + B * gv;
+        const double un = U[gi + v * nnn] + B * gv;
+        out[gi + v * nnn] = un;
+        if (kShift<R>) d.Uf[gi + v * nnn] = v == 4 ? (float)(un - eref) : (float)un;
       }
     }
   }
@@ -1124,6 +1171,8 @@ void launch_volume(const DgDevice &d, const double *U, double *out, double *g, i
 
 void launch_indicator(const DgDevice &d, const double *U, cudaStream_t s) { k_indicator<<<d.nE, 128, 0, s>>>(d, U); }
 
+void launch_shadow(const DgDevice &d, const double *U, cudaStream_t s) { k_shadow<<<8 * 152, 256, 0, s>>>(d, U); }
+
 void launch_spread(const DgDevice &d, double *alpha_out, cudaStream_t s) {
   k_spread<<<(d.nE + 255) / 256, 256, 0, s>>>(d, alpha_out);
 }
@@ -1150,4 +1199,4 @@ void launch_max_dt(const DgDevice &d, const double *U, double *out, cudaStream_t
 #define DG_CAT(a, b) DG_CAT2(a, b)
 const DgKernelTable DG_CAT(dg_kernels_n, DG_N) = {
     N,           upload,           launch_metrics, launch_face_normals, launch_face,  launch_lift,
-    launch_volume, launch_indicator, launch_spread,  launch_invariants,   launch_max_dt};
+    launch_volume, launch_indicator, launch_spread,  launch_invariants,   launch_max_dt, launch_shadow};
