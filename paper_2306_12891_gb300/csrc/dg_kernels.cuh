@@ -106,6 +106,11 @@ __host__ __device__ constexpr int vol_epb() {
 }
 constexpr int VOL_EPB = vol_epb();
 constexpr int VOL_THREADS = round32(3 * nn * VOL_EPB);
+template <typename R, bool SC> __host__ __device__ constexpr int vol_threads() { return VOL_THREADS; }
+// minimum resident CTAs per SM the register budget must allow (FP32 uses half the shared memory)
+template <typename R, bool SC> __host__ __device__ constexpr int vol_min_blocks() {
+  return std::is_same<R, float>::value && !SC ? 3 : 2;
+}
 // staged quantities per node: rho, u, v, w, 4 p_m, X, Y (+ p' for the FV operator)
 template <bool SC> __host__ __device__ constexpr int vol_np() { return SC ? 8 : 7; }
 // lifting kernel: whole elements per CTA, a thread per node (looped above 256 threads)
@@ -138,6 +143,9 @@ __device__ __forceinline__ void orient_map(int o, int p, int q, int &p2, int &q2
 
 __device__ __forceinline__ void flag_set(int *flag, int bit) { atomicOr(flag, bit); }
 
+__device__ __forceinline__ double to_double(float f) { return (double)f; }
+__device__ __forceinline__ double to_double(double x) { return x; }
+
 // five conservative values of node `node` of element e, in the arithmetic type: the FP64 state,
 // or in FP32 its shadow copy (E' = E - p_ref/(gamma-1) already applied, rounded once)
 template <typename R>
@@ -160,7 +168,7 @@ __global__ void __launch_bounds__(256) k_shadow(const DgDevice d, const double *
   const double eref = d.p_ref / (d.gamma - 1.0);
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
     const int v = (int)((t / nnn) % 5);
-    d.Uf[t] = v == 4 ? (float)(U[t] - eref) : (float)U[t];
+    d.Uf[t] = (float)(v == 4 ? U[t] - eref : U[t]);
   }
 }
 
@@ -709,7 +717,7 @@ __device__ __forceinline__ void line_geom(int dir, int line, int &pb, int &ps, i
 }
 
 template <typename R, int VF, bool SC>
-__global__ void __launch_bounds__(VOL_THREADS, kShift<R> ? 3 : 2) k_volume(const DgDevice d, const double *U, double *out,
+__global__ void __launch_bounds__(vol_threads<R, SC>(), vol_min_blocks<R, SC>()) k_volume(const DgDevice d, const double *U, double *out,
                                                         double *__restrict__ g, int mode, int first, double dt,
                                                         double A, double B) {
   constexpr int NP = vol_np<SC>();
@@ -874,16 +882,16 @@ __global__ void __launch_bounds__(VOL_THREADS, kShift<R> ? 3 : 2) k_volume(const
     const size_t gi = (size_t)e * 5 * nnn + node;
     if (mode == 0) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) out[gi + v * nnn] = miJ * (double)s[v];
+      for (int v = 0; v < 5; ++v) out[gi + v * nnn] = miJ * to_double(s[v]);
     } else {
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const double ut = miJ * (double)s[v];
+        const double ut = miJ * to_double(s[v]);
         const double gv = first ? dt * ut : A * g[gi + v * nnn] + dt * ut;
         g[gi + v * nnn] = gv;
         const double un = U[gi + v * nnn] + B * gv;
         out[gi + v * nnn] = un;
-        if (kShift<R>) d.Uf[gi + v * nnn] = v == 4 ? (float)(un - eref) : (float)un;
+        if (kShift<R>) d.Uf[gi + v * nnn] = (float)(v == 4 ? un - eref : un);
       }
     }
   }
@@ -1136,7 +1144,8 @@ void launch_volume_t(const DgDevice &d, const double *U, double *out, double *g,
     cudaFuncSetAttribute(k_volume<R, VF, SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_set = true;
   }
-  k_volume<R, VF, SC><<<(d.nE + VOL_EPB - 1) / VOL_EPB, VOL_THREADS, smem, s>>>(d, U, out, g, mode, first, dt, A, B);
+  k_volume<R, VF, SC><<<(d.nE + VOL_EPB - 1) / VOL_EPB, vol_threads<R, SC>(), smem, s>>>(d, U, out, g, mode, first, dt, A,
+                                                                                    B);
 }
 
 template <typename R>

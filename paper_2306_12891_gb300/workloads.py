@@ -85,6 +85,115 @@ def box_mesh(N: int, nel, lo=(0.0, 0.0, 0.0), hi=(TWO_PI, TWO_PI, TWO_PI), mappi
     return xyz, faces
 
 
+# ------------------------------------------------------------------ unstructured relabelling
+
+def _proper_rotations():
+    """The 24 rotations of the reference cube as (perm, signs): new axis a reads old axis perm[a],
+    reversed where signs[a] < 0 (signed permutation matrices with determinant +1)."""
+    import itertools
+
+    out = []
+    for perm in itertools.permutations(range(3)):
+        inv = sum(1 for i in range(3) for j in range(i + 1, 3) if perm[i] > perm[j])
+        for signs in itertools.product((1, -1), repeat=3):
+            if (-1) ** inv * signs[0] * signs[1] * signs[2] == 1:
+                out.append((perm, signs))
+    return out
+
+
+ROTATIONS = _proper_rotations()
+
+
+def relabel_element(N: int, arr: np.ndarray, rot) -> np.ndarray:
+    """Node array [..., n, n, n] (k, j, i) of one element re-indexed by a cube rotation: the new
+    node (i'_0, i'_1, i'_2) is the old node with i_{perm[a]} = i'_a (or N - i'_a where signs[a] < 0)."""
+    perm, signs = rot
+    n = N + 1
+    new = np.empty_like(arr)
+    idx = np.arange(n)
+    for kp in idx:
+        for jp in idx:
+            for ip in idx:
+                new_ijk = (ip, jp, kp)
+                old = [0, 0, 0]
+                for a in range(3):
+                    old[perm[a]] = new_ijk[a] if signs[a] > 0 else N - new_ijk[a]
+                new[..., kp, jp, ip] = arr[..., old[2], old[1], old[0]]
+    return new
+
+
+def _face_points(N, X, f):
+    """Coordinates [n][n][3] of local face f of one element (X [3][n][n][n]), indexed (q, p)."""
+    b = N if f % 2 else 0
+    if f // 2 == 0:
+        pts = X[:, :, :, b]          # [c][k][j] -> (q=k, p=j)
+    elif f // 2 == 1:
+        pts = X[:, :, b, :]          # [c][k][i] -> (q=k, p=i)
+    else:
+        pts = X[:, b, :, :]          # [c][j][i] -> (q=j, p=i)
+    return np.moveaxis(pts, 0, -1)   # [q][p][3]
+
+
+def build_faces(N: int, xyz: np.ndarray, period, tol: float = 1e-9) -> np.ndarray:
+    """Face table of a conforming hexahedral mesh from its node coordinates: faces whose node sets
+    coincide (modulo the periodic lengths `period`) are paired, and the orientation code mapping
+    the first element's face point (p, q) to the second's is found by trying all eight."""
+    from scipy.spatial import cKDTree
+
+    L = np.asarray(period, dtype=float)
+    n = N + 1
+
+    def wrap(P):
+        return np.mod(P, L)
+
+    nE = xyz.shape[0]
+    pts = [_face_points(N, xyz[e], f) for e in range(nE) for f in range(6)]
+    cent = np.array([wrap(P.reshape(-1, 3).mean(0)) for P in pts])
+    cent = np.where(cent >= L * (1 - 1e-12), 0.0, cent)
+    pairs = cKDTree(cent, boxsize=L).query_pairs(r=1e-6 * max(1.0, L.max()), output_type="ndarray")
+    if 2 * len(pairs) != len(pts) or len(np.unique(pairs)) != len(pts):
+        raise ValueError("face centroids do not pair up one to one")
+    table = []
+    for s1, s2 in pairs:
+        P1, P2 = pts[s1], pts[s2]
+        for o in range(8):
+            ok = True
+            for q in range(n):
+                for p in range(n):
+                    a, b = (q, p) if o & 4 else (p, q)
+                    if o & 1:
+                        a = N - a
+                    if o & 2:
+                        b = N - b
+                    d = wrap(P1[q, p] - P2[b, a] + 0.5 * L) - 0.5 * L
+                    if np.abs(d).max() > tol * max(1.0, L.max()):
+                        ok = False
+                        break
+                if not ok:
+                    break
+            if ok:
+                table.append((s1 // 6, s1 % 6, s2 // 6, s2 % 6, o))
+                break
+        else:
+            raise ValueError(f"faces {divmod(s1, 6)} and {divmod(s2, 6)} meet but their nodes do not")
+    return np.asarray(sorted(table), dtype=np.int32)
+
+
+def rotated_box_mesh(N: int, nel, seed: int, lo=(0.0, 0.0, 0.0), hi=(TWO_PI, TWO_PI, TWO_PI), mapping=None,
+                     fraction=0.5):
+    """box_mesh with a seeded random subset of elements re-indexed by random cube rotations and the
+    face table rebuilt from the coordinates (so faces of all eight orientations appear)."""
+    xyz, _ = box_mesh(N, nel, lo, hi, mapping)
+    rng = np.random.default_rng(seed)
+    rots = [None] * xyz.shape[0]
+    for e in range(xyz.shape[0]):
+        if rng.uniform() < fraction:
+            rots[e] = ROTATIONS[rng.integers(1, len(ROTATIONS))]
+            xyz[e] = relabel_element(N, xyz[e], rots[e])
+    faces = build_faces(N, xyz, np.asarray(hi) - np.asarray(lo))
+    return xyz, faces, rots
+
+
 # ------------------------------------------------------------------ initial states
 
 def cons_from_prim(rho, u, v, w, p, gamma=1.4) -> np.ndarray:

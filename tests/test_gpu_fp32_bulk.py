@@ -77,6 +77,18 @@ def test_fp32_rhs_combinations(env, vf, sf, eq, N, nel):
     assert (err <= TOL32).all(), (err, normwise(Ut, Ur))
 
 
+def test_fp32_rotated_elements(env):
+    dg, orc, torch = env
+    N = 5
+    xyz, faces, _ = W.rotated_box_mesh(N, (3, 2, 3), seed=7, mapping=_generic_map)
+    U0 = W.random_smooth_state(xyz, seed=2, amp=0.1)
+    gpu, ref, Ut, Ur = rhs_pair(env, N, xyz, faces, U0, p_ref=1.0 / 1.4, equations="ns", vflux="pirozzoli",
+                                sflux="roe", mu=0.02)
+    err = parity(Ut, Ur, flux_scale(U0, ref.Ja, ref.J, orc.dmatrix(N)))
+    print(f"PARITY32 rotated N={N}: {err}")
+    assert (err <= TOL32).all(), (err, normwise(Ut, Ur))
+
+
 @pytest.mark.parametrize("alpha", [1.0, 0.37])
 def test_fp32_fv_blend(env, alpha):
     dg, orc, torch = env

@@ -100,6 +100,17 @@ def test_rhs_every_degree(env, N):
     check_rhs(env, N, xyz, faces, U0, equations="ns", vflux="pirozzoli", sflux="roe", mu=1.0 / 1600)
 
 
+@pytest.mark.parametrize("N,eq,sc", [(3, "ns", False), (5, "euler", True), (7, "ns", False), (2, "euler", False)])
+def test_rhs_on_mesh_with_rotated_elements(env, N, eq, sc):
+    """Unstructured connectivity: half the elements re-indexed by cube rotations, faces of most of
+    the eight orientation codes, face table rebuilt from the node coordinates."""
+    xyz, faces, _ = W.rotated_box_mesh(N, (3, 2, 3), seed=N, mapping=_generic_map)
+    assert len(set(faces[:, 4])) >= 4
+    U0 = jumpy(W.random_smooth_state(xyz, seed=N, amp=0.1), seed=N + 1)
+    extra = dict(shock_capturing=True, alpha_fixed=0.4) if sc else {}
+    check_rhs(env, N, xyz, faces, U0, equations=eq, vflux="pirozzoli", sflux="roe", mu=0.02, **extra)
+
+
 def test_single_element_periodic_mesh(env):
     N = 4
     xyz, faces = W.box_mesh(N, (1, 1, 1), mapping=_generic_map)

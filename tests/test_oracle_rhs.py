@@ -163,3 +163,28 @@ def test_element_subset_matches_full_rhs(oracle_mod):
         np.testing.assert_array_equal(part[mask], full[mask])
         others = np.setdiff1d(np.arange(o.nE), mask)
         assert not part[others].any()
+
+
+@pytest.mark.parametrize("eq,sc", [("euler", False), ("ns", False), ("euler", True)])
+def test_rhs_invariant_under_element_rotation(oracle_mod, eq, sc):
+    """Re-indexing elements by rotations of the reference cube (face table rebuilt from the
+    coordinates, so faces of most of the eight orientations occur) changes nothing but the node
+    labels: the right-hand side of a rotated element is the rotated right-hand side."""
+    N = 3
+    xyz, faces = W.box_mesh(N, (3, 2, 2), mapping=_generic_map)
+    xr, fr, rots = W.rotated_box_mesh(N, (3, 2, 2), seed=3, mapping=_generic_map)
+    assert len(set(fr[:, 4])) >= 5
+    kw = dict(equations=eq, vflux="pirozzoli", sflux="roe", mu=0.05)
+    if sc:
+        kw.update(shock_capturing=True, alpha_fixed=0.4)
+    field = lambda x: W.random_smooth_state(x, seed=5, amp=0.1)
+    R1 = oracle_mod.Oracle(N, xyz, faces, **kw).rhs(field(xyz))
+    R2 = oracle_mod.Oracle(N, xr, fr, **kw).rhs(field(xr))
+    err = max(np.abs((W.relabel_element(N, R1[e], r) if r else R1[e]) - R2[e]).max() for e, r in enumerate(rots))
+    assert err < 1e-12 * np.abs(R1).max()
+    # a wrong orientation code is detected (the pin can fail)
+    bad = fr.copy()
+    i = int(np.nonzero(bad[:, 4] != 0)[0][0])
+    bad[i, 4] = 0
+    R3 = oracle_mod.Oracle(N, xr, bad, **kw).rhs(field(xr))
+    assert np.abs(R3 - R2).max() > 1e-3 * np.abs(R1).max()
