@@ -5,6 +5,11 @@ computes: the split-form DGSEM right-hand side on curved hexahedra (Sec. 2, Sec.
 its explicit Runge-Kutta step (Sec. 2, Eq. (1)), the modified Persson indicator
 (Sec. 4.1, Eq. (7)) and the DG/FV blend (Sec. 4.1, Eq. (6)).
 
+A second build of the same source (``ORC_COMPLEX_STEP``, ``Oracle(..., complex_step=True)``)
+runs every state-dependent statement in complex arithmetic: ``jvp`` and ``lserk_jvp`` return
+Im L(U + i h V) / h, the exact directional derivative of the oracle's own arithmetic (complex
+step; no subtractive cancellation), which is the reference for the discrete adjoint.
+
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
 may import this package. The CUDA path never does, and this package never imports the
 CUDA path: the two share no code.
@@ -21,6 +26,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "dgsem_oracle.c")
 HDR = os.path.join(HERE, "dgsem_oracle.h")
 LIB_PATH = os.path.join(HERE, "_build", "liboracle.so")
+LIB_CS_PATH = os.path.join(HERE, "_build", "liboracle_cs.so")
+CS_STEP = 1e-30  # complex-step size: h^2 is far below one ulp of any value the oracle forms
 
 EQUATIONS = {"euler": 0, "ns": 1, "navier_stokes": 1}
 VFLUX = {"kg": 0, "pirozzoli": 1, "ec": 2, "central": 3}
@@ -28,18 +35,20 @@ SFLUX = {"llf": 0, "roe": 1, "ec": 2}
 # s = ln((1 - 1e-4) / 1e-4): the sigmoid sharpness of Hennemann et al. (not printed in the paper)
 DEFAULT_SHARPNESS = float(np.log((1.0 - 1e-4) / 1e-4))
 
-_lib = None
+_libs = {}
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with plain -O2 and no FMA contraction (same results on x86 and Arm)."""
+    """Compile the oracle (and its complex-step build) with plain -O2 and no FMA contraction
+    (same results on x86 and Arm)."""
     os.makedirs(os.path.dirname(LIB_PATH), exist_ok=True)
     newest = max(os.path.getmtime(SRC), os.path.getmtime(HDR))
-    if force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < newest:
-        tmp = LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", tmp, SRC, "-lm"])
-        os.replace(tmp, LIB_PATH)
+    for path, defs in ((LIB_PATH, []), (LIB_CS_PATH, ["-DORC_COMPLEX_STEP"])):
+        if force or not os.path.exists(path) or os.path.getmtime(path) < newest:
+            tmp = path + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                                   "-fno-fast-math", *defs, "-o", tmp, SRC, "-lm"])
+            os.replace(tmp, path)
     return LIB_PATH
 
 
@@ -57,11 +66,10 @@ _DP = ctypes.POINTER(ctypes.c_double)
 RHS_FN = ctypes.CFUNCTYPE(None, _DP, _DP, ctypes.c_double, ctypes.c_void_p)
 
 
-def lib():
-    global _lib
-    if _lib is None:
+def lib(complex_step: bool = False):
+    if complex_step not in _libs:
         build()
-        L = ctypes.CDLL(LIB_PATH)
+        L = ctypes.CDLL(LIB_CS_PATH if complex_step else LIB_PATH)
         vp = ctypes.c_void_p
         L.orc_create.restype = vp
         L.orc_create.argtypes = [ctypes.POINTER(_Problem), ctypes.POINTER(ctypes.c_int)]
@@ -88,8 +96,8 @@ def lib():
         L.orc_viscous_flux.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp]
         L.orc_lserk_generic.argtypes = [ctypes.c_int, vp, ctypes.c_double, ctypes.c_double, RHS_FN, vp]
         L.orc_lserk_coefficients.argtypes = [vp, vp, vp]
-        _lib = L
-    return _lib
+        _libs[complex_step] = L
+    return _libs[complex_step]
 
 
 def _p(a: np.ndarray):
@@ -193,7 +201,10 @@ class Oracle:
 
     def __init__(self, N, xyz, faces, equations="euler", vflux="kg", sflux="llf", gamma=1.4, R=1.0,
                  mu=0.0, Pr=0.72, shock_capturing=False, alpha_min=0.01, alpha_max=0.7,
-                 sharpness=DEFAULT_SHARPNESS, alpha_fixed=-1.0):
+                 sharpness=DEFAULT_SHARPNESS, alpha_fixed=-1.0, complex_step=False):
+        self.cs = bool(complex_step)
+        self._L = lib(self.cs)
+        self._dtype = np.complex128 if self.cs else np.float64
         self.N = int(N)
         self.n = self.N + 1
         self.xyz = _f64(xyz)
@@ -214,62 +225,96 @@ class Oracle:
         pb.alpha_fixed = float(alpha_fixed)
         self._pb = pb
         st = ctypes.c_int(0)
-        self._s = lib().orc_create(ctypes.byref(pb), ctypes.byref(st))
+        self._s = self._L.orc_create(ctypes.byref(pb), ctypes.byref(st))
         if not self._s:
             raise ValueError(f"oracle rejected the problem (status {st.value})")
         self.shape = (self.nE, 5, self.n, self.n, self.n)
 
     def __del__(self):
         if getattr(self, "_s", None):
-            lib().orc_destroy(self._s)
+            self._L.orc_destroy(self._s)
             self._s = None
 
     @property
     def Ja(self) -> np.ndarray:
         n = self.n
-        ptr = ctypes.cast(lib().orc_state_Ja(self._s), _DP)
+        ptr = ctypes.cast(self._L.orc_state_Ja(self._s), _DP)
         return np.ctypeslib.as_array(ptr, shape=(self.nE, 3, 3, n, n, n)).copy()
 
     @property
     def J(self) -> np.ndarray:
         n = self.n
-        ptr = ctypes.cast(lib().orc_state_J(self._s), _DP)
+        ptr = ctypes.cast(self._L.orc_state_J(self._s), _DP)
         return np.ctypeslib.as_array(ptr, shape=(self.nE, n, n, n)).copy()
 
     def _U(self, U):
-        U = _f64(U)
+        U = np.ascontiguousarray(U, dtype=self._dtype)
         if U.size != int(np.prod(self.shape)):
             raise ValueError("U has the wrong size")
         return U
 
     def rhs(self, U, mask=None, return_alpha=False):
         U = self._U(U)
-        Ut = np.zeros(self.shape)
-        alpha = np.zeros(self.nE)
+        Ut = np.zeros(self.shape, dtype=self._dtype)
+        alpha = np.zeros(self.nE, dtype=self._dtype)
         m = None
         if mask is not None:
             m = np.zeros(self.nE, dtype=np.uint8)
             m[np.asarray(mask)] = 1
-        lib().orc_rhs(self._s, _p(U), _p(Ut), _p(m) if m is not None else None, _p(alpha))
+        self._L.orc_rhs(self._s, _p(U), _p(Ut), _p(m) if m is not None else None, _p(alpha))
         return (Ut, alpha) if return_alpha else Ut
 
     def indicator(self, U):
         U = self._U(U)
-        raw, a = np.zeros(self.nE), np.zeros(self.nE)
-        lib().orc_indicator(self._s, _p(U), _p(raw), _p(a))
+        raw, a = np.zeros(self.nE, dtype=self._dtype), np.zeros(self.nE, dtype=self._dtype)
+        self._L.orc_indicator(self._s, _p(U), _p(raw), _p(a))
         return raw, a
 
     def lserk_step(self, U, dt, t=0.0):
         U = self._U(U).copy()
-        lib().orc_lserk_step(self._s, _p(U), float(dt), float(t))
+        self._L.orc_lserk_step(self._s, _p(U), float(dt), float(t))
         return U
 
     def invariants(self, U, Ut):
-        out = np.zeros(8)
-        lib().orc_invariants(self._s, _p(self._U(U)), _p(self._U(Ut)), _p(out))
+        out = np.zeros(8, dtype=self._dtype)
+        self._L.orc_invariants(self._s, _p(self._U(U)), _p(self._U(Ut)), _p(out))
         return out
 
     def max_dt(self, U, cfl):
         dt = np.zeros(1)
-        lib().orc_max_dt(self._s, _p(self._U(U)), float(cfl), _p(dt))
+        self._L.orc_max_dt(self._s, _p(self._U(U)), float(cfl), _p(dt))
         return float(dt[0])
+
+    # ------------------------------------------------------------ complex-step derivatives
+
+    def _need_cs(self):
+        if not self.cs:
+            raise ValueError("derivatives need Oracle(..., complex_step=True)")
+
+    def jvp(self, U, V):
+        """(dL/dU)(U) V for the right-hand side L, by complex step."""
+        self._need_cs()
+        Z = np.asarray(U, dtype=np.float64) + 1j * CS_STEP * np.asarray(V, dtype=np.float64)
+        return self.rhs(Z).imag / CS_STEP
+
+    def lserk_jvp(self, U, V, dt, steps=1):
+        """Tangent of `steps` LSERK(5,4) steps: returns (U_K, dU_K/dU_0 V), by complex step."""
+        self._need_cs()
+        Z = np.asarray(U, dtype=np.float64) + 1j * CS_STEP * np.asarray(V, dtype=np.float64)
+        for _ in range(steps):
+            Z = self.lserk_step(Z, dt)
+        return Z.real.copy(), Z.imag / CS_STEP
+
+    def jacobian(self, U):
+        """Dense Jacobian dL/dU [M][M], M = n_elems * 5 * n^3, one complex-step column per unknown
+        (small meshes only)."""
+        self._need_cs()
+        U = np.asarray(U, dtype=np.float64).reshape(-1)
+        M = U.size
+        Jm = np.zeros((M, M))
+        Z = U.astype(np.complex128)
+        for k in range(M):
+            Z[k] += 1j * CS_STEP
+            Jm[:, k] = self.rhs(Z).imag.reshape(-1) / CS_STEP
+            Z[k] = U[k]
+        return Jm

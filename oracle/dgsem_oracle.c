@@ -26,6 +26,26 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Arithmetic on state-dependent quantities. The default build is plain double. The
+ * complex-step build (-DORC_COMPLEX_STEP, see dgsem_oracle.h) runs the same statements on
+ * double _Complex: branches and clips decide on the real part, and |x|, max(a, b) follow the
+ * real part's sign and order, so the imaginary part carries the exact one-sided derivative. */
+#ifdef ORC_COMPLEX_STEP
+#define RE(x) creal(x)
+#define R_SQRT csqrt
+#define R_LOG clog
+#define R_EXP cexp
+static orc_real R_ABS(orc_real x) { return creal(x) < 0.0 ? -x : x; }
+static orc_real R_MAX(orc_real a, orc_real b) { return creal(b) > creal(a) ? b : a; }
+#else
+#define RE(x) (x)
+#define R_SQRT sqrt
+#define R_LOG log
+#define R_EXP exp
+#define R_ABS fabs
+#define R_MAX fmax
+#endif
+
 #define NVAR 5
 #define NMAX 15
 
@@ -244,15 +264,15 @@ int orc_metrics(int N, int n_elems, const double *xyz, double *Ja, double *J) {
 /* 4. Pointwise physics                                                     */
 /* ======================================================================= */
 
-static void primitive(const double U[5], double gamma, double *rho, double u[3], double *p) {
+static void primitive(const orc_real U[5], double gamma, orc_real *rho, orc_real u[3], orc_real *p) {
   *rho = U[0];
   u[0] = U[1] / U[0]; u[1] = U[2] / U[0]; u[2] = U[3] / U[0];
   *p = (gamma - 1.0) * (U[4] - 0.5 * U[0] * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
 }
 
 /* Euler flux in Cartesian direction c */
-static void flux_cart(const double U[5], int c, double gamma, double F[5]) {
-  double rho, u[3], p;
+static void flux_cart(const orc_real U[5], int c, double gamma, orc_real F[5]) {
+  orc_real rho, u[3], p;
   primitive(U, gamma, &rho, u, &p);
   F[0] = rho * u[c];
   F[1] = U[1] * u[c] + (c == 0 ? p : 0.0);
@@ -262,39 +282,39 @@ static void flux_cart(const double U[5], int c, double gamma, double F[5]) {
 }
 
 /* contravariant flux F.a = sum_c a_c F_c(U) */
-void orc_flux_contra(const double U[5], const double a[3], double gamma, double F[5]) {
+void orc_flux_contra(const orc_real U[5], const double a[3], double gamma, orc_real F[5]) {
   for (int v = 0; v < NVAR; ++v) F[v] = 0.0;
   for (int c = 0; c < 3; ++c) {
-    double Fc[5];
+    orc_real Fc[5];
     flux_cart(U, c, gamma, Fc);
     for (int v = 0; v < NVAR; ++v) F[v] += a[c] * Fc[v];
   }
 }
 
 /* logarithmic mean (a-b)/(ln a - ln b), Ismail-Roe series near a = b */
-double orc_logmean(double a, double b) {
-  double zeta = a / b;
-  double f = (zeta - 1.0) / (zeta + 1.0);
-  double u = f * f;
-  if (u < 1e-4) {
-    double F = 1.0 + u / 3.0 + u * u / 5.0 + u * u * u / 7.0;
+orc_real orc_logmean(orc_real a, orc_real b) {
+  orc_real zeta = a / b;
+  orc_real f = (zeta - 1.0) / (zeta + 1.0);
+  orc_real u = f * f;
+  if (RE(u) < 1e-4) {
+    orc_real F = 1.0 + u / 3.0 + u * u / 5.0 + u * u * u / 7.0;
     return (a + b) / (2.0 * F);
   }
-  return (a - b) / log(zeta);
+  return (a - b) / R_LOG(zeta);
 }
 
 /* two-point volume flux with metric average {Ja} (a_avg) */
-void orc_twopoint(int kind, const double UL[5], const double UR[5], const double aL[3],
-                  const double aR[3], double gamma, double F[5]) {
+void orc_twopoint(int kind, const orc_real UL[5], const orc_real UR[5], const double aL[3],
+                  const double aR[3], double gamma, orc_real F[5]) {
   double a[3] = {0.5 * (aL[0] + aR[0]), 0.5 * (aL[1] + aR[1]), 0.5 * (aL[2] + aR[2])};
-  double rL, uL[3], pL, rR, uR[3], pR;
+  orc_real rL, uL[3], pL, rR, uR[3], pR;
   primitive(UL, gamma, &rL, uL, &pL);
   primitive(UR, gamma, &rR, uR, &pR);
-  double rho_m = 0.5 * (rL + rR), p_m = 0.5 * (pL + pR);
-  double u_m[3] = {0.5 * (uL[0] + uR[0]), 0.5 * (uL[1] + uR[1]), 0.5 * (uL[2] + uR[2])};
-  double V = u_m[0] * a[0] + u_m[1] * a[1] + u_m[2] * a[2];
+  orc_real rho_m = 0.5 * (rL + rR), p_m = 0.5 * (pL + pR);
+  orc_real u_m[3] = {0.5 * (uL[0] + uR[0]), 0.5 * (uL[1] + uR[1]), 0.5 * (uL[2] + uR[2])};
+  orc_real V = u_m[0] * a[0] + u_m[1] * a[1] + u_m[2] * a[2];
   if (kind == ORC_VF_CENTRAL) {
-    double FL[5], FR[5];
+    orc_real FL[5], FR[5];
     orc_flux_contra(UL, a, gamma, FL);
     orc_flux_contra(UR, a, gamma, FR);
     for (int v = 0; v < NVAR; ++v) F[v] = 0.5 * (FL[v] + FR[v]);
@@ -304,20 +324,20 @@ void orc_twopoint(int kind, const double UL[5], const double UR[5], const double
     F[0] = rho_m * V;
     for (int c = 0; c < 3; ++c) F[1 + c] = rho_m * V * u_m[c] + p_m * a[c];
     if (kind == ORC_VF_KG) {
-      double e_m = 0.5 * (UL[4] / rL + UR[4] / rR);           /* total specific energy */
+      orc_real e_m = 0.5 * (UL[4] / rL + UR[4] / rR);           /* total specific energy */
       F[4] = rho_m * V * e_m + p_m * V;
     } else {
-      double h_m = 0.5 * ((UL[4] + pL) / rL + (UR[4] + pR) / rR); /* total specific enthalpy */
+      orc_real h_m = 0.5 * ((UL[4] + pL) / rL + (UR[4] + pR) / rR); /* total specific enthalpy */
       F[4] = rho_m * V * h_m;
     }
     return;
   }
   /* Chandrashekar entropy-conservative flux */
-  double bL = rL / (2.0 * pL), bR = rR / (2.0 * pR);
-  double rho_ln = orc_logmean(rL, rR), beta_ln = orc_logmean(bL, bR);
-  double beta_m = 0.5 * (bL + bR);
-  double phat = rho_m / (2.0 * beta_m);
-  double q2_m = 0.5 * ((uL[0] * uL[0] + uL[1] * uL[1] + uL[2] * uL[2]) +
+  orc_real bL = rL / (2.0 * pL), bR = rR / (2.0 * pR);
+  orc_real rho_ln = orc_logmean(rL, rR), beta_ln = orc_logmean(bL, bR);
+  orc_real beta_m = 0.5 * (bL + bR);
+  orc_real phat = rho_m / (2.0 * beta_m);
+  orc_real q2_m = 0.5 * ((uL[0] * uL[0] + uL[1] * uL[1] + uL[2] * uL[2]) +
                        (uR[0] * uR[0] + uR[1] * uR[1] + uR[2] * uR[2]));
   F[0] = rho_ln * V;
   for (int c = 0; c < 3; ++c) F[1 + c] = F[0] * u_m[c] + phat * a[c];
@@ -326,45 +346,45 @@ void orc_twopoint(int kind, const double UL[5], const double UR[5], const double
 }
 
 /* Riemann flux F*(UL, UR, n) for a unit normal n */
-void orc_riemann(int kind, const double UL[5], const double UR[5], const double n[3],
-                 double gamma, double F[5]) {
+void orc_riemann(int kind, const orc_real UL[5], const orc_real UR[5], const double n[3],
+                 double gamma, orc_real F[5]) {
   if (kind == ORC_SF_EC) {
     orc_twopoint(ORC_VF_EC, UL, UR, n, n, gamma, F);
     return;
   }
-  double FL[5], FR[5];
+  orc_real FL[5], FR[5];
   orc_flux_contra(UL, n, gamma, FL);
   orc_flux_contra(UR, n, gamma, FR);
-  double rL, uL[3], pL, rR, uR[3], pR;
+  orc_real rL, uL[3], pL, rR, uR[3], pR;
   primitive(UL, gamma, &rL, uL, &pL);
   primitive(UR, gamma, &rR, uR, &pR);
-  double unL = uL[0] * n[0] + uL[1] * n[1] + uL[2] * n[2];
-  double unR = uR[0] * n[0] + uR[1] * n[1] + uR[2] * n[2];
+  orc_real unL = uL[0] * n[0] + uL[1] * n[1] + uL[2] * n[2];
+  orc_real unR = uR[0] * n[0] + uR[1] * n[1] + uR[2] * n[2];
   if (kind == ORC_SF_LLF) {
-    double cL = sqrt(gamma * pL / rL), cR = sqrt(gamma * pR / rR);
-    double lam = fmax(fabs(unL) + cL, fabs(unR) + cR);
+    orc_real cL = R_SQRT(gamma * pL / rL), cR = R_SQRT(gamma * pR / rR);
+    orc_real lam = R_MAX(R_ABS(unL) + cL, R_ABS(unR) + cR);
     for (int v = 0; v < NVAR; ++v) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (UR[v] - UL[v]);
     return;
   }
   /* Roe: Roe-averaged state, wave strengths and eigenvectors; no entropy fix */
-  double sL = sqrt(rL), sR = sqrt(rR);
-  double ut[3];
+  orc_real sL = R_SQRT(rL), sR = R_SQRT(rR);
+  orc_real ut[3];
   for (int c = 0; c < 3; ++c) ut[c] = (sL * uL[c] + sR * uR[c]) / (sL + sR);
-  double HL = (UL[4] + pL) / rL, HR = (UR[4] + pR) / rR;
-  double Ht = (sL * HL + sR * HR) / (sL + sR);
-  double q2t = ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2];
-  double ct = sqrt((gamma - 1.0) * (Ht - 0.5 * q2t));
-  double rt = sL * sR;
-  double unt = ut[0] * n[0] + ut[1] * n[1] + ut[2] * n[2];
-  double drho = rR - rL, dp = pR - pL;
-  double du[3] = {uR[0] - uL[0], uR[1] - uL[1], uR[2] - uL[2]};
-  double dun = du[0] * n[0] + du[1] * n[1] + du[2] * n[2];
-  double a1 = (dp - rt * ct * dun) / (2.0 * ct * ct);
-  double a5 = (dp + rt * ct * dun) / (2.0 * ct * ct);
-  double a2 = drho - dp / (ct * ct);
-  double dut[3] = {du[0] - dun * n[0], du[1] - dun * n[1], du[2] - dun * n[2]};
-  double l1 = fabs(unt - ct), l5 = fabs(unt + ct), l2 = fabs(unt);
-  double diss[5];
+  orc_real HL = (UL[4] + pL) / rL, HR = (UR[4] + pR) / rR;
+  orc_real Ht = (sL * HL + sR * HR) / (sL + sR);
+  orc_real q2t = ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2];
+  orc_real ct = R_SQRT((gamma - 1.0) * (Ht - 0.5 * q2t));
+  orc_real rt = sL * sR;
+  orc_real unt = ut[0] * n[0] + ut[1] * n[1] + ut[2] * n[2];
+  orc_real drho = rR - rL, dp = pR - pL;
+  orc_real du[3] = {uR[0] - uL[0], uR[1] - uL[1], uR[2] - uL[2]};
+  orc_real dun = du[0] * n[0] + du[1] * n[1] + du[2] * n[2];
+  orc_real a1 = (dp - rt * ct * dun) / (2.0 * ct * ct);
+  orc_real a5 = (dp + rt * ct * dun) / (2.0 * ct * ct);
+  orc_real a2 = drho - dp / (ct * ct);
+  orc_real dut[3] = {du[0] - dun * n[0], du[1] - dun * n[1], du[2] - dun * n[2]};
+  orc_real l1 = R_ABS(unt - ct), l5 = R_ABS(unt + ct), l2 = R_ABS(unt);
+  orc_real diss[5];
   diss[0] = l1 * a1 + l5 * a5 + l2 * a2;
   for (int c = 0; c < 3; ++c)
     diss[1 + c] = l1 * a1 * (ut[c] - ct * n[c]) + l5 * a5 * (ut[c] + ct * n[c]) +
@@ -375,12 +395,12 @@ void orc_riemann(int kind, const double UL[5], const double UR[5], const double 
 }
 
 /* Navier-Stokes-Fourier viscous flux, constant mu, Stokes hypothesis */
-void orc_viscous_flux(const double U[5], const double gradU[9], const double gradT[3], double mu,
-                      double kappa, double gamma, double Fv[15]) {
-  double rho, u[3], p;
+void orc_viscous_flux(const orc_real U[5], const orc_real gradU[9], const orc_real gradT[3], double mu,
+                      double kappa, double gamma, orc_real Fv[15]) {
+  orc_real rho, u[3], p;
   primitive(U, gamma, &rho, u, &p);
-  double div = gradU[0] + gradU[4] + gradU[8];
-  double tau[3][3];
+  orc_real div = gradU[0] + gradU[4] + gradU[8];
+  orc_real tau[3][3];
   for (int r = 0; r < 3; ++r)
     for (int c = 0; c < 3; ++c)
       tau[r][c] = mu * (gradU[r * 3 + c] + gradU[c * 3 + r] - (r == c ? 2.0 / 3.0 * div : 0.0));
@@ -404,10 +424,10 @@ struct orc_state {
   int *slot_side;   /* [nE][6] 0 = this element is L, 1 = R */
   int *slot_nbelem; /* [nE][6] neighbour element */
   int *slot_nbnode; /* [nE][6][nn] neighbour volume node facing own face point (p,q) */
-  double *grad;     /* [nE][4][3][nnn] lifted gradients of (u,v,w,T) */
-  double *Gadv;     /* [nE][6][5][nn] outward advective surface flux, own point order */
-  double *Gvis;     /* [nE][6][5][nn] outward viscous surface flux */
-  double *alpha_raw;
+  orc_real *grad;     /* [nE][4][3][nnn] lifted gradients of (u,v,w,T) */
+  orc_real *Gadv;     /* [nE][6][5][nn] outward advective surface flux, own point order */
+  orc_real *Gvis;     /* [nE][6][5][nn] outward viscous surface flux */
+  orc_real *alpha_raw;
   unsigned char *mark;
 };
 
@@ -458,11 +478,11 @@ orc_state *orc_create(const orc_problem *pb, int *status) {
   for (size_t i = 0; i < (size_t)nE * nnn; ++i)
     if (!(s->J[i] > 0.0)) { orc_destroy(s); *status = -3; return NULL; }
   if (pb->equations == ORC_NAVIER_STOKES) { /* viscous buffers only where they are used */
-    s->grad = (double *)calloc((size_t)nE * 12 * nnn, sizeof(double));
-    s->Gvis = (double *)calloc((size_t)nE * 6 * NVAR * nn, sizeof(double));
+    s->grad = (orc_real *)calloc((size_t)nE * 12 * nnn, sizeof(orc_real));
+    s->Gvis = (orc_real *)calloc((size_t)nE * 6 * NVAR * nn, sizeof(orc_real));
   }
-  s->Gadv = (double *)calloc((size_t)nE * 6 * NVAR * nn, sizeof(double));
-  s->alpha_raw = (double *)calloc(nE, sizeof(double));
+  s->Gadv = (orc_real *)calloc((size_t)nE * 6 * NVAR * nn, sizeof(orc_real));
+  s->alpha_raw = (orc_real *)calloc(nE, sizeof(orc_real));
   s->mark = (unsigned char *)calloc(nE, 1);
   *status = 0;
   return s;
@@ -479,21 +499,21 @@ void orc_destroy(orc_state *s) {
 const double *orc_state_Ja(const orc_state *s) { return s->Ja; }
 const double *orc_state_J(const orc_state *s) { return s->J; }
 
-static void load_state(const orc_state *s, const double *U, int e, int node, double out[5]) {
+static void load_state(const orc_state *s, const orc_real *U, int e, int node, orc_real out[5]) {
   for (int v = 0; v < NVAR; ++v) out[v] = U[((size_t)e * NVAR + v) * s->nnn + node];
 }
 static void load_metric(const orc_state *s, int e, int d, int node, double a[3]) {
   for (int c = 0; c < 3; ++c) a[c] = s->Ja[(((size_t)e * 3 + d) * 3 + c) * s->nnn + node];
 }
-static void load_grad(const orc_state *s, int e, int node, double gU[9], double gT[3]) {
+static void load_grad(const orc_state *s, int e, int node, orc_real gU[9], orc_real gT[3]) {
   for (int r = 0; r < 3; ++r)
     for (int c = 0; c < 3; ++c) gU[r * 3 + c] = s->grad[(((size_t)e * 4 + r) * 3 + c) * s->nnn + node];
   for (int c = 0; c < 3; ++c) gT[c] = s->grad[(((size_t)e * 4 + 3) * 3 + c) * s->nnn + node];
 }
 
 /* lifted variables w = (u, v, w, T), T = p/(rho R) */
-static void lifted_vars(const orc_state *s, const double U[5], double wv[4]) {
-  double rho, u[3], p;
+static void lifted_vars(const orc_state *s, const orc_real U[5], orc_real wv[4]) {
+  orc_real rho, u[3], p;
   primitive(U, s->pb.gamma, &rho, u, &p);
   wv[0] = u[0]; wv[1] = u[1]; wv[2] = u[2]; wv[3] = p / (rho * s->pb.R);
 }
@@ -502,12 +522,12 @@ static void lifted_vars(const orc_state *s, const double U[5], double wv[4]) {
 /* 6. BR1 lifting: J grad w = sum_d Ja^d (D_d w) + surface terms (w* - w) s n_out / w_b  */
 /* ======================================================================= */
 
-static void lift_element(orc_state *s, const double *U, int e) {
+static void lift_element(orc_state *s, const orc_real *U, int e) {
   int N = s->N, n = s->n, nnn = s->nnn;
-  double *wv = (double *)malloc(sizeof(double) * 4 * nnn);
-  double *Jg = (double *)calloc(12 * (size_t)nnn, sizeof(double));
+  orc_real *wv = (orc_real *)malloc(sizeof(orc_real) * 4 * nnn);
+  orc_real *Jg = (orc_real *)calloc(12 * (size_t)nnn, sizeof(orc_real));
   for (int node = 0; node < nnn; ++node) {
-    double Un[5], t[4];
+    orc_real Un[5], t[4];
     load_state(s, U, e, node, Un);
     lifted_vars(s, Un, t);
     for (int q = 0; q < 4; ++q) wv[q * nnn + node] = t[q];
@@ -520,7 +540,7 @@ static void lift_element(orc_state *s, const double *U, int e) {
       double a[3];
       load_metric(s, e, d, node, a);
       for (int q = 0; q < 4; ++q) {
-        double dw = 0.0;
+        orc_real dw = 0.0;
         for (int m = 0; m < n; ++m) {
           int t[3] = {ijk[0], ijk[1], ijk[2]};
           t[d] = m;
@@ -539,13 +559,14 @@ static void lift_element(orc_state *s, const double *U, int e) {
       for (int p = 0; p < n; ++p) {
         int node = face_node(N, f, p, q);
         int nbnode = s->slot_nbnode[((size_t)e * 6 + f) * s->nn + p + n * q];
-        double Unb[5], wnb[4], a[3];
+        orc_real Unb[5], wnb[4];
+        double a[3];
         load_state(s, U, nb, nbnode, Unb);
         lifted_vars(s, Unb, wnb);
         load_metric(s, e, d, node, a);
         for (int qv = 0; qv < 4; ++qv) {
-          double wown = wv[qv * nnn + node];
-          double wstar = 0.5 * (wown + wnb[qv]);
+          orc_real wown = wv[qv * nnn + node];
+          orc_real wstar = 0.5 * (wown + wnb[qv]);
           for (int c = 0; c < 3; ++c) Jg[(qv * 3 + c) * nnn + node] += (wstar - wown) * sgn * a[c] / wb;
         }
       }
@@ -560,12 +581,12 @@ static void lift_element(orc_state *s, const double *U, int e) {
 /* 7. Modified Persson indicator (Sec. 4.1, Eq. (7))                         */
 /* ======================================================================= */
 
-static double indicator_element(const orc_state *s, const double *U, int e) {
+static orc_real indicator_element(const orc_state *s, const orc_real *U, int e) {
   int N = s->N, n = s->n, nnn = s->nnn;
-  double *qv = (double *)malloc(sizeof(double) * nnn);
-  double *m = (double *)malloc(sizeof(double) * nnn);
+  orc_real *qv = (orc_real *)malloc(sizeof(orc_real) * nnn);
+  orc_real *m = (orc_real *)malloc(sizeof(orc_real) * nnn);
   for (int node = 0; node < nnn; ++node) {
-    double Un[5], rho, u[3], p;
+    orc_real Un[5], rho, u[3], p;
     load_state(s, U, e, node, Un);
     primitive(Un, s->pb.gamma, &rho, u, &p);
     qv[node] = rho * p;
@@ -574,14 +595,14 @@ static double indicator_element(const orc_state *s, const double *U, int e) {
   for (int c = 0; c < n; ++c)
     for (int b = 0; b < n; ++b)
       for (int a = 0; a < n; ++a) {
-        double sum = 0.0;
+        orc_real sum = 0.0;
         for (int k = 0; k < n; ++k)
           for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i)
               sum += s->Vinv[a * n + i] * s->Vinv[b * n + j] * s->Vinv[c * n + k] * qv[nidx(n, i, j, k)];
         m[nidx(n, a, b, c)] = sum;
       }
-  double shell[NMAX + 1] = {0}, tot[NMAX + 1] = {0};
+  orc_real shell[NMAX + 1] = {0}, tot[NMAX + 1] = {0};
   for (int c = 0; c < n; ++c)
     for (int b = 0; b < n; ++b)
       for (int a = 0; a < n; ++a) {
@@ -590,27 +611,27 @@ static double indicator_element(const orc_state *s, const double *U, int e) {
         shell[M] += m[nidx(n, a, b, c)] * m[nidx(n, a, b, c)];
       }
   for (int M = 0; M <= N; ++M) tot[M] = (M ? tot[M - 1] : 0.0) + shell[M];
-  double EN = tot[N] > 1e-300 ? shell[N] / tot[N] : 0.0;
-  double E = EN;
+  orc_real EN = RE(tot[N]) > 1e-300 ? shell[N] / tot[N] : 0.0;
+  orc_real E = EN;
   if (N >= 2) {
-    double EN1 = tot[N - 1] > 1e-300 ? shell[N - 1] / tot[N - 1] : 0.0;
-    E = EN1 > EN ? EN1 : EN;
+    orc_real EN1 = RE(tot[N - 1]) > 1e-300 ? shell[N - 1] / tot[N - 1] : 0.0;
+    E = RE(EN1) > RE(EN) ? EN1 : EN;
   }
   double T = 0.5 * pow(10.0, -1.8 * pow(N + 1.0, 0.25));
-  double alpha = 1.0 / (1.0 + exp(-s->pb.sharpness / T * (E - T)));
-  if (alpha < s->pb.alpha_min) alpha = 0.0;
-  if (alpha > s->pb.alpha_max) alpha = s->pb.alpha_max;
+  orc_real alpha = 1.0 / (1.0 + R_EXP(-s->pb.sharpness / T * (E - T)));
+  if (RE(alpha) < s->pb.alpha_min) alpha = 0.0;
+  if (RE(alpha) > s->pb.alpha_max) alpha = s->pb.alpha_max;
   free(qv); free(m);
   return alpha;
 }
 
-int orc_indicator(orc_state *s, const double *U, double *alpha_raw, double *alpha) {
+int orc_indicator(orc_state *s, const orc_real *U, orc_real *alpha_raw, orc_real *alpha) {
   for (int e = 0; e < s->nE; ++e) alpha_raw[e] = indicator_element(s, U, e);
   for (int e = 0; e < s->nE; ++e) {
-    double a = alpha_raw[e];
+    orc_real a = alpha_raw[e];
     for (int f = 0; f < 6; ++f) {
-      double b = 0.5 * alpha_raw[s->slot_nbelem[e * 6 + f]];
-      if (b > a) a = b;
+      orc_real b = 0.5 * alpha_raw[s->slot_nbelem[e * 6 + f]];
+      if (RE(b) > RE(a)) a = b;
     }
     alpha[e] = a;
   }
@@ -621,19 +642,19 @@ int orc_indicator(orc_state *s, const double *U, double *alpha_raw, double *alph
 /* 8. FV subcell operator on one element (Sec. 4.1; Hennemann et al. 2021)  */
 /* ======================================================================= */
 
-static double minmod(double a, double b) {
-  if (a * b <= 0.0) return 0.0;
-  return (fabs(a) < fabs(b)) ? a : b;
+static orc_real minmod(orc_real a, orc_real b) {
+  if (RE(a) * RE(b) <= 0.0) return 0.0;
+  return (fabs(RE(a)) < fabs(RE(b))) ? a : b;
 }
 
-static void cons_from_prim(const double q[5], double gamma, double U[5]) {
+static void cons_from_prim(const orc_real q[5], double gamma, orc_real U[5]) {
   U[0] = q[0];
   U[1] = q[0] * q[1]; U[2] = q[0] * q[2]; U[3] = q[0] * q[3];
   U[4] = q[4] / (gamma - 1.0) + 0.5 * q[0] * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
 }
 
 /* accFV[5][nnn] (reference-space divergence, before -1/J) */
-static void fv_element(const orc_state *s, const double *U, int e, double *accFV) {
+static void fv_element(const orc_state *s, const orc_real *U, int e, orc_real *accFV) {
   int N = s->N, n = s->n, nnn = s->nnn;
   double gamma = s->pb.gamma;
   double xh[NMAX + 2]; /* subcell interfaces xi_{i+1/2}, i = -1..N */
@@ -653,17 +674,17 @@ static void fv_element(const orc_state *s, const double *U, int e, double *accFV
           else { t[0] = a; t[1] = b; t[2] = i; }
           nodes[i] = njoin(n, t);
         }
-        double q[NMAX + 1][5];
+        orc_real q[NMAX + 1][5];
         for (int i = 0; i < n; ++i) {
-          double Un[5], rho, u[3], p;
+          orc_real Un[5], rho, u[3], p;
           load_state(s, U, e, nodes[i], Un);
           primitive(Un, gamma, &rho, u, &p);
           q[i][0] = rho; q[i][1] = u[0]; q[i][2] = u[1]; q[i][3] = u[2]; q[i][4] = p;
         }
         /* minmod slopes, interior subcells only; outer subcells first order */
-        double qL[NMAX + 1][5], qR[NMAX + 1][5];
+        orc_real qL[NMAX + 1][5], qR[NMAX + 1][5];
         for (int i = 0; i < n; ++i) {
-          double sig[5] = {0, 0, 0, 0, 0};
+          orc_real sig[5] = {0, 0, 0, 0, 0};
           if (i > 0 && i < N) {
             for (int v = 0; v < 5; ++v)
               sig[v] = minmod((q[i][v] - q[i - 1][v]) / (s->xi[i] - s->xi[i - 1]),
@@ -673,7 +694,7 @@ static void fv_element(const orc_state *s, const double *U, int e, double *accFV
             qL[i][v] = q[i][v] + sig[v] * (xh[i] - s->xi[i]);
             qR[i][v] = q[i][v] + sig[v] * (xh[i + 1] - s->xi[i]);
           }
-          if (qL[i][0] <= 0.0 || qL[i][4] <= 0.0 || qR[i][0] <= 0.0 || qR[i][4] <= 0.0)
+          if (RE(qL[i][0]) <= 0.0 || RE(qL[i][4]) <= 0.0 || RE(qR[i][0]) <= 0.0 || RE(qR[i][4]) <= 0.0)
             for (int v = 0; v < 5; ++v) { qL[i][v] = q[i][v]; qR[i][v] = q[i][v]; }
         }
         /* subcell interface metrics: a_{-1/2} = Ja_0, a_{i+1/2} = a_{i-1/2} + w_i (D Ja)_i */
@@ -687,7 +708,7 @@ static void fv_element(const orc_state *s, const double *U, int e, double *accFV
             ah[i + 1][c] = ah[i][c] + s->w[i] * dj;
           }
         /* fluxes at the N+2 subcell interfaces, in +xi_d direction */
-        double fh[NMAX + 2][5];
+        orc_real fh[NMAX + 2][5];
         /* element boundaries: the DG surface flux (outward at +, inward at -); the line's
          * tangential indices (a,b) are the face point (p,q) of both end faces */
         for (int v = 0; v < NVAR; ++v) {
@@ -695,12 +716,13 @@ static void fv_element(const orc_state *s, const double *U, int e, double *accFV
           fh[n][v] = s->Gadv[(((size_t)e * 6 + fp) * NVAR + v) * s->nn + a + n * b];
         }
         for (int i = 0; i < N; ++i) {
-          double UL[5], UR[5], nh[3];
+          orc_real UL[5], UR[5];
+          double nh[3];
           cons_from_prim(qR[i], gamma, UL);
           cons_from_prim(qL[i + 1], gamma, UR);
           double sa = sqrt(ah[i + 1][0] * ah[i + 1][0] + ah[i + 1][1] * ah[i + 1][1] + ah[i + 1][2] * ah[i + 1][2]);
           for (int c = 0; c < 3; ++c) nh[c] = ah[i + 1][c] / sa;
-          double Fs[5];
+          orc_real Fs[5];
           orc_riemann(s->pb.sflux, UL, UR, nh, gamma, Fs);
           for (int v = 0; v < NVAR; ++v) fh[i + 1][v] = sa * Fs[v];
         }
@@ -715,7 +737,7 @@ static void fv_element(const orc_state *s, const double *U, int e, double *accFV
 /* 9. Right-hand side                                                       */
 /* ======================================================================= */
 
-int orc_rhs(orc_state *s, const double *U, double *Ut, const unsigned char *out_mask, double *alpha_out) {
+int orc_rhs(orc_state *s, const orc_real *U, orc_real *Ut, const unsigned char *out_mask, orc_real *alpha_out) {
   const orc_problem *pb = &s->pb;
   int N = s->N, n = s->n, nn = s->nn, nnn = s->nnn, nE = s->nE;
   int ns = (pb->equations == ORC_NAVIER_STOKES);
@@ -730,7 +752,7 @@ int orc_rhs(orc_state *s, const double *U, double *Ut, const unsigned char *out_
   }
 
   /* 1. blending coefficient (indicator on the element and its neighbours) */
-  double *alpha = (double *)calloc(nE, sizeof(double));
+  orc_real *alpha = (orc_real *)calloc(nE, sizeof(orc_real));
   if (pb->shock_capturing && pb->alpha_fixed >= 0.0) {
     for (int e = 0; e < nE; ++e) alpha[e] = pb->alpha_fixed;
   } else if (pb->shock_capturing) {
@@ -738,10 +760,10 @@ int orc_rhs(orc_state *s, const double *U, double *Ut, const unsigned char *out_
       if (near[e]) s->alpha_raw[e] = indicator_element(s, U, e);
     for (int e = 0; e < nE; ++e) {
       if (!need[e]) continue;
-      double a = s->alpha_raw[e];
+      orc_real a = s->alpha_raw[e];
       for (int f = 0; f < 6; ++f) {
-        double b = 0.5 * s->alpha_raw[s->slot_nbelem[e * 6 + f]];
-        if (b > a) a = b;
+        orc_real b = 0.5 * s->alpha_raw[s->slot_nbelem[e * 6 + f]];
+        if (RE(b) > RE(a)) a = b;
       }
       alpha[e] = a;
     }
@@ -763,7 +785,8 @@ int orc_rhs(orc_state *s, const double *U, double *Ut, const unsigned char *out_
         int p2, q2;
         orient_map(N, o, p, q, &p2, &q2);
         int nodeL = face_node(N, fL, p, q), nodeR = face_node(N, fR, p2, q2);
-        double UL[5], UR[5], a[3], nh[3], Fa[5], Fv[5] = {0, 0, 0, 0, 0};
+        orc_real UL[5], UR[5], Fa[5], Fv[5] = {0, 0, 0, 0, 0};
+        double a[3], nh[3];
         load_state(s, U, eL, nodeL, UL);
         load_state(s, U, eR, nodeR, UR);
         load_metric(s, eL, dL, nodeL, a);
@@ -771,7 +794,7 @@ int orc_rhs(orc_state *s, const double *U, double *Ut, const unsigned char *out_
         for (int c = 0; c < 3; ++c) nh[c] = sgnL * a[c] / sa;
         orc_riemann(pb->sflux, UL, UR, nh, gamma, Fa);
         if (ns) {
-          double gUL[9], gTL[3], gUR[9], gTR[3], FvL[15], FvR[15];
+          orc_real gUL[9], gTL[3], gUR[9], gTR[3], FvL[15], FvR[15];
           load_grad(s, eL, nodeL, gUL, gTL);
           load_grad(s, eR, nodeR, gUR, gTR);
           orc_viscous_flux(UL, gUL, gTL, pb->mu, kappa, gamma, FvL);
@@ -793,10 +816,10 @@ int orc_rhs(orc_state *s, const double *U, double *Ut, const unsigned char *out_
   }
 
   /* 4. volume integral, surface terms, Jacobian; optional FV blend */
-  double *acc_a = (double *)malloc(sizeof(double) * NVAR * nnn);
-  double *acc_v = (double *)malloc(sizeof(double) * NVAR * nnn);
-  double *accFV = (double *)malloc(sizeof(double) * NVAR * nnn);
-  double *Fvc = (double *)malloc(sizeof(double) * 3 * NVAR * nnn); /* contravariant viscous flux */
+  orc_real *acc_a = (orc_real *)malloc(sizeof(orc_real) * NVAR * nnn);
+  orc_real *acc_v = (orc_real *)malloc(sizeof(orc_real) * NVAR * nnn);
+  orc_real *accFV = (orc_real *)malloc(sizeof(orc_real) * NVAR * nnn);
+  orc_real *Fvc = (orc_real *)malloc(sizeof(orc_real) * 3 * NVAR * nnn); /* contravariant viscous flux */
   for (int e = 0; e < nE; ++e) {
     if (!need[e]) {
       for (int v = 0; v < NVAR; ++v)
@@ -805,7 +828,7 @@ int orc_rhs(orc_state *s, const double *U, double *Ut, const unsigned char *out_
     }
     if (ns)
       for (int node = 0; node < nnn; ++node) {
-        double Un[5], gU[9], gT[3], Fv[15];
+        orc_real Un[5], gU[9], gT[3], Fv[15];
         load_state(s, U, e, node, Un);
         load_grad(s, e, node, gU, gT);
         orc_viscous_flux(Un, gU, gT, pb->mu, kappa, gamma, Fv);
@@ -819,7 +842,7 @@ int orc_rhs(orc_state *s, const double *U, double *Ut, const unsigned char *out_
     for (int node = 0; node < nnn; ++node) {
       int ijk[3];
       nsplit(n, node, ijk);
-      double Ui[5], sa[5] = {0, 0, 0, 0, 0}, sv[5] = {0, 0, 0, 0, 0};
+      orc_real Ui[5], sa[5] = {0, 0, 0, 0, 0}, sv[5] = {0, 0, 0, 0, 0};
       load_state(s, U, e, node, Ui);
       for (int d = 0; d < 3; ++d) {
         double ai[3];
@@ -828,7 +851,8 @@ int orc_rhs(orc_state *s, const double *U, double *Ut, const unsigned char *out_
           int t[3] = {ijk[0], ijk[1], ijk[2]};
           t[d] = m;
           int nm = njoin(n, t);
-          double Um[5], am[3], Fs[5];
+          orc_real Um[5], Fs[5];
+          double am[3];
           load_state(s, U, e, nm, Um);
           load_metric(s, e, d, nm, am);
           orc_twopoint(pb->vflux, Ui, Um, ai, am, gamma, Fs);
@@ -844,7 +868,7 @@ int orc_rhs(orc_state *s, const double *U, double *Ut, const unsigned char *out_
           int f = 2 * d + side, sgn = side ? 1 : -1;
           int p = (d == 0) ? ijk[1] : ijk[0];
           int q = (d == 2) ? ijk[1] : ijk[2];
-          double Fi[5];
+          orc_real Fi[5];
           orc_flux_contra(Ui, ai, gamma, Fi);
           for (int v = 0; v < NVAR; ++v) {
             sa[v] += (s->Gadv[(((size_t)e * 6 + f) * NVAR + v) * nn + p + n * q] - sgn * Fi[v]) / s->w[b];
@@ -856,15 +880,15 @@ int orc_rhs(orc_state *s, const double *U, double *Ut, const unsigned char *out_
       }
       for (int v = 0; v < NVAR; ++v) { acc_a[v * nnn + node] = sa[v]; acc_v[v * nnn + node] = sv[v]; }
     }
-    double al = alpha[e];
-    if (pb->shock_capturing && al > 0.0) fv_element(s, U, e, accFV);
+    orc_real al = alpha[e];
+    if (pb->shock_capturing && RE(al) > 0.0) fv_element(s, U, e, accFV);
     for (int v = 0; v < NVAR; ++v)
       for (int node = 0; node < nnn; ++node) {
         double Jn = s->J[(size_t)e * nnn + node];
-        double adv_dg = -acc_a[v * nnn + node] / Jn;
-        double adv = adv_dg;
-        if (pb->shock_capturing && al > 0.0) {
-          double adv_fv = -accFV[v * nnn + node] / Jn;
+        orc_real adv_dg = -acc_a[v * nnn + node] / Jn;
+        orc_real adv = adv_dg;
+        if (pb->shock_capturing && RE(al) > 0.0) {
+          orc_real adv_fv = -accFV[v * nnn + node] / Jn;
           adv = al * adv_fv + (1.0 - al) * adv_dg;
         }
         Ut[((size_t)e * NVAR + v) * nnn + node] = adv + (ns ? acc_v[v * nnn + node] / Jn : 0.0);
@@ -899,11 +923,11 @@ void orc_lserk_coefficients(double A[5], double B[5], double c[5]) {
 }
 
 /* g := 0; for each stage s: g = A_s g + dt f(u, t + c_s dt); u = u + B_s g */
-int orc_lserk_generic(int n, double *u, double dt, double t, orc_rhs_fn f, void *ctx) {
+int orc_lserk_generic(int n, orc_real *u, double dt, double t, orc_rhs_fn f, void *ctx) {
   double A[5], B[5], c[5];
   orc_lserk_coefficients(A, B, c);
-  double *g = (double *)calloc(n, sizeof(double));
-  double *ut = (double *)malloc(sizeof(double) * n);
+  orc_real *g = (orc_real *)calloc(n, sizeof(orc_real));
+  orc_real *ut = (orc_real *)malloc(sizeof(orc_real) * n);
   for (int st = 0; st < 5; ++st) {
     f(u, ut, t + c[st] * dt, ctx);
     for (int i = 0; i < n; ++i) {
@@ -915,12 +939,12 @@ int orc_lserk_generic(int n, double *u, double dt, double t, orc_rhs_fn f, void 
   return 0;
 }
 
-static void dg_rhs_cb(const double *u, double *ut, double t, void *ctx) {
+static void dg_rhs_cb(const orc_real *u, orc_real *ut, double t, void *ctx) {
   (void)t;
   orc_rhs((orc_state *)ctx, u, ut, NULL, NULL);
 }
 
-int orc_lserk_step(orc_state *s, double *U, double dt, double t) {
+int orc_lserk_step(orc_state *s, orc_real *U, double dt, double t) {
   return orc_lserk_generic(s->nE * NVAR * s->nnn, U, dt, t, dg_rhs_cb, s);
 }
 
@@ -930,7 +954,7 @@ int orc_lserk_step(orc_state *s, double *U, double dt, double t) {
 
 /* out[0..4] = sum J w Ut_v; out[5] = sum J w (v . Ut), v = entropy variables;
  * out[6] = sum J w (rho |u|^2 / 2); out[7] = sum J w d/dt(rho |u|^2 / 2) */
-int orc_invariants(orc_state *s, const double *U, const double *Ut, double out[8]) {
+int orc_invariants(orc_state *s, const orc_real *U, const orc_real *Ut, orc_real out[8]) {
   int n = s->n, nnn = s->nnn;
   double gamma = s->pb.gamma;
   for (int k = 0; k < 8; ++k) out[k] = 0.0;
@@ -939,13 +963,13 @@ int orc_invariants(orc_state *s, const double *U, const double *Ut, double out[8
       int ijk[3];
       nsplit(n, node, ijk);
       double wq = s->w[ijk[0]] * s->w[ijk[1]] * s->w[ijk[2]] * s->J[(size_t)e * nnn + node];
-      double Un[5], Utn[5], rho, u[3], p;
+      orc_real Un[5], Utn[5], rho, u[3], p;
       load_state(s, U, e, node, Un);
       load_state(s, Ut, e, node, Utn);
       primitive(Un, gamma, &rho, u, &p);
-      double q2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-      double sent = log(p) - gamma * log(rho);
-      double v[5] = {(gamma - sent) / (gamma - 1.0) - rho * q2 / (2.0 * p), rho * u[0] / p, rho * u[1] / p,
+      orc_real q2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+      orc_real sent = R_LOG(p) - gamma * R_LOG(rho);
+      orc_real v[5] = {(gamma - sent) / (gamma - 1.0) - rho * q2 / (2.0 * p), rho * u[0] / p, rho * u[1] / p,
                      rho * u[2] / p, -rho / p};
       for (int k = 0; k < 5; ++k) out[k] += wq * Utn[k];
       out[5] += wq * (v[0] * Utn[0] + v[1] * Utn[1] + v[2] * Utn[2] + v[3] * Utn[3] + v[4] * Utn[4]);
@@ -956,19 +980,19 @@ int orc_invariants(orc_state *s, const double *U, const double *Ut, double out[8
 }
 
 /* dt = cfl * min over nodes of 2 J / ((2N+1) sum_d (|u . Ja^d| + c |Ja^d|)) */
-int orc_max_dt(orc_state *s, const double *U, double cfl, double *dt) {
+int orc_max_dt(orc_state *s, const orc_real *U, double cfl, double *dt) {
   int nnn = s->nnn;
   double best = INFINITY;
   for (int e = 0; e < s->nE; ++e)
     for (int node = 0; node < nnn; ++node) {
-      double Un[5], rho, u[3], p;
+      orc_real Un[5], rho, u[3], p;
       load_state(s, U, e, node, Un);
       primitive(Un, s->pb.gamma, &rho, u, &p);
-      double c = sqrt(s->pb.gamma * p / rho), lam = 0.0;
+      double c = sqrt(s->pb.gamma * RE(p) / RE(rho)), lam = 0.0;
       for (int d = 0; d < 3; ++d) {
         double a[3];
         load_metric(s, e, d, node, a);
-        lam += fabs(u[0] * a[0] + u[1] * a[1] + u[2] * a[2]) + c * sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+        lam += fabs(RE(u[0]) * a[0] + RE(u[1]) * a[1] + RE(u[2]) * a[2]) + c * sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
       }
       double v = 2.0 * s->J[(size_t)e * nnn + node] / ((2.0 * s->N + 1.0) * lam);
       if (v < best) best = v;

@@ -31,6 +31,19 @@
 extern "C" {
 #endif
 
+/* orc_real is the type of every quantity that depends on the state U. The default build
+ * uses double. The complex-step build (-DORC_COMPLEX_STEP, a second library) runs the same
+ * source on double _Complex: for a real state U, direction V and h = 1e-30, Im L(U + i h V) / h
+ * is the directional derivative of the right-hand side L (and of the LSERK step) with no
+ * cancellation error, which makes it the reference for the discrete adjoint. Metrics, basis
+ * and coefficients stay double in both builds. */
+#ifdef ORC_COMPLEX_STEP
+#include <complex.h>
+typedef double _Complex orc_real;
+#else
+typedef double orc_real;
+#endif
+
 enum { ORC_EULER = 0, ORC_NAVIER_STOKES = 1 };
 enum { ORC_VF_KG = 0, ORC_VF_PIROZZOLI = 1, ORC_VF_EC = 2, ORC_VF_CENTRAL = 3 };
 enum { ORC_SF_LLF = 0, ORC_SF_ROE = 1, ORC_SF_EC = 2 };
@@ -63,15 +76,15 @@ int orc_invert(int n, const double *A, double *Ainv);            /* Gauss-Jordan
 int orc_metrics(int N, int n_elems, const double *xyz, double *Ja, double *J);
 
 /* ---- pointwise fluxes (exposed for unit pins) ---- */
-double orc_logmean(double a, double b);
-void orc_flux_contra(const double U[5], const double a[3], double gamma, double F[5]);
-void orc_twopoint(int kind, const double UL[5], const double UR[5], const double aL[3],
-                  const double aR[3], double gamma, double F[5]);
-void orc_riemann(int kind, const double UL[5], const double UR[5], const double nhat[3],
-                 double gamma, double F[5]);
+orc_real orc_logmean(orc_real a, orc_real b);
+void orc_flux_contra(const orc_real U[5], const double a[3], double gamma, orc_real F[5]);
+void orc_twopoint(int kind, const orc_real UL[5], const orc_real UR[5], const double aL[3],
+                  const double aR[3], double gamma, orc_real F[5]);
+void orc_riemann(int kind, const orc_real UL[5], const orc_real UR[5], const double nhat[3],
+                 double gamma, orc_real F[5]);
 /* gradU[r][c] = d u_r / d x_c, gradT[c]; Fv[c][v] = viscous flux in Cartesian direction c */
-void orc_viscous_flux(const double U[5], const double gradU[9], const double gradT[3],
-                      double mu, double kappa, double gamma, double Fv[15]);
+void orc_viscous_flux(const orc_real U[5], const orc_real gradU[9], const orc_real gradT[3],
+                      double mu, double kappa, double gamma, orc_real Fv[15]);
 
 /* ---- solver ---- */
 orc_state *orc_create(const orc_problem *pb, int *status);
@@ -80,15 +93,15 @@ const double *orc_state_Ja(const orc_state *s);
 const double *orc_state_J(const orc_state *s);
 /* out_mask (n_elems bytes, nullable): compute Ut only where mask != 0 (others set to 0).
  * alpha (n_elems, nullable): receives the blending coefficient used (0 without shock capturing). */
-int orc_rhs(orc_state *s, const double *U, double *Ut, const unsigned char *out_mask, double *alpha);
-int orc_indicator(orc_state *s, const double *U, double *alpha_raw, double *alpha);
-int orc_lserk_step(orc_state *s, double *U, double dt, double t);
-int orc_invariants(orc_state *s, const double *U, const double *Ut, double out[8]);
-int orc_max_dt(orc_state *s, const double *U, double cfl, double *dt);
+int orc_rhs(orc_state *s, const orc_real *U, orc_real *Ut, const unsigned char *out_mask, orc_real *alpha);
+int orc_indicator(orc_state *s, const orc_real *U, orc_real *alpha_raw, orc_real *alpha);
+int orc_lserk_step(orc_state *s, orc_real *U, double dt, double t);
+int orc_invariants(orc_state *s, const orc_real *U, const orc_real *Ut, orc_real out[8]);
+int orc_max_dt(orc_state *s, const orc_real *U, double cfl, double *dt);
 
 /* LSERK(5,4) on a generic system u' = f(u, t) (used to pin the scheme on scalar ODEs). */
-typedef void (*orc_rhs_fn)(const double *u, double *ut, double t, void *ctx);
-int orc_lserk_generic(int n, double *u, double dt, double t, orc_rhs_fn f, void *ctx);
+typedef void (*orc_rhs_fn)(const orc_real *u, orc_real *ut, double t, void *ctx);
+int orc_lserk_generic(int n, orc_real *u, double dt, double t, orc_rhs_fn f, void *ctx);
 void orc_lserk_coefficients(double A[5], double B[5], double c[5]);
 
 #ifdef __cplusplus
