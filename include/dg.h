@@ -130,6 +130,37 @@ dg_status dg_invariants(dg_ctx *ctx, const double *U, const double *Ut, double o
 dg_status dg_invariants_noalloc(int N, int n_elems, double gamma, const double *U, const double *Ut,
                                 const double *J, double *out8, void *cuda_stream);
 
+/* ---- Discrete adjoint (vector-Jacobian products). The paper's solver (Sec. 2) is an explicit
+ * method of lines U' = L(U); these calls give the exact transposed derivatives of the discrete
+ * operator this library applies, for gradient-based use (optimisation, sensitivities, training).
+ * Supported: FP64 (DG_FP64), no shock capturing, volume flux DG_VFLUX_KG or DG_VFLUX_PIROZZOLI, any
+ * surface flux, Euler or Navier-Stokes. Anything else returns DG_ERR_UNSUPPORTED before any
+ * launch. The Roe and LLF fluxes contain |.| and max: where an argument is exactly zero (or two are
+ * equal) the one-sided derivative of the branch the forward kernel takes is used.
+ * Work buffers are library-owned; the state buffers of the LSERK adjoints are allocated on first
+ * use (DG_ERR_OOM if that fails) and kept until dg_free. All arrays are device arrays
+ * [n_elems][5][n]^3 on the context stream; asynchronous unless stated. ---- */
+
+/* Ubar = (dL/dU)(U)^T lambda. Ubar must overlap neither U nor lambda. */
+dg_status dg_rhs_vjp(dg_ctx *ctx, const double *U, const double *lambda, double *Ubar, double t);
+
+/* Reverse of one LSERK(5,4) step from state U (unchanged): on entry Ubar is the cotangent of the
+ * state after the step, on exit that of U. The step's four inner stage states are recomputed
+ * (library-owned, 4 state buffers); the stages are then run backwards:
+ * gbar = B_5 Ubar; for s = 5..1: Ubar += dt (dL/dU)(U^(s-1))^T gbar; gbar = A_s gbar + B_(s-1) Ubar. */
+dg_status dg_lserk_step_vjp(dg_ctx *ctx, const double *U, double *Ubar, double dt, double t);
+
+/* Reverse of n_steps LSERK steps from U0 (unchanged) with two-level checkpointing: a forward sweep
+ * stores the state every `interval` steps (ceil(n_steps/interval) buffers); each segment is then
+ * recomputed once from its checkpoint, keeping its start states (interval buffers), and reversed
+ * step by step with dg_lserk_step_vjp. On entry Ubar is the cotangent of U(n_steps), on exit that
+ * of U0. Memory: ceil(n_steps/interval) + interval + 5 state buffers. Synchronising only on error. */
+dg_status dg_lserk_steps_vjp(dg_ctx *ctx, const double *U0, double *Ubar, double dt, double t, int n_steps,
+                             int interval);
+
+/* grad = d/dU of the kinetic-energy integral sum J w rho|u|^2/2 (out[6] of dg_invariants). */
+dg_status dg_kinetic_energy_grad(dg_ctx *ctx, const double *U, double *grad);
+
 /* *dt = cfl * min over nodes of 2J / ((2N+1) sum_d (|u.Ja^d| + c|Ja^d|)) (synchronising). */
 dg_status dg_max_dt(dg_ctx *ctx, const double *U, double cfl, double *dt);
 
@@ -142,7 +173,7 @@ dg_status dg_get_metrics(dg_ctx *ctx, double *Ja, double *J);
 
 /* Kernel timing on the context stream: when enabled, CUDA events bracket every launch and
  * per-kernel totals accumulate (ms, launches). Names: "face", "lift", "volume", "indicator",
- * "spread", "other". dg_timing_get fills up to `cap` entries and returns the count. */
+ * "spread", "other", "adj_face", "adj_visc", "adj_volume". dg_timing_get fills up to `cap` entries and returns the count. */
 dg_status dg_timing_enable(dg_ctx *ctx, int enable);
 int dg_timing_get(dg_ctx *ctx, const char **names, double *ms, long long *launches, int cap);
 /* total kernel launches issued by this context */

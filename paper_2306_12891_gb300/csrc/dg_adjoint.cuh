@@ -1,0 +1,513 @@
+// dg_adjoint.cuh -- discrete adjoint (vector-Jacobian product) of the FP64 split-form DGSEM
+// right-hand side L(U) for ONE polynomial degree; included after dg_kernels.cuh in the same
+// translation unit (same anonymous namespace, same constant tables).
+//
+// Given a cotangent lambda of Ut = L(U), the kernels form Ubar = (dL/dU)^T lambda, the transpose
+// of exactly the operator the forward kernels apply (zero-diagonal flux differencing with the
+// SBP surface identity, Riemann flux once per face point, BR1 lifting with central face values,
+// -(1/(2 w_b)) phi_nb for the neighbour's viscous flux, -1/J). With l = -lambda/J per node:
+//
+//   adj_face    per face point: c = s/w_0 (l_L - l_R) is the cotangent of F*(U_L, U_R, n); its
+//               transposed Jacobian goes to both sides' face slots. The Riemann solver is
+//               differentiated in forward mode (dual numbers, 5 seeds per pass, 2 passes) through
+//               the same templated code the forward kernel runs.
+//   adj_visc    (Navier-Stokes) per element: recompute the lifted gradients; transpose the
+//               viscous divergence (D^T sweeps of l, neighbour term through the face), the
+//               contravariant projection and the Navier-Stokes-Fourier flux (pointwise), then the
+//               lifting (D^T sweeps, central face value): cotangents of (u, v, w, T) per node plus
+//               face slots for the neighbour's share.
+//   adj_volume  per element: the two-point flux differencing transposed pair by pair. With
+//               sums S = x_i + x_m the Kennedy-Gruber / Pirozzoli fluxes are polynomials in
+//               (S_rho, S_u, S_p, S_X), so each pair adds the same cotangent vector to both of its
+//               nodes' primitive accumulators; then per node the primitive cotangents (plus the
+//               viscous ones) are chained to the conservative variables, the face slots are added,
+//               and either Ubar is written or the LSERK(5,4) reverse stage is applied in place.
+#pragma once
+#include "dg_dual.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------------------------------------
+// adjoint of the face kernel
+// ---------------------------------------------------------------------------------------------
+template <int SF>
+__global__ void __launch_bounds__(128) k_adj_face(const DgDevice d, const double *__restrict__ U,
+                                                  const double *__restrict__ lam, double *__restrict__ slots) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)d.nF * nn) return;
+  const int f = (int)(t / nn), pq = (int)(t % nn), p = pq % n, q = pq / n;
+  const int *F5 = d.face + 5 * f;
+  const int eL = F5[0], fL = F5[1], eR = F5[2], fR = F5[3], o = F5[4];
+  int p2, q2;
+  orient_map(o, p, q, p2, q2);
+  const int nodeL = face_node(fL, p, q), nodeR = face_node(fR, p2, q2);
+  const int pqR = p2 + n * q2;
+  const double *nr = d.nrm + (size_t)f * 4 * nn + pq;
+  double UL[5], UR[5], cF[5];
+  load_state<double>(d, U, eL, nodeL, UL);
+  load_state<double>(d, U, eR, nodeR, UR);
+  const double iJL = d.invJ[(size_t)eL * nnn + nodeL], iJR = d.invJ[(size_t)eR * nnn + nodeR];
+  const double sw = nr[3 * nn] * c_invw[0];  // w_0 = w_N
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+    cF[v] = sw * (iJR * lam[((size_t)eR * 5 + v) * nnn + nodeR] - iJL * lam[((size_t)eL * 5 + v) * nnn + nodeL]);
+  using D5 = Dual<5>;
+  const D5 nv[3] = {D5(nr[0]), D5(nr[nn]), D5(nr[2 * nn])};
+  const D5 gam(d.gamma), zero(0.0);
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    D5 A[5], B[5], Fd[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      A[v] = D5(UL[v]);
+      B[v] = D5(UR[v]);
+      if (side == 0) A[v].d[v] = 1.0;
+      else B[v].d[v] = 1.0;
+    }
+    riemann<D5>(SF, A, B, nv, gam, zero, zero, Fd);
+    double *out = slots + ((size_t)(side ? eR : eL) * 6 + (side ? fR : fL)) * 5 * nn + (side ? pqR : pq);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      double gk = 0.0;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) gk += cF[v] * Fd[v].d[k];
+      out[k * nn] = gk;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// adjoint of the lifting + viscous flux + viscous divergence (Navier-Stokes)
+// shared memory per element: W[4][nnn] (u, v, w, T), L[4][nnn] (l of momentum and energy),
+// H[12][nnn] (cotangent of the direction-d reference derivative of w_q), Om[3][nnn]
+// ---------------------------------------------------------------------------------------------
+constexpr int ADJV_SLOTS = 23;
+
+// the neighbour's volume node facing face point (pp, qq) of element e's face f
+__device__ __forceinline__ void neighbour_node(const DgDevice &d, size_t e, int f, int pp, int qq, int &nb, int &fnb,
+                                               int &nbnode, int &nbpq) {
+  const int *ef = d.ef + (e * 6 + f) * 4;
+  nb = ef[0];
+  fnb = ef[1];
+  int p2, q2;
+  orient_map(ef[2], pp, qq, p2, q2);
+  nbnode = face_node(fnb, p2, q2);
+  nbpq = p2 + n * q2;
+}
+
+__global__ void __launch_bounds__(LIFT_THREADS) k_adj_visc(const DgDevice d, const double *__restrict__ U,
+                                                           const double *__restrict__ lam, double *__restrict__ cotW,
+                                                           double *__restrict__ sigma) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  double *Ws = reinterpret_cast<double *>(sm_raw);  // [EPB][4][nnn]
+  double *Ls = Ws + LIFT_EPB * 4 * nnn;              // [EPB][4][nnn]
+  double *Hs = Ls + LIFT_EPB * 4 * nnn;              // [EPB][12][nnn]
+  double *Os = Hs + LIFT_EPB * 12 * nnn;             // [EPB][3][nnn]
+  const int e0 = blockIdx.x * LIFT_EPB;
+  const double gm1 = d.gamma - 1.0, iR = 1.0 / d.R, mu = d.mu, kappa = d.kappa;
+  for (int t = threadIdx.x; t < LIFT_EPB * nnn; t += blockDim.x) {
+    const int le = t / nnn, node = t % nnn, e = e0 + le;
+    if (e >= d.nE) continue;
+    double Uv[5];
+    load_state<double>(d, U, e, node, Uv);
+    const double r = Uv[0], ir = 1.0 / r;
+    const double u = Uv[1] * ir, v = Uv[2] * ir, w = Uv[3] * ir;
+    const double p = gm1 * (Uv[4] - 0.5 * r * (u * u + v * v + w * w));
+    double *W = Ws + le * 4 * nnn + node;
+    W[0] = u;
+    W[nnn] = v;
+    W[2 * nnn] = w;
+    W[3 * nnn] = p * ir * iR;
+    const double miJ = -d.invJ[(size_t)e * nnn + node];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Ls[(le * 4 + q) * nnn + node] = miJ * lam[((size_t)e * 5 + 1 + q) * nnn + node];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < LIFT_EPB * nnn; t += blockDim.x) {
+    const int le = t / nnn, node = t % nnn, e = e0 + le;
+    if (e >= d.nE) continue;
+    const int ijk[3] = {node % n, (node / n) % n, node / nn};
+    const double *W = Ws + le * 4 * nnn;
+    const double *L = Ls + le * 4 * nnn;
+    double Ja[3][3];
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Ja[dd][c] = d.Ja[(((size_t)e * 3 + dd) * 3 + c) * nnn + node];
+    // forward: lifted gradients g[q][c] of w_q, as the lifting kernel forms them
+    double g[4][3];
+    // reverse seed: zeta[dd][q] = cotangent of the contravariant viscous flux Fv^dd_q at this node
+    double zeta[3][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) g[q][0] = g[q][1] = g[q][2] = 0.0;
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) {
+      const int id = ijk[dd];
+      const int st = dd == 0 ? 1 : dd == 1 ? n : nn;
+      const int base = node - id * st;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        double s = 0.0, z = 0.0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          s += c_D[id * n + m] * W[q * nnn + base + m * st];
+          if (m != id) z -= c_D[m * n + id] * L[q * nnn + base + m * st];
+        }
+        g[q][0] += Ja[dd][0] * s;
+        g[q][1] += Ja[dd][1] * s;
+        g[q][2] += Ja[dd][2] * s;
+        zeta[dd][q] = z;
+      }
+      if (id == 0 || id == N) {
+        const int f = 2 * dd + (id == N ? 1 : 0);
+        const int pp = dd == 0 ? ijk[1] : ijk[0], qq = dd == 2 ? ijk[1] : ijk[2];
+        int nb, fnb, nbnode, nbpq;
+        neighbour_node(d, e, f, pp, qq, nb, fnb, nbnode, nbpq);
+        double Un[5];
+        load_state<double>(d, U, nb, nbnode, Un);
+        const double r = Un[0], ir = 1.0 / r;
+        const double wn[4] = {Un[1] * ir, Un[2] * ir, Un[3] * ir,
+                              gm1 * (Un[4] - 0.5 * (Un[1] * Un[1] + Un[2] * Un[2] + Un[3] * Un[3]) * ir) * ir * iR};
+        const double sc = (id == N ? 1.0 : -1.0) * c_invw[id];
+        const double sgf = (f & 1) ? 0.5 : -0.5;
+        const double miJn = -d.invJ[(size_t)nb * nnn + nbnode];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const double jq = sc * (0.5 * (wn[q] - W[q * nnn + node]));
+          g[q][0] += Ja[dd][0] * jq;
+          g[q][1] += Ja[dd][1] * jq;
+          g[q][2] += Ja[dd][2] * jq;
+          zeta[dd][q] += c_invw[id] * sgf * (miJn * lam[((size_t)nb * 5 + 1 + q) * nnn + nbnode]);
+        }
+      }
+    }
+    const double iJ = d.invJ[(size_t)e * nnn + node];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { g[q][0] *= iJ; g[q][1] *= iJ; g[q][2] *= iJ; }
+    const double u[3] = {W[node], W[nnn + node], W[2 * nnn + node]};
+    const double div = g[0][0] + g[1][1] + g[2][2];
+    double tau[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) tau[k][c] = mu * (g[k][c] + g[c][k]) - (k == c ? 2.0 / 3.0 * mu * div : 0.0);
+    // Z[c][q]: cotangent of the Cartesian viscous flux F_c,q (F_c,k = tau_kc; F_c,3 = u.tau_c + kappa dT/dx_c)
+    double Z[3][4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) Z[c][q] = Ja[0][c] * zeta[0][q] + Ja[1][c] * zeta[1][q] + Ja[2][c] * zeta[2][q];
+    double Y[3][3], om[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      om[k] = Z[0][3] * tau[k][0] + Z[1][3] * tau[k][1] + Z[2][3] * tau[k][2];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Y[k][c] = Z[c][k] + Z[c][3] * u[k];
+    }
+    const double trY = Y[0][0] + Y[1][1] + Y[2][2];
+    double Gm[4][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Gm[k][c] = mu * (Y[k][c] + Y[c][k]) - (k == c ? 2.0 / 3.0 * mu * trY : 0.0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Gm[3][c] = kappa * Z[c][3];
+    double *H = Hs + le * 12 * nnn + node;
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        H[(dd * 4 + q) * nnn] = iJ * (Ja[dd][0] * Gm[q][0] + Ja[dd][1] * Gm[q][1] + Ja[dd][2] * Gm[q][2]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Os[(le * 3 + k) * nnn + node] = om[k];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < LIFT_EPB * nnn; t += blockDim.x) {
+    const int le = t / nnn, node = t % nnn, e = e0 + le;
+    if (e >= d.nE) continue;
+    const int ijk[3] = {node % n, (node / n) % n, node / nn};
+    const double *H = Hs + le * 12 * nnn;
+    double cw[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) {
+      const int id = ijk[dd];
+      const int st = dd == 0 ? 1 : dd == 1 ? n : nn;
+      const int base = node - id * st;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        double s = 0.0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) s += c_D[m * n + id] * H[(dd * 4 + q) * nnn + base + m * st];
+        cw[q] += s;
+      }
+      if (id == 0 || id == N) {
+        const int f = 2 * dd + (id == N ? 1 : 0);
+        const int pq = (dd == 0 ? ijk[1] : ijk[0]) + n * (dd == 2 ? ijk[1] : ijk[2]);
+        const double hs = (id == N ? 0.5 : -0.5) * c_invw[id];
+        double *sg = sigma + ((size_t)e * 6 + f) * 4 * nn + pq;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const double h = hs * H[(dd * 4 + q) * nnn + node];
+          cw[q] -= h;
+          sg[q * nn] = h;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) cw[k] += Os[(le * 3 + k) * nnn + node];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cotW[((size_t)e * 4 + q) * nnn + node] = cw[q];
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// adjoint of the volume kernel
+// staged per element: P[6][PS] = (rho, u, v, w, 4p, X) with X = h (Pirozzoli) or e = E/rho (KG),
+// Lm[5][PS] = l, and per direction Acc[3][6][PS] = cotangents of (rho, u, v, w, 4p, X)
+// ---------------------------------------------------------------------------------------------
+constexpr int ADJ_NP = 6;
+constexpr int ADJ_SLOTS = ADJ_NP + 5 + 18;
+
+// Transposed flux differencing along one line. The forward pair term (scaled by the folded
+// 1/2 factors) is c.F with F0 = S_rho V, F_k = F0 S_u,k + S_p S_j,k, F4 = F0 S_X (+ S_p V / 2 for KG),
+// V = S_u . S_j and c_v = D'_im l_i,v + D'_mi l_m,v (D' = D/4 for mass, D/8 otherwise).
+template <int VF>
+__device__ __forceinline__ void adj_line(const double *__restrict__ P, const double *__restrict__ Lm, int pb, int ps,
+                                         const double *__restrict__ Jd, int gb, int gs, double *__restrict__ Ac) {
+#pragma unroll 1
+  for (int i = 0; i < n; ++i) {
+    const int ai = pb + i * ps, gi = gb + i * gs;
+    const double ri = P[ai], ui = P[PS + ai], vi = P[2 * PS + ai], wi = P[3 * PS + ai];
+    const double pi = P[4 * PS + ai], xi_ = P[5 * PS + ai];
+    const double li0 = Lm[ai], li1 = Lm[PS + ai], li2 = Lm[2 * PS + ai], li3 = Lm[3 * PS + ai], li4 = Lm[4 * PS + ai];
+    const double jxi = __ldg(Jd + gi), jyi = __ldg(Jd + nnn + gi), jzi = __ldg(Jd + 2 * nnn + gi);
+    double ac[6];
+#pragma unroll
+    for (int v = 0; v < 6; ++v) ac[v] = (i == 0) ? 0.0 : Ac[v * PS + ai];
+#pragma unroll
+    for (int m = i + 1; m < n; ++m) {
+      const int am = pb + m * ps, gm = gb + m * gs;
+      const double Sr = ri + P[am], Su = ui + P[PS + am], Sv = vi + P[2 * PS + am], Sw = wi + P[3 * PS + am];
+      const double Sp = pi + P[4 * PS + am], Sx = xi_ + P[5 * PS + am];
+      const double Sjx = jxi + __ldg(Jd + gm), Sjy = jyi + __ldg(Jd + nnn + gm), Sjz = jzi + __ldg(Jd + 2 * nnn + gm);
+      const double dqi = c_Dq[i * n + m], dqm = c_Dq[m * n + i], dei = c_De[i * n + m], dem = c_De[m * n + i];
+      const double c0 = dqi * li0 + dqm * Lm[am];
+      const double c1 = dei * li1 + dem * Lm[PS + am];
+      const double c2 = dei * li2 + dem * Lm[2 * PS + am];
+      const double c3 = dei * li3 + dem * Lm[3 * PS + am];
+      const double c4 = dei * li4 + dem * Lm[4 * PS + am];
+      const double Vp = Su * Sjx + Sv * Sjy + Sw * Sjz;
+      const double F0 = Sr * Vp;
+      const double phi = c0 + c1 * Su + c2 * Sv + c3 * Sw + c4 * Sx;  // d(c.F)/dF0
+      double gV = phi * Sr, gP = c1 * Sjx + c2 * Sjy + c3 * Sjz;
+      if (VF == VF_KG) {
+        gV += 0.5 * c4 * Sp;
+        gP += 0.5 * c4 * Vp;
+      }
+      const double g[6] = {phi * Vp, c1 * F0 + gV * Sjx, c2 * F0 + gV * Sjy, c3 * F0 + gV * Sjz, gP, c4 * F0};
+#pragma unroll
+      for (int v = 0; v < 6; ++v) {
+        ac[v] += g[v];
+        if (i == 0) Ac[v * PS + am] = g[v];
+        else Ac[v * PS + am] += g[v];
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 6; ++v) Ac[v * PS + ai] = ac[v];
+  }
+}
+
+template <int VF>
+__global__ void __launch_bounds__(VOL_THREADS, 1) k_adj_volume(const DgDevice d, const double *__restrict__ U,
+                                                              const double *lam, const double *__restrict__ fslots,
+                                                              const double *__restrict__ cotW,
+                                                              const double *__restrict__ sigma, double *out,
+                                                              double *gbar, int mode, double dt, double A, double B,
+                                                              int update_g) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  double *P = reinterpret_cast<double *>(sm_raw);  // [EPB][6][PS]
+  double *Lm = P + VOL_EPB * ADJ_NP * PS;          // [EPB][5][PS]
+  double *Acc = Lm + VOL_EPB * 5 * PS;             // [EPB][3][6][PS]
+  const int e0 = blockIdx.x * VOL_EPB;
+  const double gam = d.gamma, gm1 = gam - 1.0;
+  for (int t = threadIdx.x; t < VOL_EPB * nnn; t += blockDim.x) {
+    const int le = t / nnn, node = t % nnn, e = e0 + le;
+    if (e >= d.nE) continue;
+    double Uv[5];
+    load_state<double>(d, U, e, node, Uv);
+    const double r = Uv[0], ir = 1.0 / r;
+    const double u = Uv[1] * ir, v = Uv[2] * ir, w = Uv[3] * ir;
+    const double p = gm1 * (Uv[4] - 0.5 * (Uv[1] * u + Uv[2] * v + Uv[3] * w));
+    if (!(r > 0.0) || !(p > 0.0) || !isfinite(Uv[4])) flag_set(d.flag, 1);
+    const int pn = pidx(node);
+    double *Pe = P + le * ADJ_NP * PS + pn;
+    Pe[0] = r; Pe[PS] = u; Pe[2 * PS] = v; Pe[3 * PS] = w; Pe[4 * PS] = 4.0 * p;
+    Pe[5 * PS] = VF == VF_PIR ? (Uv[4] + p) * ir : Uv[4] * ir;
+    const double miJ = -d.invJ[(size_t)e * nnn + node];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Lm[(le * 5 + k) * PS + pn] = miJ * lam[((size_t)e * 5 + k) * nnn + node];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < VOL_EPB * 3 * nn; t += blockDim.x) {
+    const int le = t / (3 * nn), r = t % (3 * nn), dir = r / nn, line = r % nn, e = e0 + le;
+    if (e >= d.nE) continue;
+    int pb, ps, gb, gs, a, b;
+    line_geom(dir, line, pb, ps, gb, gs, a, b);
+    adj_line<VF>(P + le * ADJ_NP * PS, Lm + le * 5 * PS, pb, ps, d.Ja + ((size_t)e * 3 + dir) * 3 * nnn, gb, gs,
+                 Acc + (le * 3 + dir) * ADJ_NP * PS);
+  }
+  __syncthreads();
+  const bool ns = d.equations == 1;
+  const double iR = 1.0 / d.R;
+  for (int t = threadIdx.x; t < VOL_EPB * nnn; t += blockDim.x) {
+    const int le = t / nnn, node = t % nnn, e = e0 + le;
+    if (e >= d.nE) continue;
+    const int ijk[3] = {node % n, (node / n) % n, node / nn};
+    const int pn = pidx(node);
+    const double *Pe = P + le * ADJ_NP * PS + pn;
+    const double r = Pe[0], u[3] = {Pe[PS], Pe[2 * PS], Pe[3 * PS]}, p = 0.25 * Pe[4 * PS], X = Pe[5 * PS];
+    double gp[6];
+#pragma unroll
+    for (int v = 0; v < 6; ++v)
+      gp[v] = Acc[(le * 3 + 0) * ADJ_NP * PS + v * PS + pn] + Acc[(le * 3 + 1) * ADJ_NP * PS + v * PS + pn] +
+              Acc[(le * 3 + 2) * ADJ_NP * PS + v * PS + pn];
+    const double ir = 1.0 / r;
+    double g_r = gp[0], g_u[3] = {gp[1], gp[2], gp[3]}, g_p = 4.0 * gp[4];
+    const double g_x = gp[5];
+    if (ns) {  // cotangents of (u, v, w, T) from the viscous adjoint, own part + the neighbours' face shares
+      double cw[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cw[q] = cotW[((size_t)e * 4 + q) * nnn + node];
+#pragma unroll
+      for (int dd = 0; dd < 3; ++dd) {
+        const int id = ijk[dd];
+        if (id != 0 && id != N) continue;
+        const int f = 2 * dd + (id == N ? 1 : 0);
+        const int pp = dd == 0 ? ijk[1] : ijk[0], qq = dd == 2 ? ijk[1] : ijk[2];
+        int nb, fnb, nbnode, nbpq;
+        neighbour_node(d, e, f, pp, qq, nb, fnb, nbnode, nbpq);
+        const double *sg = sigma + ((size_t)nb * 6 + fnb) * 4 * nn + nbpq;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cw[q] += sg[q * nn];
+      }
+      g_u[0] += cw[0];
+      g_u[1] += cw[1];
+      g_u[2] += cw[2];
+      g_p += cw[3] * ir * iR;         // T = p / (rho R)
+      g_r -= cw[3] * p * ir * ir * iR;
+    }
+    // chain to U = (rho, m, E): u = m / rho, p = (gamma-1)(E - |m|^2 / (2 rho)), X = h or e
+    const double q2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    double gU[5];
+    gU[0] = g_r - ir * (g_u[0] * u[0] + g_u[1] * u[1] + g_u[2] * u[2]) + g_p * gm1 * 0.5 * q2;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gU[1 + k] = ir * g_u[k] - g_p * gm1 * u[k];
+    gU[4] = g_p * gm1;
+    if (VF == VF_PIR) {  // h = (E + p) / rho
+      gU[0] += g_x * ir * (gm1 * 0.5 * q2 - X);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) gU[1 + k] -= g_x * ir * gm1 * u[k];
+      gU[4] += g_x * ir * gam;
+    } else {  // e = E / rho
+      gU[0] -= g_x * ir * X;
+      gU[4] += g_x * ir;
+    }
+    // advective surface terms: transposed Riemann-flux Jacobians in this element's face slots
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) {
+      const int id = ijk[dd];
+      if (id != 0 && id != N) continue;
+      const int f = 2 * dd + (id == N ? 1 : 0);
+      const int pq = (dd == 0 ? ijk[1] : ijk[0]) + n * (dd == 2 ? ijk[1] : ijk[2]);
+      const double *fs = fslots + ((size_t)e * 6 + f) * 5 * nn + pq;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) gU[v] += fs[v * nn];
+    }
+    const size_t gi = (size_t)e * 5 * nnn + node;
+    if (mode == 0) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) out[gi + v * nnn] = gU[v];
+    } else {  // reverse LSERK stage: Ubar += dt * VJP; gbar = A gbar + B Ubar (gbar is lam, read above)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double ub = out[gi + v * nnn] + dt * gU[v];
+        out[gi + v * nnn] = ub;
+        if (update_g) gbar[gi + v * nnn] = A * gbar[gi + v * nnn] + B * ub;
+      }
+    }
+  }
+}
+
+// gradient of the kinetic-energy integral sum_e sum_ijk w_i w_j w_k J rho |u|^2 / 2
+__global__ void __launch_bounds__(256) k_ke_grad(const DgDevice d, const double *__restrict__ U,
+                                                 double *__restrict__ grad) {
+  const long long total = (long long)d.nE * nnn;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const size_t e = (size_t)(t / nnn);
+    const int node = (int)(t % nnn);
+    const double wq = c_w[node % n] * c_w[(node / n) % n] * c_w[node / nn] * d.J[t];
+    const double *Ue = U + e * 5 * nnn + node;
+    const double ir = 1.0 / Ue[0];
+    const double u = Ue[nnn] * ir, v = Ue[2 * nnn] * ir, w = Ue[3 * nnn] * ir;
+    double *G = grad + e * 5 * nnn + node;
+    G[0] = -0.5 * wq * (u * u + v * v + w * w);
+    G[nnn] = wq * u;
+    G[2 * nnn] = wq * v;
+    G[3 * nnn] = wq * w;
+    G[4 * nnn] = 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------------
+void launch_adj_face(const DgDevice &d, const double *U, const double *lam, double *slots, cudaStream_t s) {
+  const long long pts = (long long)d.nF * nn;
+  const unsigned grid = (unsigned)((pts + 127) / 128);
+  switch (d.sflux) {
+    case SF_LLF: k_adj_face<SF_LLF><<<grid, 128, 0, s>>>(d, U, lam, slots); break;
+    case SF_ROE: k_adj_face<SF_ROE><<<grid, 128, 0, s>>>(d, U, lam, slots); break;
+    default: k_adj_face<SF_EC><<<grid, 128, 0, s>>>(d, U, lam, slots); break;
+  }
+}
+
+void launch_adj_visc(const DgDevice &d, const double *U, const double *lam, double *cotW, double *sigma,
+                     cudaStream_t s) {
+  const size_t smem = sizeof(double) * LIFT_EPB * ADJV_SLOTS * nnn;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_adj_visc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
+  k_adj_visc<<<(d.nE + LIFT_EPB - 1) / LIFT_EPB, LIFT_THREADS, smem, s>>>(d, U, lam, cotW, sigma);
+}
+
+template <int VF>
+void launch_adj_volume_t(const DgDevice &d, const double *U, const double *lam, const double *fslots,
+                         const double *cotW, const double *sigma, double *out, double *gbar, int mode, double dt,
+                         double A, double B, int update_g, cudaStream_t s) {
+  const size_t smem = sizeof(double) * VOL_EPB * ADJ_SLOTS * PS;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_adj_volume<VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
+  k_adj_volume<VF><<<(d.nE + VOL_EPB - 1) / VOL_EPB, VOL_THREADS, smem, s>>>(d, U, lam, fslots, cotW, sigma, out,
+                                                                            gbar, mode, dt, A, B, update_g);
+}
+
+void launch_adj_volume(const DgDevice &d, const double *U, const double *lam, const double *fslots,
+                       const double *cotW, const double *sigma, double *out, double *gbar, int mode, double dt,
+                       double A, double B, int update_g, cudaStream_t s) {
+  if (d.vflux == VF_KG)
+    launch_adj_volume_t<VF_KG>(d, U, lam, fslots, cotW, sigma, out, gbar, mode, dt, A, B, update_g, s);
+  else
+    launch_adj_volume_t<VF_PIR>(d, U, lam, fslots, cotW, sigma, out, gbar, mode, dt, A, B, update_g, s);
+}
+
+void launch_ke_grad(const DgDevice &d, const double *U, double *grad, cudaStream_t s) {
+  k_ke_grad<<<8 * 152, 256, 0, s>>>(d, U, grad);
+}
+
+}  // namespace

@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -31,8 +32,12 @@ const DgKernelTable *kernels_for(int N) {
 std::mutex g_upload_mutex;
 std::vector<unsigned> g_uploaded;  // bitmask of degrees per device
 
-enum KernelClass { KC_FACE = 0, KC_LIFT, KC_VOLUME, KC_INDICATOR, KC_SPREAD, KC_OTHER, KC_COUNT };
-const char *kKernelNames[KC_COUNT] = {"face", "lift", "volume", "indicator", "spread", "other"};
+enum KernelClass {
+  KC_FACE = 0, KC_LIFT, KC_VOLUME, KC_INDICATOR, KC_SPREAD, KC_OTHER, KC_ADJ_FACE, KC_ADJ_VISC, KC_ADJ_VOLUME,
+  KC_COUNT
+};
+const char *kKernelNames[KC_COUNT] = {"face",  "lift",     "volume",   "indicator", "spread",
+                                      "other", "adj_face", "adj_visc", "adj_volume"};
 
 // LSERK(5,4) of Carpenter and Kennedy, 2N-storage form (published coefficients)
 const double kA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
@@ -64,6 +69,8 @@ struct dg_ctx {
   double t_ms[KC_COUNT] = {0};
   long long t_count[KC_COUNT] = {0};
   size_t n_state = 0;          // doubles in U
+  // adjoint: library-owned state buffers (stage states, gbar, checkpoints), allocated on first use
+  std::vector<double *> adj_pool;
 };
 
 namespace {
@@ -144,6 +151,63 @@ dg_status stage(dg_ctx *c, const double *U, double *out, int mode, int st, doubl
 __global__ void k_fill(double *p, int count, double v) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < count) p[i] = v;
+}
+
+__global__ void k_scale(double *__restrict__ y, const double *__restrict__ x, double a, size_t count) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+
+// ---- discrete adjoint ----
+
+dg_status adjoint_supported(dg_ctx *c, const char *who) {
+  const DgDevice &d = c->d;
+  if (d.precision != DG_FP64 || d.shock_capturing || (d.vflux != DG_VFLUX_KG && d.vflux != DG_VFLUX_PIROZZOLI))
+    return fail(c, DG_ERR_UNSUPPORTED,
+                std::string(who) + ": the adjoint needs DG_FP64, no shock capturing and the KG or Pirozzoli volume flux");
+  return DG_OK;
+}
+
+// at least `count` library-owned state buffers in the adjoint pool
+dg_status adj_pool(dg_ctx *c, size_t count) {
+  while (c->adj_pool.size() < count) {
+    double *p = nullptr;
+    DG_TRY(dev_alloc(c, &p, c->n_state));
+    c->adj_pool.push_back(p);
+  }
+  return DG_OK;
+}
+
+// one vector-Jacobian product of L at U with cotangent lam (see DgKernelTable::adj_volume for modes);
+// the forward work buffers serve as scratch: Fsurf = face slots, Fv = cotW, Wsurf = sigma
+dg_status vjp(dg_ctx *c, const double *U, const double *lam, double *out, int mode, double dt, double A, double B,
+              int update_g) {
+  DgDevice &d = c->d;
+  DG_TRY(launch(c, KC_ADJ_FACE, [&] { c->K->adj_face(d, U, lam, d.Fsurf, c->stream); }));
+  if (d.equations == DG_NAVIER_STOKES)
+    DG_TRY(launch(c, KC_ADJ_VISC, [&] { c->K->adj_visc(d, U, lam, d.Fv, d.Wsurf, c->stream); }));
+  DG_TRY(launch(c, KC_ADJ_VOLUME, [&] {
+    c->K->adj_volume(d, U, lam, d.Fsurf, d.Fv, d.Wsurf, out, const_cast<double *>(lam), mode, dt, A, B, update_g,
+                     c->stream);
+  }));
+  return DG_OK;
+}
+
+dg_status copy_state(dg_ctx *c, double *dst, const double *src) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, sizeof(double) * c->n_state, cudaMemcpyDeviceToDevice, c->stream);
+  return e ? cuda_fail(c, e, "state copy") : DG_OK;
+}
+
+// reverse of one LSERK step from U; pool[0..3] = stage states 1..4, pool[4] = gbar
+dg_status step_vjp(dg_ctx *c, const double *U, double *Ubar, double dt) {
+  DG_TRY(adj_pool(c, 5));
+  double *S[5] = {const_cast<double *>(U), c->adj_pool[0], c->adj_pool[1], c->adj_pool[2], c->adj_pool[3]};
+  for (int st = 0; st < 4; ++st) DG_TRY(stage(c, S[st], S[st + 1], 1, st, dt));
+  double *gbar = c->adj_pool[4];
+  DG_TRY(launch(c, KC_OTHER, [&] { k_scale<<<8 * 152, 256, 0, c->stream>>>(gbar, Ubar, kB[4], c->n_state); }));
+  for (int st = 4; st >= 0; --st)
+    DG_TRY(vjp(c, S[st], gbar, Ubar, 1, dt, kA[st], st > 0 ? kB[st - 1] : 0.0, st > 0));
+  return DG_OK;
 }
 
 }  // namespace
@@ -353,6 +417,55 @@ dg_status dg_lserk_step_host(dg_ctx *c, double *U_host, double dt, double t) {
   if (!e) e = cudaStreamSynchronize(c->stream);
   if (e) return cuda_fail(c, e, "D2H");
   return DG_OK;
+}
+
+dg_status dg_rhs_vjp(dg_ctx *c, const double *U, const double *lambda, double *Ubar, double t) {
+  (void)t;
+  if (!c || !U || !lambda || !Ubar || Ubar == U || Ubar == lambda)
+    return fail(c, DG_ERR_ARG, "dg_rhs_vjp: null or aliased arrays");
+  DG_TRY(adjoint_supported(c, "dg_rhs_vjp"));
+  return vjp(c, U, lambda, Ubar, 0, 0.0, 0.0, 0.0, 0);
+}
+
+dg_status dg_lserk_step_vjp(dg_ctx *c, const double *U, double *Ubar, double dt, double t) {
+  (void)t;
+  if (!c || !U || !Ubar || U == Ubar || !std::isfinite(dt)) return fail(c, DG_ERR_ARG, "dg_lserk_step_vjp: bad argument");
+  DG_TRY(adjoint_supported(c, "dg_lserk_step_vjp"));
+  return step_vjp(c, U, Ubar, dt);
+}
+
+dg_status dg_lserk_steps_vjp(dg_ctx *c, const double *U0, double *Ubar, double dt, double t, int n_steps,
+                             int interval) {
+  (void)t;
+  if (!c || !U0 || !Ubar || U0 == Ubar || n_steps < 0 || interval < 1 || !std::isfinite(dt))
+    return fail(c, DG_ERR_ARG, "dg_lserk_steps_vjp: bad argument");
+  DG_TRY(adjoint_supported(c, "dg_lserk_steps_vjp"));
+  if (n_steps == 0) return DG_OK;
+  if (interval > n_steps) interval = n_steps;
+  const int ncp = (n_steps + interval - 1) / interval;
+  // pool: [0..4] step_vjp scratch, [5 .. 5+ncp) checkpoints, then interval-1 segment states
+  DG_TRY(adj_pool(c, 5 + (size_t)ncp + (size_t)interval - 1));
+  double **cp = c->adj_pool.data() + 5, **seg = cp + ncp;
+  DG_TRY(copy_state(c, cp[0], U0));
+  for (int j = 1; j < ncp; ++j) {
+    DG_TRY(copy_state(c, cp[j], cp[j - 1]));
+    DG_TRY(steps_impl(c, cp[j], dt, interval));
+  }
+  for (int j = ncp - 1; j >= 0; --j) {
+    const int len = std::min(interval, n_steps - j * interval);
+    auto state = [&](int i) { return i == 0 ? cp[j] : seg[i - 1]; };
+    for (int i = 1; i < len; ++i) {
+      DG_TRY(copy_state(c, state(i), state(i - 1)));
+      DG_TRY(steps_impl(c, state(i), dt, 1));
+    }
+    for (int i = len - 1; i >= 0; --i) DG_TRY(step_vjp(c, state(i), Ubar, dt));
+  }
+  return DG_OK;
+}
+
+dg_status dg_kinetic_energy_grad(dg_ctx *c, const double *U, double *grad) {
+  if (!c || !U || !grad || U == grad) return fail(c, DG_ERR_ARG, "dg_kinetic_energy_grad: bad argument");
+  return launch(c, KC_OTHER, [&] { c->K->ke_grad(c->d, U, grad, c->stream); });
 }
 
 dg_status dg_indicator(dg_ctx *c, const double *U, double *alpha) {

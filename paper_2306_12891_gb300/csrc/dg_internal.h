@@ -64,6 +64,17 @@ struct DgKernelTable {
   void (*invariants)(const DgDevice &d, const double *U, const double *Ut, double *out8_dev, cudaStream_t s);
   void (*max_dt)(const DgDevice &d, const double *U, double *out_dev, cudaStream_t s);
   void (*shadow)(const DgDevice &d, const double *U, cudaStream_t s);  // FP32 shadow of U (FP32-bulk)
+  // adjoint (FP64, no shock capturing): transposed Riemann-flux Jacobians into face slots
+  // [nE][6][5][n^2]; viscous adjoint into cotW [nE][4][n^3] (u, v, w, T) and sigma [nE][6][4][n^2];
+  // volume adjoint. mode 0: out = (dL/dU)^T lam. mode 1: reverse LSERK stage, out (= Ubar) += dt *
+  // VJP, then, if update_g, gbar (== lam) = A gbar + B Ubar.
+  void (*adj_face)(const DgDevice &d, const double *U, const double *lam, double *slots, cudaStream_t s);
+  void (*adj_visc)(const DgDevice &d, const double *U, const double *lam, double *cotW, double *sigma,
+                   cudaStream_t s);
+  void (*adj_volume)(const DgDevice &d, const double *U, const double *lam, const double *fslots, const double *cotW,
+                     const double *sigma, double *out, double *gbar, int mode, double dt, double A, double B,
+                     int update_g, cudaStream_t s);
+  void (*ke_grad)(const DgDevice &d, const double *U, double *grad, cudaStream_t s);  // d(kinetic energy)/dU
 };
 
 extern const DgKernelTable dg_kernels_n1, dg_kernels_n2, dg_kernels_n3, dg_kernels_n4, dg_kernels_n5,

@@ -1203,9 +1203,3 @@ void launch_max_dt(const DgDevice &d, const double *U, double *out, cudaStream_t
 }
 
 }  // namespace
-
-#define DG_CAT2(a, b) a##b
-#define DG_CAT(a, b) DG_CAT2(a, b)
-const DgKernelTable DG_CAT(dg_kernels_n, DG_N) = {
-    N,           upload,           launch_metrics, launch_face_normals, launch_face,  launch_lift,
-    launch_volume, launch_indicator, launch_spread,  launch_invariants,   launch_max_dt, launch_shadow};

@@ -1,3 +1,5 @@
-// Kernels of the split-form DGSEM right-hand side for polynomial degree N = 1.
+// Kernels of the split-form DGSEM right-hand side and its adjoint for polynomial degree N = 1.
 #define DG_N 1
 #include "dg_kernels.cuh"
+#include "dg_adjoint.cuh"
+#include "dg_table.cuh"

@@ -1,3 +1,5 @@
-// Kernels of the split-form DGSEM right-hand side for polynomial degree N = 6.
+// Kernels of the split-form DGSEM right-hand side and its adjoint for polynomial degree N = 6.
 #define DG_N 6
 #include "dg_kernels.cuh"
+#include "dg_adjoint.cuh"
+#include "dg_table.cuh"

@@ -83,6 +83,10 @@ def lib() -> ctypes.CDLL:
             "dg_basis": (i, [i, vp, vp, vp]),
             "dg_probe_fma": (i, [i, vp, vp]),
             "dg_invariants_noalloc": (i, [i, i, d, vp, vp, vp, vp, vp]),
+            "dg_rhs_vjp": (i, [vp, vp, vp, vp, d]),
+            "dg_lserk_step_vjp": (i, [vp, vp, vp, d, d]),
+            "dg_lserk_steps_vjp": (i, [vp, vp, vp, d, d, i, i]),
+            "dg_kinetic_energy_grad": (i, [vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -199,6 +203,35 @@ class DG:
         self._check(lib().dg_lserk_step_host(self._ctx, ctypes.c_void_p(ptr), float(dt), float(t)),
                     "dg_lserk_step_host")
         return U_host
+
+    # ------------------------------------------------------------------ adjoint
+    def rhs_vjp(self, U, lam, Ubar=None, t=0.0):
+        """Ubar = (dL/dU)(U)^T lam."""
+        if Ubar is None:
+            Ubar = self.torch.empty_like(U)
+        self._check(lib().dg_rhs_vjp(self._ctx, self._state(U), self._state(lam, "lambda"), self._state(Ubar, "Ubar"),
+                                     float(t)), "dg_rhs_vjp")
+        return Ubar
+
+    def lserk_step_vjp(self, U, Ubar, dt, t=0.0):
+        """In place: Ubar (cotangent after one step from U) -> cotangent of U."""
+        self._check(lib().dg_lserk_step_vjp(self._ctx, self._state(U), self._state(Ubar, "Ubar"), float(dt), float(t)),
+                    "dg_lserk_step_vjp")
+        return Ubar
+
+    def lserk_steps_vjp(self, U0, Ubar, dt, n_steps, interval=10, t=0.0):
+        """In place: Ubar (cotangent of U after n_steps from U0) -> cotangent of U0, with checkpoints
+        every `interval` steps."""
+        self._check(lib().dg_lserk_steps_vjp(self._ctx, self._state(U0), self._state(Ubar, "Ubar"), float(dt),
+                                             float(t), int(n_steps), int(interval)), "dg_lserk_steps_vjp")
+        return Ubar
+
+    def kinetic_energy_grad(self, U, grad=None):
+        if grad is None:
+            grad = self.torch.empty_like(U)
+        self._check(lib().dg_kinetic_energy_grad(self._ctx, self._state(U), self._state(grad, "grad")),
+                    "dg_kinetic_energy_grad")
+        return grad
 
     def indicator(self, U, alpha=None):
         if alpha is None:

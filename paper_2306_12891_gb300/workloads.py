@@ -19,6 +19,7 @@ from numpy.polynomial import legendre as _leg
 
 TWO_PI = 2.0 * math.pi
 BLAST_SEED = 20230622
+ADJOINT_SEED = 20230623  # perturbation of the Taylor-Green base state for the adjoint workload
 
 
 def lgl_points(N: int) -> np.ndarray:
@@ -240,6 +241,32 @@ def density_wave(xyz, t=0.0, gamma=1.4, amp=0.2):
     return cons_from_prim(rho, one, one, one, one, gamma)
 
 
+def smooth_field(xyz, rng, modes=4, terms=8):
+    """Seeded smooth periodic field on [0,2pi]^3: a sum of `terms` Fourier modes with integer
+    wavenumbers |k_i| <= modes (not all zero), random phases and amplitudes in [-1, 1], scaled to
+    max |f| = 1 over the nodes."""
+    x, y, z = xyz[:, 0], xyz[:, 1], xyz[:, 2]
+    f = np.zeros_like(x)
+    for _ in range(terms):
+        k = np.zeros(3, dtype=int)
+        while not k.any():
+            k = rng.integers(-modes, modes + 1, size=3)
+        f += rng.uniform(-1, 1) * np.sin(k[0] * x + k[1] * y + k[2] * z + rng.uniform(0, TWO_PI))
+    return f / max(np.abs(f).max(), 1e-300)
+
+
+def tgv_perturbed(xyz, seed=ADJOINT_SEED, amp=1e-2, modes=4, gamma=1.4, mach=0.1):
+    """Taylor-Green vortex plus a seeded smooth perturbation of (rho, u, v, w, p) from the lowest
+    `modes` Fourier modes: amplitude amp relative to rho0 = 1, U0 = 1 and rho0 U0^2."""
+    base = taylor_green(xyz, mach=mach, gamma=gamma)
+    rho = base[:, 0]
+    u, v, w = base[:, 1] / rho, base[:, 2] / rho, base[:, 3] / rho
+    p = (gamma - 1.0) * (base[:, 4] - 0.5 * rho * (u * u + v * v + w * w))
+    rng = np.random.default_rng(seed)
+    d = [amp * smooth_field(xyz, rng, modes) for _ in range(5)]
+    return cons_from_prim(rho + d[0], u + d[1], v + d[2], w + d[3], p + d[4], gamma)
+
+
 def random_smooth_state(xyz, seed, amp=0.05, gamma=1.4, modes=2):
     """Seeded smooth periodic perturbation of a rest state (for parity tests of generic fields)."""
     rng = np.random.default_rng(seed)
@@ -304,6 +331,8 @@ class Workload:
             return freestream(xyz, gamma=self.gamma)
         if self.initial == "density_wave":
             return density_wave(xyz, gamma=self.gamma)
+        if self.initial == "tgv_perturbed":
+            return tgv_perturbed(xyz, gamma=self.gamma)
         raise ValueError(self.initial)
 
     def physics(self) -> dict:
@@ -329,4 +358,9 @@ WORKLOADS = {
     "tgv_ns_n7_48x48x48_curved_fp32": Workload("tgv_ns_n7_48x48x48_curved_fp32", 7, (48, 48, 48), "ns",
                                                "pirozzoli", "roe", "tgv", mapping="sine_0.05",
                                                mu=1.0 / RE_TGV, precision="fp32_bulk", steps=1000, cfl=0.9),
+    # differentiation form: Navier-Stokes (Pirozzoli + Roe + BR1, curved), N=5, 24^3, perturbed TGV;
+    # gradient of the kinetic energy after 50 LSERK steps (checkpoints every 10 steps)
+    "tgv_ns_n5_24x24x24_adjoint": Workload("tgv_ns_n5_24x24x24_adjoint", 5, (24, 24, 24), "ns", "pirozzoli",
+                                           "roe", "tgv_perturbed", mapping="sine_0.05", mu=1.0 / RE_TGV,
+                                           steps=50, cfl=0.9),
 }
