@@ -152,11 +152,19 @@ dg_status dg_lserk_step_vjp(dg_ctx *ctx, const double *U, double *Ubar, double d
 
 /* Reverse of n_steps LSERK steps from U0 (unchanged) with two-level checkpointing: a forward sweep
  * stores the state every `interval` steps (ceil(n_steps/interval) buffers); each segment is then
- * recomputed once from its checkpoint, keeping its start states (interval buffers), and reversed
- * step by step with dg_lserk_step_vjp. On entry Ubar is the cotangent of U(n_steps), on exit that
- * of U0. Memory: ceil(n_steps/interval) + interval + 5 state buffers. Synchronising only on error. */
+ * recomputed once from its checkpoint and reversed step by step. On entry Ubar is the cotangent of
+ * U(n_steps), on exit that of U0. Memory: when 5 + ceil(n_steps/interval) + 5*interval state buffers
+ * fit with 10% of the device memory to spare, the recomputation keeps every stage state of the
+ * segment; otherwise it keeps the step start states (5 + ceil(n_steps/interval) + interval - 1
+ * buffers) and each step's stages are recomputed before it is reversed. Both give identical bits.
+ * Not synchronising (cudaMemGetInfo aside). */
 dg_status dg_lserk_steps_vjp(dg_ctx *ctx, const double *U0, double *Ubar, double dt, double t, int n_steps,
                              int interval);
+
+/* Budget in bytes for the state buffers of dg_lserk_steps_vjp (decides whether a segment's stage
+ * states are kept); 0 restores the default (free device memory less 10% of the total). Buffers
+ * already allocated are kept. */
+dg_status dg_adjoint_memory_limit(dg_ctx *ctx, double bytes);
 
 /* grad = d/dU of the kinetic-energy integral sum J w rho|u|^2/2 (out[6] of dg_invariants). */
 dg_status dg_kinetic_energy_grad(dg_ctx *ctx, const double *U, double *grad);

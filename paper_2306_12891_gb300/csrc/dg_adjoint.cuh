@@ -8,9 +8,9 @@
 // -(1/(2 w_b)) phi_nb for the neighbour's viscous flux, -1/J). With l = -lambda/J per node:
 //
 //   adj_face    per face point: c = s/w_0 (l_L - l_R) is the cotangent of F*(U_L, U_R, n); its
-//               transposed Jacobian goes to both sides' face slots. The Riemann solver is
-//               differentiated in forward mode (dual numbers, 5 seeds per pass, 2 passes) through
-//               the same templated code the forward kernel runs.
+//               transposed Jacobian goes to both sides' face slots. Roe and LLF: hand-written
+//               reverse mode of the forward statements; EC: forward-mode dual numbers (5 seeds per
+//               pass, 2 passes) through the same templated code the forward kernel runs.
 //   adj_visc    (Navier-Stokes) per element: recompute the lifted gradients; transpose the
 //               viscous divergence (D^T sweeps of l, neighbour term through the face), the
 //               contravariant projection and the Navier-Stokes-Fourier flux (pointwise), then the
@@ -26,6 +26,198 @@
 #include "dg_dual.cuh"
 
 namespace {
+
+// ---------------------------------------------------------------------------------------------
+// reverse-mode derivatives of the Riemann fluxes (the statements of riemann<double>, transposed)
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ double sgn_of(double x) { return x < 0.0 ? -1.0 : 1.0; }  // d|x|/dx, +1 at 0
+
+// primitives of one side: ir = 1/rho, u = m ir, p = (gamma-1)(E - |m|^2 ir / 2)
+struct Side {
+  double ir, u[3], p, un;
+};
+
+__device__ __forceinline__ Side side_of(const double U[5], const double nv[3], double gm1) {
+  Side s;
+  s.ir = 1.0 / U[0];
+  s.u[0] = U[1] * s.ir;
+  s.u[1] = U[2] * s.ir;
+  s.u[2] = U[3] * s.ir;
+  s.p = gm1 * (U[4] - 0.5 * (U[1] * s.u[0] + U[2] * s.u[1] + U[3] * s.u[2]));
+  s.un = s.u[0] * nv[0] + s.u[1] * nv[1] + s.u[2] * nv[2];
+  return s;
+}
+
+// cotangents of (u, p, un, ir) of one side -> cotangent of U (added to g)
+__device__ __forceinline__ void side_back(const double U[5], const Side &s, const double nv[3], double gm1,
+                                          double cu[3], double cp, double cun, double cir, double g[5]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) cu[k] += cun * nv[k];
+  // p = gm1 (E - |m|^2 ir / 2): dp/dE = gm1, dp/dm_k = -gm1 u_k, dp/dir = -gm1 |m|^2 / 2
+  g[4] += gm1 * cp;
+  const double m2 = U[1] * U[1] + U[2] * U[2] + U[3] * U[3];
+  cir -= 0.5 * gm1 * m2 * cp;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    g[1 + k] += cu[k] * s.ir - gm1 * s.u[k] * cp;
+    cir += cu[k] * U[1 + k];
+  }
+  g[0] -= cir * s.ir * s.ir;
+}
+
+// Euler flux F = (rho un, m un + p n, (E + p) un) of one side, reversed: adds dF^T cF to the side's
+// cotangents (cu, cp, cun) and to g directly
+__device__ __forceinline__ void flux_back(const double U[5], const Side &s, const double nv[3], const double cF[5],
+                                          double &cp, double &cun, double g[5]) {
+  cun += cF[0] * U[0] + cF[1] * U[1] + cF[2] * U[2] + cF[3] * U[3] + cF[4] * (U[4] + s.p);
+  cp += cF[1] * nv[0] + cF[2] * nv[1] + cF[3] * nv[2] + cF[4] * s.un;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) g[v] += cF[v] * s.un;
+}
+
+// gL = (dF*/dU_L)^T cF, gR = (dF*/dU_R)^T cF for the LLF flux
+__device__ void llf_vjp(const double UL[5], const double UR[5], const double nv[3], double gam, const double cF[5],
+                        double gL[5], double gR[5]) {
+  const double gm1 = gam - 1.0;
+  const Side L = side_of(UL, nv, gm1), R = side_of(UR, nv, gm1);
+  const double cL = sqrt(gam * L.p / UL[0]), cR = sqrt(gam * R.p / UR[0]);
+  const double aL = fabs(L.un) + cL, aR = fabs(R.un) + cR;
+  const bool rwins = aR > aL;  // the forward's max picks the right argument only when strictly larger
+  const double lam = rwins ? aR : aL;
+  double clam = 0.0, hF[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    hF[v] = 0.5 * cF[v];
+    gL[v] = 0.5 * lam * cF[v];
+    gR[v] = -0.5 * lam * cF[v];
+    clam -= 0.5 * cF[v] * (UR[v] - UL[v]);
+  }
+  double cuL[3] = {0, 0, 0}, cuR[3] = {0, 0, 0}, cpL = 0, cpR = 0, cunL = 0, cunR = 0, cirL = 0, cirR = 0;
+  flux_back(UL, L, nv, hF, cpL, cunL, gL);
+  flux_back(UR, R, nv, hF, cpR, cunR, gR);
+  // lam = |un_X| + sqrt(gamma p_X / rho_X) of the winning side X
+  if (rwins) {
+    cunR += clam * sgn_of(R.un);
+    cpR += clam * 0.5 * cR / R.p;
+    gR[0] -= clam * 0.5 * cR / UR[0];
+  } else {
+    cunL += clam * sgn_of(L.un);
+    cpL += clam * 0.5 * cL / L.p;
+    gL[0] -= clam * 0.5 * cL / UL[0];
+  }
+  side_back(UL, L, nv, gm1, cuL, cpL, cunL, cirL, gL);
+  side_back(UR, R, nv, gm1, cuR, cpR, cunR, cirR, gR);
+}
+
+// the same for Roe's flux (no entropy fix), statement by statement in reverse
+__device__ void roe_vjp(const double UL[5], const double UR[5], const double nv[3], double gam, const double cF[5],
+                        double gL[5], double gR[5]) {
+  const double gm1 = gam - 1.0;
+  const Side L = side_of(UL, nv, gm1), R = side_of(UR, nv, gm1);
+  // forward
+  const double sL = sqrt(UL[0]), sR = sqrt(UR[0]);
+  const double iw = 1.0 / (sL + sR);
+  double ut[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) ut[k] = (sL * L.u[k] + sR * R.u[k]) * iw;
+  const double EpL = UL[4] + L.p, EpR = UR[4] + R.p;
+  const double hL = EpL * L.ir, hR = EpR * R.ir;
+  const double Ht = (sL * hL + sR * hR) * iw;
+  const double q2 = ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2];
+  const double c2 = gm1 * (Ht - 0.5 * q2);
+  const double ct = sqrt(c2), ic2 = 1.0 / c2;
+  const double rt = sL * sR;
+  const double unt = ut[0] * nv[0] + ut[1] * nv[1] + ut[2] * nv[2];
+  const double dr = UR[0] - UL[0], dp = R.p - L.p;
+  const double du[3] = {R.u[0] - L.u[0], R.u[1] - L.u[1], R.u[2] - L.u[2]};
+  const double dun = du[0] * nv[0] + du[1] * nv[1] + du[2] * nv[2];
+  const double A1 = dp - rt * ct * dun, A5 = dp + rt * ct * dun;
+  const double a1 = 0.5 * A1 * ic2, a5 = 0.5 * A5 * ic2, a2 = dr - dp * ic2;
+  double dt[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) dt[k] = du[k] - dun * nv[k];
+  const double s1 = fabs(unt - ct), s5 = fabs(unt + ct), l2 = fabs(unt);
+  const double l1a1 = s1 * a1, l5a5 = s5 * a5, l2a2 = l2 * a2, l2r = l2 * rt;
+  const double utdt = ut[0] * dt[0] + ut[1] * dt[1] + ut[2] * dt[2];
+  // reverse: F = (FL + FR - D) / 2
+  double cD[5], hF[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) { cD[v] = -0.5 * cF[v]; hF[v] = 0.5 * cF[v]; }
+  double cnt = cD[1] * nv[0] + cD[2] * nv[1] + cD[3] * nv[2];  // sum_k cD_k n_k
+  double cut_dot = cD[1] * ut[0] + cD[2] * ut[1] + cD[3] * ut[2];
+  const double c_l1a1 = cD[0] + cut_dot - ct * cnt + cD[4] * (Ht - unt * ct);
+  const double c_l5a5 = cD[0] + cut_dot + ct * cnt + cD[4] * (Ht + unt * ct);
+  const double c_l2a2 = cD[0] + cut_dot + cD[4] * 0.5 * q2;
+  const double c_l2r = cD[1] * dt[0] + cD[2] * dt[1] + cD[3] * dt[2] + cD[4] * utdt;
+  const double sum15 = l1a1 + l5a5 + l2a2;
+  double c_ut[3], c_dt[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    c_ut[k] = cD[1 + k] * sum15 + cD[4] * l2r * dt[k];
+    c_dt[k] = (cD[1 + k] + cD[4] * ut[k]) * l2r;
+  }
+  double c_ct = (l5a5 - l1a1) * (cnt + cD[4] * unt);
+  double c_unt = cD[4] * ct * (l5a5 - l1a1);
+  double c_Ht = cD[4] * (l1a1 + l5a5);
+  double c_q2 = cD[4] * 0.5 * l2a2;
+  // products with the wave speeds
+  const double c_a1 = c_l1a1 * s1, c_a5 = c_l5a5 * s5, c_a2 = c_l2a2 * l2;
+  const double c_s1 = c_l1a1 * a1, c_s5 = c_l5a5 * a5;
+  const double c_l2 = c_l2a2 * a2 + c_l2r * rt;
+  double c_rt = c_l2r * l2;
+  const double g1 = sgn_of(unt - ct), g5 = sgn_of(unt + ct), g2 = sgn_of(unt);
+  c_unt += g1 * c_s1 + g5 * c_s5 + g2 * c_l2;
+  c_ct += -g1 * c_s1 + g5 * c_s5;
+  // tangential jump dt = du - dun n
+  double c_du[3];
+  double c_dun = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) { c_du[k] = c_dt[k]; c_dun -= c_dt[k] * nv[k]; }
+  // wave strengths
+  double c_dr = c_a2, c_dp = -c_a2 * ic2, c_ic2 = -c_a2 * dp;
+  c_dp += 0.5 * (c_a1 + c_a5) * ic2;
+  const double cdiff = 0.5 * (c_a5 - c_a1) * ic2;  // cotangent of rt ct dun
+  c_rt += cdiff * ct * dun;
+  c_ct += cdiff * rt * dun;
+  c_dun += cdiff * rt * ct;
+  c_ic2 += 0.5 * (c_a1 * A1 + c_a5 * A5);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) { c_du[k] += c_dun * nv[k]; c_ut[k] += c_unt * nv[k]; }
+  // Roe averages
+  double c_c2 = -c_ic2 * ic2 * ic2 + c_ct * 0.5 / ct;
+  c_Ht += gm1 * c_c2;
+  c_q2 -= 0.5 * gm1 * c_c2;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) c_ut[k] += 2.0 * ut[k] * c_q2;
+  double c_sL = c_rt * sR + c_Ht * hL * iw, c_sR = c_rt * sL + c_Ht * hR * iw;
+  double c_iw = c_Ht * (sL * hL + sR * hR);
+  const double c_hL = c_Ht * sL * iw, c_hR = c_Ht * sR * iw;
+  double cuL[3], cuR[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    c_sL += c_ut[k] * L.u[k] * iw;
+    c_sR += c_ut[k] * R.u[k] * iw;
+    c_iw += c_ut[k] * (sL * L.u[k] + sR * R.u[k]);
+    cuL[k] = c_ut[k] * sL * iw - c_du[k];
+    cuR[k] = c_ut[k] * sR * iw + c_du[k];
+  }
+  c_sL -= c_iw * iw * iw;
+  c_sR -= c_iw * iw * iw;
+  // enthalpies h = (E + p) ir
+  double cpL = -c_dp + c_hL * L.ir, cpR = c_dp + c_hR * R.ir;
+  double cirL = c_hL * EpL, cirR = c_hR * EpR;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) { gL[v] = 0.0; gR[v] = 0.0; }
+  gL[4] += c_hL * L.ir;
+  gR[4] += c_hR * R.ir;
+  gL[0] += -c_dr + c_sL * 0.5 / sL;
+  gR[0] += c_dr + c_sR * 0.5 / sR;
+  double cunL = 0.0, cunR = 0.0;
+  flux_back(UL, L, nv, hF, cpL, cunL, gL);
+  flux_back(UR, R, nv, hF, cpR, cunR, gR);
+  side_back(UL, L, nv, gm1, cuL, cpL, cunL, cirL, gL);
+  side_back(UR, R, nv, gm1, cuR, cpR, cunR, cirR, gR);
+}
 
 // ---------------------------------------------------------------------------------------------
 // adjoint of the face kernel
@@ -51,6 +243,21 @@ __global__ void __launch_bounds__(128) k_adj_face(const DgDevice d, const double
 #pragma unroll
   for (int v = 0; v < 5; ++v)
     cF[v] = sw * (iJR * lam[((size_t)eR * 5 + v) * nnn + nodeR] - iJL * lam[((size_t)eL * 5 + v) * nnn + nodeL]);
+  if (SF != SF_EC) {  // hand-written reverse mode
+    const double nv[3] = {nr[0], nr[nn], nr[2 * nn]};
+    double gL[5], gR[5];
+    if (SF == SF_ROE) roe_vjp(UL, UR, nv, d.gamma, cF, gL, gR);
+    else llf_vjp(UL, UR, nv, d.gamma, cF, gL, gR);
+    double *oL = slots + ((size_t)eL * 6 + fL) * 5 * nn + pq;
+    double *oR = slots + ((size_t)eR * 6 + fR) * 5 * nn + pqR;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      oL[k * nn] = gL[k];
+      oR[k * nn] = gR[k];
+    }
+    return;
+  }
+  // entropy-conservative flux: forward-mode dual numbers through riemann<>
   using D5 = Dual<5>;
   const D5 nv[3] = {D5(nr[0]), D5(nr[nn]), D5(nr[2 * nn])};
   const D5 gam(d.gamma), zero(0.0);

@@ -71,6 +71,7 @@ struct dg_ctx {
   size_t n_state = 0;          // doubles in U
   // adjoint: library-owned state buffers (stage states, gbar, checkpoints), allocated on first use
   std::vector<double *> adj_pool;
+  size_t adj_limit = 0;        // bytes the adjoint's state buffers may use (0: free memory less 10%)
 };
 
 namespace {
@@ -198,11 +199,9 @@ dg_status copy_state(dg_ctx *c, double *dst, const double *src) {
   return e ? cuda_fail(c, e, "state copy") : DG_OK;
 }
 
-// reverse of one LSERK step from U; pool[0..3] = stage states 1..4, pool[4] = gbar
-dg_status step_vjp(dg_ctx *c, const double *U, double *Ubar, double dt) {
-  DG_TRY(adj_pool(c, 5));
-  double *S[5] = {const_cast<double *>(U), c->adj_pool[0], c->adj_pool[1], c->adj_pool[2], c->adj_pool[3]};
-  for (int st = 0; st < 4; ++st) DG_TRY(stage(c, S[st], S[st + 1], 1, st, dt));
+// reverse of one LSERK step whose five stage input states are S[0..4] (gbar in pool[4]):
+// gbar = B_5 Ubar; for s = 5..1: Ubar += dt (dL/dU)(S[s-1])^T gbar; gbar = A_s gbar + B_(s-1) Ubar
+dg_status reverse_stages(dg_ctx *c, double *const S[5], double *Ubar, double dt) {
   double *gbar = c->adj_pool[4];
   DG_TRY(launch(c, KC_OTHER, [&] { k_scale<<<8 * 152, 256, 0, c->stream>>>(gbar, Ubar, kB[4], c->n_state); }));
   for (int st = 4; st >= 0; --st)
@@ -210,6 +209,13 @@ dg_status step_vjp(dg_ctx *c, const double *U, double *Ubar, double dt) {
   return DG_OK;
 }
 
+// reverse of one LSERK step from U, recomputing its four inner stage states into pool[0..3]
+dg_status step_vjp(dg_ctx *c, const double *U, double *Ubar, double dt) {
+  DG_TRY(adj_pool(c, 5));
+  double *S[5] = {const_cast<double *>(U), c->adj_pool[0], c->adj_pool[1], c->adj_pool[2], c->adj_pool[3]};
+  for (int st = 0; st < 4; ++st) DG_TRY(stage(c, S[st], S[st + 1], 1, st, dt));
+  return reverse_stages(c, S, Ubar, dt);
+}
 }  // namespace
 
 extern "C" {
@@ -443,9 +449,24 @@ dg_status dg_lserk_steps_vjp(dg_ctx *c, const double *U0, double *Ubar, double d
   if (n_steps == 0) return DG_OK;
   if (interval > n_steps) interval = n_steps;
   const int ncp = (n_steps + interval - 1) / interval;
-  // pool: [0..4] step_vjp scratch, [5 .. 5+ncp) checkpoints, then interval-1 segment states
-  DG_TRY(adj_pool(c, 5 + (size_t)ncp + (size_t)interval - 1));
+  // Keep all five stage states of a segment when they fit (HBM is large): the segment's
+  // recomputation then yields every state the reverse sweep needs. Otherwise keep only the step
+  // start states and recompute each step's stages before reversing it.
+  const size_t state_bytes = sizeof(double) * c->n_state;
+  const size_t have = c->adj_pool.size();
+  const size_t want_store = 5 + (size_t)ncp + 5 * (size_t)interval;
+  bool store;
+  if (c->adj_limit) {
+    store = want_store * state_bytes <= c->adj_limit;
+  } else {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const size_t extra = want_store > have ? (want_store - have) * state_bytes : 0;
+    store = extra + total_b / 10 < free_b;
+  }
+  DG_TRY(adj_pool(c, store ? want_store : 5 + (size_t)ncp + (size_t)interval - 1));
   double **cp = c->adj_pool.data() + 5, **seg = cp + ncp;
+  // forward sweep: checkpoints every `interval` steps
   DG_TRY(copy_state(c, cp[0], U0));
   for (int j = 1; j < ncp; ++j) {
     DG_TRY(copy_state(c, cp[j], cp[j - 1]));
@@ -453,13 +474,34 @@ dg_status dg_lserk_steps_vjp(dg_ctx *c, const double *U0, double *Ubar, double d
   }
   for (int j = ncp - 1; j >= 0; --j) {
     const int len = std::min(interval, n_steps - j * interval);
-    auto state = [&](int i) { return i == 0 ? cp[j] : seg[i - 1]; };
-    for (int i = 1; i < len; ++i) {
-      DG_TRY(copy_state(c, state(i), state(i - 1)));
-      DG_TRY(steps_impl(c, state(i), dt, 1));
+    if (store) {
+      // S(i, s): input state of stage s of step i of the segment; S(0, 0) is the checkpoint
+      auto S = [&](int i, int st) { return (i == 0 && st == 0) ? cp[j] : seg[5 * i + st]; };
+      for (int i = 0; i < len; ++i)
+        for (int st = 0; st < 5; ++st) {
+          if (i == len - 1 && st == 4) break;  // the segment's end state is not needed
+          double *out = st < 4 ? S(i, st + 1) : S(i + 1, 0);
+          DG_TRY(stage(c, S(i, st), out, 1, st, dt));
+        }
+      for (int i = len - 1; i >= 0; --i) {
+        double *st5[5] = {S(i, 0), S(i, 1), S(i, 2), S(i, 3), S(i, 4)};
+        DG_TRY(reverse_stages(c, st5, Ubar, dt));
+      }
+    } else {
+      auto state = [&](int i) { return i == 0 ? cp[j] : seg[i - 1]; };
+      for (int i = 1; i < len; ++i) {
+        DG_TRY(copy_state(c, state(i), state(i - 1)));
+        DG_TRY(steps_impl(c, state(i), dt, 1));
+      }
+      for (int i = len - 1; i >= 0; --i) DG_TRY(step_vjp(c, state(i), Ubar, dt));
     }
-    for (int i = len - 1; i >= 0; --i) DG_TRY(step_vjp(c, state(i), Ubar, dt));
   }
+  return DG_OK;
+}
+
+dg_status dg_adjoint_memory_limit(dg_ctx *c, double bytes) {
+  if (!c || !(bytes >= 0.0)) return fail(c, DG_ERR_ARG, "dg_adjoint_memory_limit: bad argument");
+  c->adj_limit = (size_t)bytes;
   return DG_OK;
 }
 

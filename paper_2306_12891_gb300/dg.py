@@ -87,6 +87,7 @@ def lib() -> ctypes.CDLL:
             "dg_lserk_step_vjp": (i, [vp, vp, vp, d, d]),
             "dg_lserk_steps_vjp": (i, [vp, vp, vp, d, d, i, i]),
             "dg_kinetic_energy_grad": (i, [vp, vp, vp]),
+            "dg_adjoint_memory_limit": (i, [vp, d]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -225,6 +226,10 @@ class DG:
         self._check(lib().dg_lserk_steps_vjp(self._ctx, self._state(U0), self._state(Ubar, "Ubar"), float(dt),
                                              float(t), int(n_steps), int(interval)), "dg_lserk_steps_vjp")
         return Ubar
+
+    def adjoint_memory_limit(self, nbytes: float = 0.0):
+        """Budget for the checkpointed adjoint's state buffers (0: default)."""
+        self._check(lib().dg_adjoint_memory_limit(self._ctx, float(nbytes)), "dg_adjoint_memory_limit")
 
     def kinetic_energy_grad(self, U, grad=None):
         if grad is None:

@@ -179,6 +179,13 @@ def test_checkpoint_schedules_agree(env):
         Ub = seed.clone()
         gpu.lserk_steps_vjp(U0, Ub, dt, K, interval)
         outs.append(Ub)
+    # a small memory budget: segment stage states are not kept, each step's stages are recomputed
+    gpu.adjoint_memory_limit(1.0)
+    for interval in (3, 7):
+        Ub = seed.clone()
+        gpu.lserk_steps_vjp(U0, Ub, dt, K, interval)
+        outs.append(Ub)
+    gpu.adjoint_memory_limit(0.0)
     # by hand: store every state, reverse step by step
     states = [U0.clone()]
     for _ in range(K):
