@@ -59,6 +59,22 @@ def volume_kernel_flops_per_element(N: int, navier_stokes: bool) -> float:
     return 45.0 * pairs + per_node * n ** 3 + per_face_pt * 6 * n * n
 
 
+def adjoint_volume_flops_per_element(N: int, navier_stokes: bool) -> float:
+    """Algorithmic FP64 flops of one adjoint-volume launch per element (FMA = 2 flops), counted from
+    the statements of the kernel:
+      pair (KG/Pirozzoli transposed): 9 sums, 5 pair cotangents c_v (2 mul + add = 15), V 5, F0 1,
+        d(c.F)/dF0 8, gV 1, gP 5, the six primitive cotangents 12, accumulation into both nodes 12
+        -> 67 per pair, 3 n^2 n(n-1)/2 pairs per element;
+      per node: primitives and l = -lambda/J 20, direction sum 12, chain to U 25, reverse LSERK 20,
+        Navier-Stokes: T chain 6 and the neighbours' face shares 4 per face point;
+      per face point: 5 additions of the face slots."""
+    n = N + 1
+    pairs = 3 * n * n * n * (n - 1) // 2
+    per_node = 20 + 12 + 25 + 20 + (6 if navier_stokes else 0)
+    per_face_pt = 5 + (4 if navier_stokes else 0)
+    return 67.0 * pairs + per_node * n ** 3 + per_face_pt * 6 * n * n
+
+
 def volume_kernel_bytes_per_element(N: int, navier_stokes: bool, real_bytes: int) -> float:
     """Algorithmic DRAM bytes of one volume-kernel launch per element in an LSERK stage after the
     first: U and the LSERK register g read and written (FP64), the metric terms Ja (real type),
@@ -217,6 +233,61 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+ADJOINT_WORKLOAD = "tgv_ns_n5_24x24x24_adjoint"
+
+
+def run_adjoint(stream, peak_fp64: float, interval: int = 10) -> dict:
+    """The differentiation form: gradient of the kinetic energy after K = 50 LSERK steps with
+    respect to the initial state (N = 5, 24^3, Navier-Stokes), through dg_kinetic_energy_grad and the
+    checkpointed dg_lserk_steps_vjp; timed with CUDA events against the forward run itself."""
+    import torch
+
+    from paper_2306_12891_gb300 import dg
+
+    w = WORKLOADS[ADJOINT_WORKLOAD]
+    xyz, faces = w.mesh()
+    s = dg.DG(w.N, xyz, faces, stream=stream, **w.physics())
+    U0 = torch.from_numpy(w.initial_state(xyz)).cuda()
+    dt = s.max_dt(U0, w.cfl)
+    K = w.steps
+
+    def gradient():
+        UK = s.lserk_steps(U0.clone(), dt, K)
+        g = s.kinetic_energy_grad(UK)
+        s.lserk_steps_vjp(U0, g, dt, K, interval)
+        return g
+
+    gradient()  # warm-up: allocates the checkpoint and stage buffers
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    s.lserk_steps(U0.clone(), dt, K)
+    ev[1].record(stream)
+    s.timing_enable(True)
+    s.timing_get()
+    ev[2].record(stream)
+    gradient()
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    kt = s.timing_get()
+    s.timing_enable(False)
+    s.check()
+    fwd_ms, grad_ms = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+    adj_ms, adj_n = kt.get("adj_volume", (0.0, 0))
+    flops = adjoint_volume_flops_per_element(w.N, True) * w.n_elems
+    achieved = flops / (adj_ms / adj_n * 1e-3) if adj_n else 0.0
+    total = sum(v[0] for v in kt.values())
+    return {"workload": ADJOINT_WORKLOAD, "N": w.N, "elements": w.n_elems, "dofs": w.dofs, "steps": K,
+            "checkpoint_interval": interval, "objective": "kinetic energy at step K (sum J w rho|u|^2/2)",
+            "forward_ms": fwd_ms, "gradient_ms": grad_ms, "gradient_over_forward": grad_ms / fwd_ms,
+            "value": w.dofs * STAGES * K / (grad_ms * 1e-3), "unit": "DOF-stage/s (reverse sweep incl. recomputation)",
+            "roofline": {"bound": "alu", "kernel": "adj_volume (transposed flux differencing, FP64 pipe)",
+                         "achieved": achieved / 1e12, "peak": peak_fp64 / 1e12, "unit": "TFLOP/s",
+                         "frac": achieved / peak_fp64, "traffic": None, "flops_per_launch": flops},
+            "kernels": {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / max(total, 1e-9), 4)}
+                        for k, v in kt.items() if v[1]}}
+
+
 def run_gpu(args):
     import torch
 
@@ -356,6 +427,8 @@ def run_gpu(args):
     }
     if fp32:
         line["fp32_bulk"] = fp32
+    if args.adjoint and not args.nel and world == 1:
+        line["adjoint"] = run_adjoint(stream, peak_fp64)
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -369,6 +442,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-fp32", dest="fp32", action="store_false", help="skip the FP32-bulk comparison")
+    ap.add_argument("--no-adjoint", dest="adjoint", action="store_false", help="skip the adjoint (gradient) block")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk"])
     ap.add_argument("--nel", type=int, default=None, help="elements per direction (default: the workload's 32)")
