@@ -123,14 +123,21 @@ def barrier(world):
 
 
 def max_over_ranks(world, x: float) -> float:
+    """Largest x over the ranks (the timed region ends when the slowest replica ends)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as td
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if td.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     td.all_reduce(t, op=td.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate(world: int, units_per_rank: float, seconds_per_rank: float) -> float:
+    """Whole-job throughput of `world` independent replicas: all ranks' units / the slowest rank's time."""
+    return world * units_per_rank / max_over_ranks(world, seconds_per_rank)
 
 
 class ClockSampler:

@@ -1,0 +1,46 @@
+"""The multi-GPU path of bench.py is replicas only (the hot path is not sharded in this build): every
+rank runs the whole workload, the ranks meet at barriers around the timed region, and the reported
+value is all ranks' units divided by the slowest rank's time. This exercises that host logic with
+world_size 2 on the gloo backend (CPU processes, no GPU)."""
+import os
+import socket
+
+import pytest
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    import torch.distributed as td
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    td.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+
+    bench.barrier(world)
+    seconds = 1.0 + rank  # rank 1 is the slower replica
+    m = bench.max_over_ranks(world, seconds)
+    value = bench.aggregate(world, 1000.0, seconds)
+    bench.barrier(world)
+    out.put((rank, m, value))
+    td.destroy_process_group()
+
+
+def test_two_replicas_gloo():
+    mp = pytest.importorskip("torch.multiprocessing")
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [r[1] for r in res] == [2.0, 2.0]            # both ranks see the slowest rank's time
+    assert [r[2] for r in res] == [1000.0, 1000.0]      # 2 x 1000 units / 2 s
