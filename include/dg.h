@@ -199,6 +199,13 @@ dg_status dg_basis(int N, double *xi, double *w, double *D);
  * `cuda_stream` (synchronising) and returns FLOP/s in *flops. */
 dg_status dg_probe_fma(int kind, void *cuda_stream, double *flops);
 
+/* Self-check of the library's integer-pipe float<->double conversions (used by the FP32-bulk
+ * epilogue) against the GPU's own conversions on `count` counter-generated bit patterns per
+ * direction, special values included. mismatches[0]: float->double, mismatches[1]: double->float
+ * (round to nearest even); by design float subnormals and doubles below 2^-126 in magnitude
+ * convert to zero and are not counted. Synchronising. */
+dg_status dg_check_conversions(void *cuda_stream, long long count, long long mismatches[2]);
+
 #ifdef __cplusplus
 }
 #endif

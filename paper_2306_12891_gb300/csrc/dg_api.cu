@@ -310,6 +310,17 @@ dg_status dg_init(const dg_mesh *mesh, int N, int nodes, const dg_params *prm, v
   d.alpha_min = prm->alpha_min; d.alpha_max = prm->alpha_max; d.sharpness = prm->sharpness;
   d.alpha_fixed = prm->alpha_fixed;
   d.p_ref = prm->precision == DG_FP32_BULK ? prm->p_ref : 0.0;
+  d.gm1 = d.gamma - 1.0;
+  d.iR = 1.0 / d.R;
+  d.href = d.p_ref * d.gamma / (d.gamma - 1.0);
+  d.eref = d.p_ref / (d.gamma - 1.0);
+  d.gamma_f = (float)d.gamma;
+  d.gm1_f = (float)d.gamma - 1.0f;
+  d.iR_f = 1.0f / (float)d.R;
+  d.p_ref_f = (float)d.p_ref;
+  d.href_f = (float)d.href;
+  d.mu_f = (float)d.mu;
+  d.kappa_f = (float)d.kappa;
   c->n_state = (size_t)nE * 5 * nnn;
   const bool fp32 = prm->precision == DG_FP32_BULK;
 

@@ -24,6 +24,11 @@ struct DgDevice {
   int equations, vflux, sflux, precision, shock_capturing;
   double gamma, R, mu, kappa, alpha_min, alpha_max, sharpness, alpha_fixed;
   double p_ref;        // reference pressure removed from the momentum flux (FP32-bulk only; 0 in FP64)
+  // per-context constants computed once on the host (the FP32 kernels would otherwise form them
+  // per thread on the FP64 pipe): gamma-1, 1/R, p_ref gamma/(gamma-1), p_ref/(gamma-1), and their
+  // FP32 roundings
+  double gm1, iR, href, eref;
+  float gamma_f, gm1_f, iR_f, p_ref_f, href_f, mu_f, kappa_f;
   // geometry (built at init)
   const double *xyz;   // [nE][3][n^3]  (init only)
   double *Ja;          // [nE][3 d][3 c][n^3]

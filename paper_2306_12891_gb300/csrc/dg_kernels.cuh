@@ -30,6 +30,7 @@
 
 #include <type_traits>
 
+#include "dg_convert.cuh"
 #include "dg_internal.h"
 
 #ifndef DG_N
@@ -74,6 +75,27 @@ template <> struct Tab<float> {
   static __device__ __forceinline__ float invw(int k) { return f_invw[k]; }
   static __device__ __forceinline__ float xi(int k) { return f_xi[k]; }
   static __device__ __forceinline__ float xh(int k) { return f_xh[k]; }
+};
+
+// per-context constants in the arithmetic type (precomputed on the host)
+template <typename R> struct Cst;
+template <> struct Cst<double> {
+  static __device__ __forceinline__ double gam(const DgDevice &d) { return d.gamma; }
+  static __device__ __forceinline__ double gm1(const DgDevice &d) { return d.gm1; }
+  static __device__ __forceinline__ double iR(const DgDevice &d) { return d.iR; }
+  static __device__ __forceinline__ double pref(const DgDevice &d) { return d.p_ref; }
+  static __device__ __forceinline__ double href(const DgDevice &d) { return d.href; }
+  static __device__ __forceinline__ double mu(const DgDevice &d) { return d.mu; }
+  static __device__ __forceinline__ double kappa(const DgDevice &d) { return d.kappa; }
+};
+template <> struct Cst<float> {
+  static __device__ __forceinline__ float gam(const DgDevice &d) { return d.gamma_f; }
+  static __device__ __forceinline__ float gm1(const DgDevice &d) { return d.gm1_f; }
+  static __device__ __forceinline__ float iR(const DgDevice &d) { return d.iR_f; }
+  static __device__ __forceinline__ float pref(const DgDevice &d) { return d.p_ref_f; }
+  static __device__ __forceinline__ float href(const DgDevice &d) { return d.href_f; }
+  static __device__ __forceinline__ float mu(const DgDevice &d) { return d.mu_f; }
+  static __device__ __forceinline__ float kappa(const DgDevice &d) { return d.kappa_f; }
 };
 
 // per-stage buffers and metric copies in the arithmetic type
@@ -165,7 +187,7 @@ __device__ __forceinline__ void load_state(const DgDevice &d, const double *__re
 // FP32 shadow of the state: Uf = float(U), with E' = E - p_ref/(gamma-1) formed in FP64 first
 __global__ void __launch_bounds__(256) k_shadow(const DgDevice d, const double *__restrict__ U) {
   const long long total = (long long)d.nE * 5 * nnn;
-  const double eref = d.p_ref / (d.gamma - 1.0);
+  const double eref = d.eref;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
     const int v = (int)((t / nnn) % 5);
     d.Uf[t] = (float)(v == 4 ? U[t] - eref : U[t]);
@@ -392,7 +414,7 @@ __global__ void __launch_bounds__(256) k_face(const DgDevice d, const double *__
   orient_map(o, p, q, p2, q2);
   const int nodeL = face_node(fL, p, q), nodeR = face_node(fR, p2, q2);
   const int pqR = p2 + n * q2;
-  const R pref = (R)d.p_ref, href = (R)(d.p_ref * d.gamma / (d.gamma - 1.0)), gam = (R)d.gamma;
+  const R pref = Cst<R>::pref(d), href = Cst<R>::href(d), gam = Cst<R>::gam(d);
   R UL[5], UR[5], nv[3];
   load_state<R>(d, U, eL, nodeL, UL);
   load_state<R>(d, U, eR, nodeR, UR);
@@ -418,7 +440,7 @@ __global__ void __launch_bounds__(256) k_face(const DgDevice d, const double *__
     R pL = gm1 * (UL[4] - R(0.5) * (UL[1] * wL[0] + UL[2] * wL[1] + UL[3] * wL[2]));
     R pR = gm1 * (UR[4] - R(0.5) * (UR[1] * wR[0] + UR[2] * wR[1] + UR[3] * wR[2]));
     if (kShift<R>) { pL += pref; pR += pref; }
-    const R iR = R(1) / (R)d.R;
+    const R iR = Cst<R>::iR(d);
     const R jump[4] = {R(0.5) * (wR[0] - wL[0]), R(0.5) * (wR[1] - wL[1]), R(0.5) * (wR[2] - wL[2]),
                        R(0.5) * (pR * irR - pL * irL) * iR};
     R *jL = Buf<R>::Wsurf(d) + ((size_t)eL * 6 + fL) * 4 * nn;
@@ -435,14 +457,17 @@ __global__ void __launch_bounds__(256) k_face(const DgDevice d, const double *__
 // BR1 lifting + viscous flux: grad w = (1/J)[sum_d Ja^d D_d w + sum_faces (1/w_b) s n_out (w* - w)],
 // then Fv^d = sum_c Ja^d_c Fv_c(U, grad w) stored per node (4 components: momentum, energy).
 // ---------------------------------------------------------------------------------------------
+// resident 256-thread CTAs per SM the register budget must allow: FP32 five (48 registers), FP64 three
+template <typename R> __host__ __device__ constexpr int lift_min_blocks() { return std::is_same<R, float>::value ? 5 : 3; }
+
 template <typename R>
-__global__ void __launch_bounds__(LIFT_THREADS) k_lift(const DgDevice d, const double *__restrict__ U) {
+__global__ void __launch_bounds__(LIFT_THREADS, lift_min_blocks<R>()) k_lift(const DgDevice d, const double *__restrict__ U) {
   __shared__ R W[LIFT_EPB][4][nnn];
   __shared__ R sD[n][n + 1];  // D, rows padded: lanes read different rows without bank conflicts
   for (int t = threadIdx.x; t < nn; t += blockDim.x) sD[t / n][t % n] = Tab<R>::D(t);
   const int e0 = blockIdx.x * LIFT_EPB;
-  const R gm1 = (R)(d.gamma - 1.0), iR = R(1) / (R)d.R;
-  const R pref = (R)d.p_ref;
+  const R gm1 = Cst<R>::gm1(d), iR = Cst<R>::iR(d);
+  const R pref = Cst<R>::pref(d);
   const R *Jab = Buf<R>::Ja(d);
   for (int t = threadIdx.x; t < LIFT_EPB * nnn; t += blockDim.x) {
     const int le = t / nnn, node = t % nnn, e = e0 + le;
@@ -459,7 +484,7 @@ __global__ void __launch_bounds__(LIFT_THREADS) k_lift(const DgDevice d, const d
     W[le][3][node] = p * ir * iR;
   }
   __syncthreads();
-  const R mu = (R)d.mu, kappa = (R)d.kappa;
+  const R mu = Cst<R>::mu(d), kappa = Cst<R>::kappa(d);
   for (int t = threadIdx.x; t < LIFT_EPB * nnn; t += blockDim.x) {
     const int le = t / nnn, node = t % nnn, e = e0 + le;
     if (e >= d.nE) continue;
@@ -726,9 +751,9 @@ __global__ void __launch_bounds__(vol_threads<R, SC>(), vol_min_blocks<R, SC>())
   R *Acc = P + VOL_EPB * NP * PS;         // [EPB][3][5][PS]
   R *AccT = Acc + VOL_EPB * 15 * PS;      // [EPB][5][nnn] (SC only)
   const int e0 = blockIdx.x * VOL_EPB;
-  const R gam = (R)d.gamma, gm1 = gam - R(1);
-  const R pref = (R)d.p_ref, href = (R)(d.p_ref * d.gamma / (d.gamma - 1.0));
-  const double eref = d.p_ref / (d.gamma - 1.0);
+  const R gam = Cst<R>::gam(d), gm1 = Cst<R>::gm1(d);
+  const R pref = Cst<R>::pref(d), href = Cst<R>::href(d);
+  const double eref = d.eref;
   const R *Jab = Buf<R>::Ja(d);
   const int vf = VF;
   // phase A: stage primitive quantities
@@ -892,6 +917,178 @@ __global__ void __launch_bounds__(vol_threads<R, SC>(), vol_min_blocks<R, SC>())
         const double un = U[gi + v * nnn] + B * gv;
         out[gi + v * nnn] = un;
         if (kShift<R>) d.Uf[gi + v * nnn] = (float)(v == 4 ? un - eref : un);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// FP32-bulk volume kernel without the blend: one thread per node. FP32 flux arithmetic is cheap on
+// this GPU, so the pair symmetry that halves the FP64 work is given up here: each thread forms
+// all 3(n-1) two-point fluxes of its node's lines and keeps its sums in registers, which removes
+// the partner accumulators and two block barriers of the line-per-thread layout, and the metric
+// terms are staged in shared memory with the primitives (one coalesced load per element).
+// ---------------------------------------------------------------------------------------------
+constexpr int NODE_EPB = nnn >= 256 ? 1 : 256 / nnn;
+constexpr int NODE_THREADS = round32(NODE_EPB * nnn);
+constexpr int NODE_SLOTS = 7 + 9 + 12;  // staged primitives, metric terms, contravariant viscous flux
+
+
+// scaled two-point flux of the staged nodes a and b through the metric sums Sj (see line_fluxdiff)
+template <int VF>
+__device__ __forceinline__ void pair_flux_f(const float *__restrict__ P, int a, int b, float Sjx, float Sjy,
+                                            float Sjz, float gam, float pref, float F[5]) {
+  const float ri = P[a], ui = P[PS + a], vi = P[2 * PS + a], wi = P[3 * PS + a];
+  const float rm = P[b], um = P[PS + b], vm = P[2 * PS + b], wm = P[3 * PS + b];
+  if (VF == VF_PIR || VF == VF_KG) {
+    const float Su = ui + um, Sv = vi + vm, Sw = wi + wm;
+    const float Vp = Su * Sjx + Sv * Sjy + Sw * Sjz;
+    F[0] = (ri + rm) * Vp;
+    const float Sp = P[4 * PS + a] + P[4 * PS + b];
+    F[1] = F[0] * Su + Sp * Sjx;
+    F[2] = F[0] * Sv + Sp * Sjy;
+    F[3] = F[0] * Sw + Sp * Sjz;
+    if (VF == VF_PIR) F[4] = F[0] * (P[5 * PS + a] + P[5 * PS + b]);
+    else F[4] = F[0] * (P[5 * PS + a] + P[5 * PS + b]) + (P[6 * PS + a] + P[6 * PS + b]) * Vp;
+  } else {
+    const float av[3] = {0.5f * Sjx, 0.5f * Sjy, 0.5f * Sjz};
+    if (VF == VF_EC) {
+      ec_flux<float>(ri, ui, vi, wi, P[6 * PS + a], rm, um, vm, wm, P[6 * PS + b], av, gam, pref, F);
+    } else {
+      const float Vi = ui * av[0] + vi * av[1] + wi * av[2], Vm = um * av[0] + vm * av[1] + wm * av[2];
+      const float pm2 = 0.125f * (P[4 * PS + a] + P[4 * PS + b]);
+      F[0] = 0.5f * (ri * Vi + rm * Vm);
+      F[1] = 0.5f * (ri * ui * Vi + rm * um * Vm) + pm2 * av[0];
+      F[2] = 0.5f * (ri * vi * Vi + rm * vm * Vm) + pm2 * av[1];
+      F[3] = 0.5f * (ri * wi * Vi + rm * wm * Vm) + pm2 * av[2];
+      F[4] = 0.5f * (P[5 * PS + a] * Vi + P[5 * PS + b] * Vm);
+    }
+  }
+}
+
+template <int VF>
+__global__ void __launch_bounds__(NODE_THREADS, 2) k_volume_f32(const DgDevice d, const double *U, double *out,
+                                                                 double *__restrict__ g, int mode, int first,
+                                                                 double dt, double A, double B) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  float *P = reinterpret_cast<float *>(sm_raw);  // [EPB][7][PS] staged primitives (as k_volume)
+  float *JS = P + NODE_EPB * 7 * PS;             // [EPB][9][PS] metric terms Ja^d_c, slot 3d + c
+  float *FS = JS + NODE_EPB * 9 * PS;            // [EPB][12][PS] contravariant viscous flux (NS)
+  const int e0 = blockIdx.x * NODE_EPB;
+  const float gam = d.gamma_f, gm1 = d.gm1_f, pref = d.p_ref_f;
+  const double eref = d.eref;
+  for (int t = threadIdx.x; t < NODE_EPB * nnn; t += blockDim.x) {
+    const int le = t / nnn, node = t % nnn, e = e0 + le;
+    if (e >= d.nE) continue;
+    float Uv[5];
+    load_state<float>(d, U, e, node, Uv);
+    const float r = Uv[0], ir = 1.0f / r;
+    const float u = Uv[1] * ir, v = Uv[2] * ir, w = Uv[3] * ir;
+    const float pm = gm1 * (Uv[4] - 0.5f * (Uv[1] * u + Uv[2] * v + Uv[3] * w));
+    const float p = pm + pref;
+    const float Et = Uv[4] + (float)eref;
+    if (!(r > 0.0f) || !(p > 0.0f) || !isfinite(Uv[4])) flag_set(d.flag, 1);
+    const int pn = pidx(node);
+    float *Pe = P + le * 7 * PS + pn;
+    Pe[0] = r; Pe[PS] = u; Pe[2 * PS] = v; Pe[3 * PS] = w; Pe[4 * PS] = 4.0f * pm;
+    if (VF == VF_PIR) Pe[5 * PS] = (Et + p) * ir;
+    else if (VF == VF_KG) { Pe[5 * PS] = Et * ir; Pe[6 * PS] = 2.0f * p; }
+    else if (VF == VF_EC) Pe[6 * PS] = p;
+    else Pe[5 * PS] = Et + p;
+    const float *Jn = d.Jaf + (size_t)e * 9 * nnn + node;
+    float *Je = JS + le * 9 * PS + pn;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Je[k * PS] = Jn[k * nnn];
+    if (d.equations == 1) {
+      const float *Fn = d.Fv_f + (size_t)e * 12 * nnn + node;
+      float *Fe = FS + le * 12 * PS + pn;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) Fe[k * PS] = Fn[k * nnn];
+    }
+  }
+  __syncthreads();
+  const bool ns = d.equations == 1;
+  const float *Fvb = d.Fv_f, *Fsb = d.Fsurf_f;
+  for (int t = threadIdx.x; t < NODE_EPB * nnn; t += blockDim.x) {
+    const int le = t / nnn, node = t % nnn, e = e0 + le;
+    if (e >= d.nE) continue;
+    const int ijk[3] = {node % n, (node / n) % n, node / nn};
+    const int pn = pidx(node);
+    const float *Pe = P + le * 7 * PS;
+    const float *Je = JS + le * 9 * PS;
+    float s[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) {
+      const int id = ijk[dd];
+      const int sp = dd == 0 ? 1 : dd == 1 ? (n + 1) : (n + 1) * n;  // padded stride along the line
+      const int pb = pn - id * sp;
+      const float jx = Je[(3 * dd) * PS + pn], jy = Je[(3 * dd + 1) * PS + pn], jz = Je[(3 * dd + 2) * PS + pn];
+#pragma unroll
+      for (int m = 0; m < n; ++m) {  // m = id contributes 0 (zero diagonal of the scaled tables)
+        const int am = pb + m * sp;
+        float F[5];
+        pair_flux_f<VF>(Pe, pn, am, jx + Je[(3 * dd) * PS + am], jy + Je[(3 * dd + 1) * PS + am],
+                        jz + Je[(3 * dd + 2) * PS + am], gam, pref, F);
+        if (VF == VF_PIR || VF == VF_KG) {
+          const float cq = f_Dq[id * n + m], ce = f_De[id * n + m];
+          s[0] += cq * F[0];
+#pragma unroll
+          for (int v = 1; v < 5; ++v) s[v] += ce * F[v];
+        } else {
+          const float c2 = f_D2[id * n + m];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) s[v] += c2 * F[v];
+        }
+      }
+      if (id == 0 || id == N) {  // surface term: (1/w_b) times the outward face flux
+        const int f = 2 * dd + (id == N ? 1 : 0);
+        const int pp = dd == 0 ? ijk[1] : ijk[0], qq = dd == 2 ? ijk[1] : ijk[2];
+        const float *fs = Fsb + ((size_t)e * 6 + f) * 5 * nn + pp + n * qq;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) s[v] += f_invw[id] * fs[v * nn];
+      }
+      if (ns) {
+        // viscous divergence along the line (zero diagonal: 2D/2 from the scaled table) and the
+        // neighbour's outward normal viscous flux -(1/(2 w_b)) phi_nb at the element faces
+        const float *Fvd = FS + (le * 12 + dd * 4) * PS + pb;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float acc = 0.0f;
+#pragma unroll
+          for (int m = 0; m < n; ++m) acc += 0.5f * f_D2[id * n + m] * Fvd[q * PS + m * sp];
+          s[1 + q] -= acc;
+        }
+        if (id == 0 || id == N) {
+          const int f = 2 * dd + (id == N ? 1 : 0);
+          const int pp = dd == 0 ? ijk[1] : ijk[0], qq = dd == 2 ? ijk[1] : ijk[2];
+          const int *ef = d.ef + ((size_t)e * 6 + f) * 4;
+          const int nb = ef[0], fnb = ef[1], o = ef[2];
+          int p2, q2;
+          orient_map(o, pp, qq, p2, q2);
+          const int nbnode = face_node(fnb, p2, q2);
+          const float sg = (fnb & 1) ? 0.5f : -0.5f;
+          const float *Fvn = Fvb + ((size_t)nb * 12 + (fnb >> 1) * 4) * nnn + nbnode;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) s[1 + q] += f_invw[id] * sg * Fvn[q * nnn];
+        }
+      }
+    }
+    // Jacobian and output / LSERK(5,4) stage in FP64
+    const double miJ = -d.invJ[(size_t)e * nnn + node];
+    const size_t gi = (size_t)e * 5 * nnn + node;
+    if (mode == 0) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) out[gi + v * nnn] = miJ * f2d_int(s[v]);
+    } else {
+      const double dtJ = dt * miJ;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double du = dtJ * f2d_int(s[v]);
+        const double gv = first ? du : A * g[gi + v * nnn] + du;
+        g[gi + v * nnn] = gv;
+        const double un = U[gi + v * nnn] + B * gv;
+        out[gi + v * nnn] = un;
+        d.Uf[gi + v * nnn] = d2f_int(v == 4 ? un - eref : un);
       }
     }
   }
@@ -1148,10 +1345,30 @@ void launch_volume_t(const DgDevice &d, const double *U, double *out, double *g,
                                                                                     B);
 }
 
+template <int VF>
+void launch_volume_f32(const DgDevice &d, const double *U, double *out, double *g, int mode, int first, double dt,
+                       double A, double B, cudaStream_t s) {
+  const size_t smem = sizeof(float) * NODE_EPB * NODE_SLOTS * PS;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_volume_f32<VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
+  k_volume_f32<VF><<<(d.nE + NODE_EPB - 1) / NODE_EPB, NODE_THREADS, smem, s>>>(d, U, out, g, mode, first, dt, A, B);
+}
+
 template <typename R>
 void launch_volume_r(const DgDevice &d, const double *U, double *out, double *g, int mode, int first, double dt,
                      double A, double B, cudaStream_t s) {
   const bool sc = d.shock_capturing != 0;
+  if (std::is_same<R, float>::value && !sc) {  // FP32-bulk without the blend: node-per-thread kernel
+    switch (d.vflux) {
+      case VF_KG: launch_volume_f32<VF_KG>(d, U, out, g, mode, first, dt, A, B, s); return;
+      case VF_PIR: launch_volume_f32<VF_PIR>(d, U, out, g, mode, first, dt, A, B, s); return;
+      case VF_EC: launch_volume_f32<VF_EC>(d, U, out, g, mode, first, dt, A, B, s); return;
+      default: launch_volume_f32<VF_CEN>(d, U, out, g, mode, first, dt, A, B, s); return;
+    }
+  }
   switch (d.vflux) {
     case VF_KG:
       if (sc) launch_volume_t<R, VF_KG, true>(d, U, out, g, mode, first, dt, A, B, s);

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/dg.h"
+#include "dg_convert.cuh"
 
 namespace {
 
@@ -52,7 +53,63 @@ dg_status run(cudaStream_t st, int iters, double *flops) {
   return DG_OK;
 }
 
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {  // splitmix64 finaliser
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// f2d_int / d2f_int against the hardware conversions on counter-generated bit patterns:
+// bad[0] = float->double mismatches (float subnormals excluded: they become zero by design),
+// bad[1] = double->float mismatches (inputs below 2^-126 in magnitude excluded: they become zero)
+__global__ void __launch_bounds__(256) k_check_conversions(unsigned long long count, unsigned long long *bad) {
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long h = mix64(i);
+    unsigned u = (unsigned)h;
+    if ((i & 15) == 0) u &= 0x807FFFFFu;                // exponent 0: zero and subnormals
+    if ((i & 15) == 1) u |= 0x7F800000u;                // exponent 255: infinities and NaNs
+    const float f = __uint_as_float(u);
+    const double rf = (double)f, gf = f2d_int(f);
+    const bool subn = ((u >> 23) & 0xFFu) == 0u && (u & 0x7FFFFFu) != 0u;
+    const bool okf = __double_as_longlong(rf) == __double_as_longlong(gf) || (isnan(rf) && isnan(gf));
+    if (!subn && !okf) atomicAdd(bad, 1ull);
+    // doubles with exponents around the float range (under- and overflow included)
+    unsigned long long b = mix64(i ^ 0x5DEECE66Dull);
+    const unsigned long long ex = 840ull + (b >> 55) % 330ull;
+    b = (b & 0x800FFFFFFFFFFFFFull) | (ex << 52);
+    if ((i & 7) == 1) b = (b & ~0x1FFFFFFFull) | 0x10000000ull;  // exactly halfway between two floats
+    if ((i & 7) == 2) b |= 0x7FF0000000000000ull;                // infinities and NaNs
+    const double x = __longlong_as_double((long long)b);
+    const float rd = __double2float_rn(x), gd = d2f_int(x);
+    const bool tiny = fabs(x) < 1.1754943508222875e-38;
+    const bool okd = __float_as_uint(rd) == __float_as_uint(gd) || (isnan(rd) && isnan(gd));
+    if (!tiny && !okd) atomicAdd(bad + 1, 1ull);
+  }
+}
+
 }  // namespace
+
+extern "C" dg_status dg_check_conversions(void *cuda_stream, long long count, long long mismatches[2]) {
+  if (!mismatches || count <= 0) return DG_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  unsigned long long *bad = nullptr;
+  if (cudaMalloc(&bad, 2 * sizeof(unsigned long long)) != cudaSuccess) return DG_ERR_OOM;
+  cudaMemsetAsync(bad, 0, 2 * sizeof(unsigned long long), st);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_check_conversions<<<sms * 8, 256, 0, st>>>((unsigned long long)count, bad);
+  unsigned long long h[2] = {0, 0};
+  cudaError_t e = cudaMemcpyAsync(h, bad, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  cudaFree(bad);
+  if (e != cudaSuccess) return DG_ERR_CUDA;
+  mismatches[0] = (long long)h[0];
+  mismatches[1] = (long long)h[1];
+  return DG_OK;
+}
 
 extern "C" dg_status dg_probe_fma(int kind, void *cuda_stream, double *flops) {
   if (!flops || (kind != 0 && kind != 1)) return DG_ERR_ARG;

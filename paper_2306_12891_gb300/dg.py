@@ -88,6 +88,7 @@ def lib() -> ctypes.CDLL:
             "dg_lserk_steps_vjp": (i, [vp, vp, vp, d, d, i, i]),
             "dg_kinetic_energy_grad": (i, [vp, vp, vp]),
             "dg_adjoint_memory_limit": (i, [vp, d]),
+            "dg_check_conversions": (i, [vp, ctypes.c_longlong, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -121,6 +122,16 @@ def probe_fma(kind: str = "fp64", stream=None) -> float:
     if st != DG_OK:
         raise DGError(st, "dg_probe_fma")
     return out.value
+
+
+def check_conversions(count: int = 1 << 24, stream=None):
+    """(float->double, double->float) mismatches of the library's integer-pipe conversions against
+    the GPU's own, on `count` generated bit patterns each."""
+    out = (ctypes.c_longlong * 2)()
+    st = lib().dg_check_conversions(_stream_ptr(stream), int(count), out)
+    if st != DG_OK:
+        raise DGError(st, "dg_check_conversions")
+    return int(out[0]), int(out[1])
 
 
 class DG:

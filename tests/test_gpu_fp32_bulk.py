@@ -146,3 +146,12 @@ def test_fp32_ten_steps_tgv(env):
     scale = flux_scale(U0, ref.Ja, ref.J, orc.dmatrix(w.N))
     print(f"PARITY32 tgv N=7 3^3 after {K} steps: Linf {linf} L2 {l2}; Linf/change {linf / change}")
     assert (linf <= 5 * K * TOL32 * dt * scale).all(), (linf, dt * scale)
+
+
+def test_integer_pipe_conversions(env):
+    """The FP32-bulk epilogue converts float <-> double on the integer pipes; it must agree bit for
+    bit with the GPU's own conversions (round to nearest even) outside the documented flush range."""
+    dg, orc, torch = env
+    bad = dg.check_conversions(1 << 24)
+    print(f"conversion mismatches (f2d, d2f) over 2^24 patterns each: {bad}")
+    assert bad == (0, 0)
