@@ -59,7 +59,8 @@ class _Problem(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("R", ctypes.c_double), ("mu", ctypes.c_double),
                 ("Pr", ctypes.c_double), ("shock_capturing", ctypes.c_int), ("alpha_min", ctypes.c_double),
                 ("alpha_max", ctypes.c_double), ("sharpness", ctypes.c_double),
-                ("alpha_fixed", ctypes.c_double)]
+                ("alpha_fixed", ctypes.c_double), ("wm_index", ctypes.c_int), ("wm_uinf", ctypes.c_double),
+                ("wm_mainf", ctypes.c_double), ("wm_van_driest", ctypes.c_int)]
 
 
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -96,6 +97,15 @@ def lib(complex_step: bool = False):
         L.orc_viscous_flux.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp]
         L.orc_lserk_generic.argtypes = [ctypes.c_int, vp, ctypes.c_double, ctypes.c_double, RHS_FN, vp]
         L.orc_lserk_coefficients.argtypes = [vp, vp, vp]
+        if not complex_step:
+            L.orc_spalding_yplus.restype = ctypes.c_double
+            L.orc_spalding_yplus.argtypes = [ctypes.c_double]
+            L.orc_wall_uplus.restype = ctypes.c_double
+            L.orc_wall_uplus.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
+            L.orc_van_driest.restype = ctypes.c_double
+            L.orc_van_driest.argtypes = [ctypes.c_double] * 5
+            L.orc_wall_utau.restype = ctypes.c_double
+            L.orc_wall_utau.argtypes = [ctypes.c_double] * 7 + [ctypes.c_int]
         _libs[complex_step] = L
     return _libs[complex_step]
 
@@ -173,6 +183,27 @@ def viscous_flux(U, gradU, gradT, mu, kappa, gamma=1.4):
     return Fv.reshape(3, 5)
 
 
+# ---------------------------------------------------------------- wall model (Sec. 3)
+
+def spalding_yplus(uplus: float) -> float:
+    return lib().orc_spalding_yplus(float(uplus))
+
+
+def wall_uplus(Re_h: float):
+    """(u+, Newton iterations) solving u+ y+(u+) = Re_h."""
+    it = ctypes.c_int(0)
+    return lib().orc_wall_uplus(float(Re_h), ctypes.byref(it)), it.value
+
+
+def van_driest(u, uinf, mainf, gamma=1.4, Pr=0.72) -> float:
+    return lib().orc_van_driest(float(u), float(uinf), float(mainf), float(gamma), float(Pr))
+
+
+def wall_utau(U, h, nu, uinf=1.0, mainf=0.0, gamma=1.4, Pr=0.72, van_driest_on=False) -> float:
+    return lib().orc_wall_utau(float(U), float(h), float(nu), float(uinf), float(mainf), float(gamma), float(Pr),
+                               int(bool(van_driest_on)))
+
+
 def lserk_coefficients():
     A, B, c = np.zeros(5), np.zeros(5), np.zeros(5)
     lib().orc_lserk_coefficients(_p(A), _p(B), _p(c))
@@ -201,7 +232,8 @@ class Oracle:
 
     def __init__(self, N, xyz, faces, equations="euler", vflux="kg", sflux="llf", gamma=1.4, R=1.0,
                  mu=0.0, Pr=0.72, shock_capturing=False, alpha_min=0.01, alpha_max=0.7,
-                 sharpness=DEFAULT_SHARPNESS, alpha_fixed=-1.0, complex_step=False):
+                 sharpness=DEFAULT_SHARPNESS, alpha_fixed=-1.0, wm_index=1, wm_uinf=1.0, wm_mainf=0.0,
+                 wm_van_driest=False, complex_step=False):
         self.cs = bool(complex_step)
         self._L = lib(self.cs)
         self._dtype = np.complex128 if self.cs else np.float64
@@ -223,6 +255,8 @@ class Oracle:
         pb.shock_capturing = int(bool(shock_capturing))
         pb.alpha_min, pb.alpha_max, pb.sharpness = alpha_min, alpha_max, sharpness
         pb.alpha_fixed = float(alpha_fixed)
+        pb.wm_index, pb.wm_uinf, pb.wm_mainf = int(wm_index), float(wm_uinf), float(wm_mainf)
+        pb.wm_van_driest = int(bool(wm_van_driest))
         self._pb = pb
         st = ctypes.c_int(0)
         self._s = self._L.orc_create(ctypes.byref(pb), ctypes.byref(st))

@@ -35,6 +35,7 @@
 #define R_SQRT csqrt
 #define R_LOG clog
 #define R_EXP cexp
+#define R_ASIN casin
 static orc_real R_ABS(orc_real x) { return creal(x) < 0.0 ? -x : x; }
 static orc_real R_MAX(orc_real a, orc_real b) { return creal(b) > creal(a) ? b : a; }
 #else
@@ -42,6 +43,7 @@ static orc_real R_MAX(orc_real a, orc_real b) { return creal(b) > creal(a) ? b :
 #define R_SQRT sqrt
 #define R_LOG log
 #define R_EXP exp
+#define R_ASIN asin
 #define R_ABS fabs
 #define R_MAX fmax
 #endif
@@ -412,6 +414,68 @@ void orc_viscous_flux(const orc_real U[5], const orc_real gradU[9], const orc_re
 }
 
 /* ======================================================================= */
+/* 4b. Wall model (Sec. 3)                                                  */
+/* ======================================================================= */
+
+/* Spalding's law of the wall (Eq. (2)): y+ = u+ + 0.1108 [exp(0.4 u+) - 1 - 0.4u+ - (0.4u+)^2/2!
+ * - (0.4u+)^3/3! - (0.4u+)^4/4!] */
+static orc_real spalding(orc_real up) {
+  orc_real k = 0.4 * up;
+  return up + 0.1108 * (R_EXP(k) - 1.0 - k - k * k / 2.0 - k * k * k / 6.0 - k * k * k * k / 24.0);
+}
+/* dy+/du+ */
+static orc_real spalding_d(orc_real up) {
+  orc_real k = 0.4 * up;
+  return 1.0 + 0.1108 * 0.4 * (R_EXP(k) - 1.0 - k - k * k / 2.0 - k * k * k / 6.0);
+}
+
+double orc_spalding_yplus(double uplus) {
+#ifdef ORC_COMPLEX_STEP
+  return creal(spalding(uplus));
+#else
+  return spalding(uplus);
+#endif
+}
+
+/* With y+ = h u_tau / nu and u+ = U / u_tau, Spalding's law becomes g(u+) = u+ y+(u+) - Re_h = 0
+ * with Re_h = h U / nu. g is increasing and convex for u+ > 0 and y+(u+) >= u+, so the root lies
+ * at or below sqrt(Re_h); Newton started at min(sqrt(Re_h), 60) decreases monotonically to it
+ * (or overshoots once from below when the root exceeds 60, Re_h > 1.7e11). */
+orc_real orc_wall_uplus(orc_real Re_h, int *iters) {
+  if (!(RE(Re_h) > 0.0)) { if (iters) *iters = 0; return 0.0; }
+  orc_real up = R_SQRT(Re_h);
+  if (RE(up) > 60.0) up = 60.0;
+  int it = 0;
+  for (; it < 100; ++it) {
+    orc_real g = up * spalding(up) - Re_h;
+    orc_real dg = spalding(up) + up * spalding_d(up);
+    orc_real step = g / dg;
+    up = up - step;
+    if (fabs(RE(step)) <= 1e-15 * fabs(RE(up))) { ++it; break; }
+  }
+  if (iters) *iters = it;
+  return up;
+}
+
+/* van Driest transform with freestream edge values (Eq. (5)):
+ * u_eq = (u_inf / b) asin(b u / u_inf), b = sqrt(r m) / sqrt(1 + r m), m = (gamma-1)/2 Ma_inf^2,
+ * recovery factor r = Pr^(1/3) */
+orc_real orc_van_driest(orc_real u, double uinf, double mainf, double gamma, double Pr) {
+  double m = 0.5 * (gamma - 1.0) * mainf * mainf * cbrt(Pr);
+  double b = sqrt(m) / sqrt(1.0 + m);
+  if (!(b > 0.0) || !(uinf > 0.0)) return u;
+  return uinf / b * R_ASIN(b * u / uinf);
+}
+
+orc_real orc_wall_utau(orc_real U, double h, orc_real nu, double uinf, double mainf, double gamma, double Pr,
+                       int van_driest) {
+  orc_real ueq = van_driest ? orc_van_driest(U, uinf, mainf, gamma, Pr) : U;
+  if (!(RE(ueq) > 0.0)) return 0.0;
+  orc_real up = orc_wall_uplus(h * ueq / nu, NULL);
+  return ueq / up;
+}
+
+/* ======================================================================= */
 /* 5. Solver state                                                          */
 /* ======================================================================= */
 
@@ -459,6 +523,14 @@ orc_state *orc_create(const orc_problem *pb, int *status) {
   for (int f = 0; f < s->nF; ++f) {
     const int *F = pb->faces + 5 * f;
     int eL = F[0], fL = F[1], eR = F[2], fR = F[3], o = F[4];
+    if (eR == -1) { /* wall face: one slot, the wall model imposes the boundary condition */
+      if (eL < 0 || eL >= nE || fL < 0 || fL > 5 || fR != ORC_BC_WALL_MODEL || s->slot_face[eL * 6 + fL] >= 0 ||
+          pb->wm_index < 1 || pb->wm_index > pb->N) {
+        orc_destroy(s); *status = -2; return NULL;
+      }
+      s->slot_face[eL * 6 + fL] = f; s->slot_side[eL * 6 + fL] = 0; s->slot_nbelem[eL * 6 + fL] = -1;
+      continue;
+    }
     if (eL < 0 || eL >= nE || eR < 0 || eR >= nE || fL < 0 || fL > 5 || fR < 0 || fR > 5 || o < 0 || o > 7 ||
         s->slot_face[eL * 6 + fL] >= 0 || s->slot_face[eR * 6 + fR] >= 0) {
       orc_destroy(s); *status = -2; return NULL;
@@ -511,6 +583,17 @@ static void load_grad(const orc_state *s, int e, int node, orc_real gU[9], orc_r
   for (int c = 0; c < 3; ++c) gT[c] = s->grad[(((size_t)e * 4 + 3) * 3 + c) * s->nnn + node];
 }
 
+/* mirror image of U about the plane with normal direction a (any length): the momentum's normal
+ * component changes sign, density and energy stay */
+static void wall_ghost(const orc_real U[5], const double a[3], orc_real G[5]) {
+  double s = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+  double nh[3] = {a[0] / s, a[1] / s, a[2] / s};
+  orc_real mn = U[1] * nh[0] + U[2] * nh[1] + U[3] * nh[2];
+  G[0] = U[0];
+  for (int c = 0; c < 3; ++c) G[1 + c] = U[1 + c] - 2.0 * mn * nh[c];
+  G[4] = U[4];
+}
+
 /* lifted variables w = (u, v, w, T), T = p/(rho R) */
 static void lifted_vars(const orc_state *s, const orc_real U[5], orc_real wv[4]) {
   orc_real rho, u[3], p;
@@ -558,12 +641,17 @@ static void lift_element(orc_state *s, const orc_real *U, int e) {
     for (int q = 0; q < n; ++q)
       for (int p = 0; p < n; ++p) {
         int node = face_node(N, f, p, q);
-        int nbnode = s->slot_nbnode[((size_t)e * 6 + f) * s->nn + p + n * q];
         orc_real Unb[5], wnb[4];
         double a[3];
-        load_state(s, U, nb, nbnode, Unb);
-        lifted_vars(s, Unb, wnb);
         load_metric(s, e, d, node, a);
+        if (nb < 0) { /* wall: ghost state mirrored about the wall, same temperature */
+          orc_real Ui[5];
+          load_state(s, U, e, node, Ui);
+          wall_ghost(Ui, a, Unb);
+        } else {
+          load_state(s, U, nb, s->slot_nbnode[((size_t)e * 6 + f) * s->nn + p + n * q], Unb);
+        }
+        lifted_vars(s, Unb, wnb);
         for (int qv = 0; qv < 4; ++qv) {
           orc_real wown = wv[qv * nnn + node];
           orc_real wstar = 0.5 * (wown + wnb[qv]);
@@ -630,6 +718,7 @@ int orc_indicator(orc_state *s, const orc_real *U, orc_real *alpha_raw, orc_real
   for (int e = 0; e < s->nE; ++e) {
     orc_real a = alpha_raw[e];
     for (int f = 0; f < 6; ++f) {
+      if (s->slot_nbelem[e * 6 + f] < 0) continue;
       orc_real b = 0.5 * alpha_raw[s->slot_nbelem[e * 6 + f]];
       if (RE(b) > RE(a)) a = b;
     }
@@ -737,6 +826,58 @@ static void fv_element(const orc_state *s, const orc_real *U, int e, orc_real *a
 /* 9. Right-hand side                                                       */
 /* ======================================================================= */
 
+/* Surface fluxes of a wall-modelled wall face (Sec. 3) into the slot of element e, face f:
+ *  - advective: the Riemann flux against the mirror state (no penetration);
+ *  - viscous (Navier-Stokes): the wall shear stress of the wall model, tau_w = rho u_tau^2,
+ *    against the tangential velocity at the exchange node (wm_index nodes from the wall along the
+ *    element's wall-normal line, distance h = |x_exchange - x_wall|, nu = mu / rho there), with an
+ *    adiabatic wall at rest (no energy flux). */
+static void wall_face(orc_state *s, const orc_real *U, int e, int f) {
+  const orc_problem *pb = &s->pb;
+  int N = s->N, n = s->n, nn = s->nn, nnn = s->nnn;
+  int d = f / 2, side = f % 2, sgn = side ? 1 : -1;
+  int ns = pb->equations == ORC_NAVIER_STOKES;
+  for (int q = 0; q < n; ++q)
+    for (int p = 0; p < n; ++p) {
+      int node = face_node(N, f, p, q);
+      int ijk[3];
+      nsplit(n, node, ijk);
+      orc_real Ui[5], Ug[5], Fa[5];
+      double a[3], nh[3];
+      load_state(s, U, e, node, Ui);
+      load_metric(s, e, d, node, a);
+      double sa = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+      for (int c = 0; c < 3; ++c) nh[c] = sgn * a[c] / sa;
+      wall_ghost(Ui, a, Ug);
+      orc_riemann(pb->sflux, Ui, Ug, nh, pb->gamma, Fa);
+      for (int v = 0; v < NVAR; ++v) s->Gadv[(((size_t)e * 6 + f) * NVAR + v) * nn + p + n * q] = sa * Fa[v];
+      if (!ns) continue;
+      int t[3] = {ijk[0], ijk[1], ijk[2]};
+      t[d] = side ? N - pb->wm_index : pb->wm_index;
+      int xnode = njoin(n, t);
+      orc_real Ux[5], rho, u[3], pr;
+      load_state(s, U, e, xnode, Ux);
+      primitive(Ux, pb->gamma, &rho, u, &pr);
+      double h = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        double dx = pb->xyz[((size_t)e * 3 + c) * nnn + xnode] - pb->xyz[((size_t)e * 3 + c) * nnn + node];
+        h += dx * dx;
+      }
+      h = sqrt(h);
+      orc_real un = u[0] * nh[0] + u[1] * nh[1] + u[2] * nh[2];
+      orc_real ut[3] = {u[0] - un * nh[0], u[1] - un * nh[1], u[2] - un * nh[2]};
+      orc_real Ut = R_SQRT(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
+      orc_real Fv[5] = {0, 0, 0, 0, 0};
+      if (RE(Ut) > 0.0) {
+        orc_real utau = orc_wall_utau(Ut, h, pb->mu / rho, pb->wm_uinf, pb->wm_mainf, pb->gamma, pb->Pr,
+                                      pb->wm_van_driest);
+        orc_real tau = rho * utau * utau;
+        for (int c = 0; c < 3; ++c) Fv[1 + c] = -tau * ut[c] / Ut; /* outward viscous flux: drag */
+      }
+      for (int v = 0; v < NVAR; ++v) s->Gvis[(((size_t)e * 6 + f) * NVAR + v) * nn + p + n * q] = sa * Fv[v];
+    }
+}
+
 int orc_rhs(orc_state *s, const orc_real *U, orc_real *Ut, const unsigned char *out_mask, orc_real *alpha_out) {
   const orc_problem *pb = &s->pb;
   int N = s->N, n = s->n, nn = s->nn, nnn = s->nnn, nE = s->nE;
@@ -748,7 +889,8 @@ int orc_rhs(orc_state *s, const orc_real *U, orc_real *Ut, const unsigned char *
   for (int e = 0; e < nE; ++e) {
     if (!need[e]) continue;
     near[e] = 1;
-    for (int f = 0; f < 6; ++f) near[s->slot_nbelem[e * 6 + f]] = 1;
+    for (int f = 0; f < 6; ++f)
+      if (s->slot_nbelem[e * 6 + f] >= 0) near[s->slot_nbelem[e * 6 + f]] = 1;
   }
 
   /* 1. blending coefficient (indicator on the element and its neighbours) */
@@ -762,6 +904,7 @@ int orc_rhs(orc_state *s, const orc_real *U, orc_real *Ut, const unsigned char *
       if (!need[e]) continue;
       orc_real a = s->alpha_raw[e];
       for (int f = 0; f < 6; ++f) {
+        if (s->slot_nbelem[e * 6 + f] < 0) continue;
         orc_real b = 0.5 * s->alpha_raw[s->slot_nbelem[e * 6 + f]];
         if (RE(b) > RE(a)) a = b;
       }
@@ -778,6 +921,10 @@ int orc_rhs(orc_state *s, const orc_real *U, orc_real *Ut, const unsigned char *
   for (int f = 0; f < s->nF; ++f) {
     const int *F = pb->faces + 5 * f;
     int eL = F[0], fL = F[1], eR = F[2], fR = F[3], o = F[4];
+    if (eR < 0) {
+      if (need[eL]) wall_face(s, U, eL, fL);
+      continue;
+    }
     if (!need[eL] && !need[eR]) continue;
     int dL = fL / 2, sgnL = (fL % 2) ? 1 : -1;
     for (int q = 0; q < n; ++q)

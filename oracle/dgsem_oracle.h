@@ -47,6 +47,7 @@ typedef double orc_real;
 enum { ORC_EULER = 0, ORC_NAVIER_STOKES = 1 };
 enum { ORC_VF_KG = 0, ORC_VF_PIROZZOLI = 1, ORC_VF_EC = 2, ORC_VF_CENTRAL = 3 };
 enum { ORC_SF_LLF = 0, ORC_SF_ROE = 1, ORC_SF_EC = 2 };
+enum { ORC_BC_WALL_MODEL = 0 };
 
 typedef struct {
   int N;
@@ -61,6 +62,12 @@ typedef struct {
   int shock_capturing; /* 0/1: DG/FV blend with the modal indicator */
   double alpha_min, alpha_max, sharpness;
   double alpha_fixed;  /* >= 0: blend with this coefficient on every element instead */
+  /* wall-modelled walls (faces with elemR = -1, faceR = ORC_BC_WALL_MODEL; Sec. 3): the wall shear
+   * stress comes from Spalding's law at the exchange node wm_index nodes away from the wall, with
+   * the input velocity mapped by the van Driest transform when wm_van_driest != 0 */
+  int wm_index;
+  double wm_uinf, wm_mainf;
+  int wm_van_driest;
 } orc_problem;
 
 /* Opaque precomputed state (basis, metrics, connectivity). */
@@ -85,6 +92,16 @@ void orc_riemann(int kind, const orc_real UL[5], const orc_real UR[5], const dou
 /* gradU[r][c] = d u_r / d x_c, gradT[c]; Fv[c][v] = viscous flux in Cartesian direction c */
 void orc_viscous_flux(const orc_real U[5], const orc_real gradU[9], const orc_real gradT[3],
                       double mu, double kappa, double gamma, orc_real Fv[15]);
+
+/* ---- wall model (Sec. 3, Eq. (2) Spalding's law of the wall, Eq. (5) van Driest transform) ---- */
+double orc_spalding_yplus(double uplus);                 /* y+ of u+ */
+/* u+ solving u+ * y+(u+) = Re_h = h U / nu (Newton, monotone from above); *iters = iterations used */
+orc_real orc_wall_uplus(orc_real Re_h, int *iters);
+/* equivalent incompressible velocity of u (Eq. (5)); u itself when mainf == 0 */
+orc_real orc_van_driest(orc_real u, double uinf, double mainf, double gamma, double Pr);
+/* friction velocity at wall distance h for tangential speed U and kinematic viscosity nu */
+orc_real orc_wall_utau(orc_real U, double h, orc_real nu, double uinf, double mainf, double gamma, double Pr,
+                       int van_driest);
 
 /* ---- solver ---- */
 orc_state *orc_create(const orc_problem *pb, int *status);

@@ -45,12 +45,17 @@ def _curved_tgv(x, y, z):
 MAPPINGS = {None: None, "none": None, "sine_0.05": _curved_tgv}
 
 
-def box_mesh(N: int, nel, lo=(0.0, 0.0, 0.0), hi=(TWO_PI, TWO_PI, TWO_PI), mapping=None):
+WALL = -1  # elemR of a wall-modelled boundary face (faceR = 0, the wall-model kind)
+
+
+def box_mesh(N: int, nel, lo=(0.0, 0.0, 0.0), hi=(TWO_PI, TWO_PI, TWO_PI), mapping=None, z_walls=False):
     """Periodic box of nel = (nx, ny, nz) hexahedra with degree-N LGL nodes.
 
     Returns (xyz, faces). Node coordinates along each axis are lo + (e + s_i) h with
     s = (1 + xi)/2, so the two elements sharing a face hold bit-identical face nodes.
     `mapping` (a name in MAPPINGS or a callable (x, y, z) -> (x', y', z')) curves the mesh.
+    z_walls: the planes z = lo and z = hi are wall-modelled walls (a channel) instead of periodic:
+    their faces are (elem, local face, -1, 0, 0).
     """
     nx, ny, nz = (int(v) for v in nel)
     if min(nx, ny, nz) < 1:
@@ -83,6 +88,13 @@ def box_mesh(N: int, nel, lo=(0.0, 0.0, 0.0), hi=(TWO_PI, TWO_PI, TWO_PI), mappi
     faces[0::3] = np.stack([e, np.full(nE, 1), eid(ex + 1, ey, ez), np.full(nE, 0), np.zeros(nE, int)], 1)
     faces[1::3] = np.stack([e, np.full(nE, 3), eid(ex, ey + 1, ez), np.full(nE, 2), np.zeros(nE, int)], 1)
     faces[2::3] = np.stack([e, np.full(nE, 5), eid(ex, ey, ez + 1), np.full(nE, 4), np.zeros(nE, int)], 1)
+    if z_walls:
+        top = faces[2::3][:, 0] // (nx * ny) == nz - 1  # z-faces that would wrap around
+        zf = faces[2::3].copy()
+        zf[top, 2:] = (WALL, 0, 0)
+        bottom = np.stack([e[ez == 0], np.full(int((ez == 0).sum()), 4), np.full(int((ez == 0).sum()), WALL),
+                           np.zeros(int((ez == 0).sum()), int), np.zeros(int((ez == 0).sum()), int)], 1)
+        faces = np.concatenate([faces[0::3], faces[1::3], zf, bottom]).astype(np.int32)
     return xyz, faces
 
 
