@@ -45,6 +45,8 @@ enum { DG_SFLUX_LLF = 0, DG_SFLUX_ROE = 1, DG_SFLUX_EC = 2 };
 /* DG_FP64: all arithmetic FP64. DG_FP32_BULK: volume/surface/lifting arithmetic in FP32 with FP32
  * accumulation; LSERK state, metrics, Jacobian scaling and reductions stay FP64. U, Ut stay FP64. */
 enum { DG_FP64 = 0, DG_FP32_BULK = 1 };
+/* boundary kinds (faceR of a face with elemR = -1) */
+enum { DG_BC_WALL_MODEL = 0 };
 /* Legendre-Gauss-Lobatto nodes (Sec. 2), the only node set */
 enum { DG_NODES_LGL = 0 };
 
@@ -59,7 +61,8 @@ typedef struct {
                          local faces 0:xi-, 1:xi+, 2:eta-, 3:eta+, 4:zeta-, 5:zeta+;
                          face point (p,q) = the two tangential node indices in increasing
                          dimension order; orient maps L's (p,q) to R's:
-                         (a,b) = bit2 ? (q,p) : (p,q); a = N-a if bit0; b = N-b if bit1 */
+                         (a,b) = bit2 ? (q,p) : (p,q); a = N-a if bit0; b = N-b if bit1.
+                         A boundary face has elemR = -1, faceR = its DG_BC_* kind, orient 0. */
 } dg_mesh;
 
 typedef struct {
@@ -77,6 +80,16 @@ typedef struct {
                               pressure term of the momentum flux. Exact: its contribution is p_ref times the
                               discrete metric identity, zero. Set it near the mean pressure (e.g. p0 of a
                               low-Mach flow) so FP32 forms p - p_ref from O(1) numbers; 0 disables it. */
+  /* Wall-modelled walls (Sec. 3): faces with elemR = -1 and faceR = DG_BC_WALL_MODEL. The advective
+   * flux is the Riemann flux against the mirror state (no penetration), the BR1 face value uses the
+   * same mirror state, and the viscous flux through the wall is the wall shear stress
+   * tau_w = rho u_tau^2 against the tangential velocity at the exchange node (wm_index nodes from the
+   * wall along the element's wall-normal line, 1 <= wm_index <= N): u_tau from Spalding's law of the
+   * wall (Sec. 3, Eq. (2)), the input velocity mapped by the van Driest transform (Eq. (5), freestream
+   * speed wm_uinf and Mach number wm_mainf) when wm_van_driest != 0; adiabatic wall at rest. */
+  int wm_index;
+  double wm_uinf, wm_mainf;
+  int wm_van_driest;
 } dg_params;
 
 /* Build a solver for `mesh` at polynomial degree N (1..7) with `nodes` = DG_NODES_LGL.
@@ -141,6 +154,8 @@ dg_status dg_invariants_noalloc(int N, int n_elems, double gamma, const double *
  * use (DG_ERR_OOM if that fails) and kept until dg_free. All arrays are device arrays
  * [n_elems][5][n]^3 on the context stream; asynchronous unless stated. ---- */
 
+/* (Meshes with wall faces are not supported by the adjoint: DG_ERR_UNSUPPORTED.) */
+
 /* Ubar = (dL/dU)(U)^T lambda. Ubar must overlap neither U nor lambda. */
 dg_status dg_rhs_vjp(dg_ctx *ctx, const double *U, const double *lambda, double *Ubar, double t);
 
@@ -198,6 +213,14 @@ dg_status dg_basis(int N, double *xi, double *w, double *D);
 /* Measure the GPU's FMA throughput: kind 0 = FP64, 1 = FP32. Runs a bounded FMA-chain kernel on
  * `cuda_stream` (synchronising) and returns FLOP/s in *flops. */
 dg_status dg_probe_fma(int kind, void *cuda_stream, double *flops);
+
+/* The wall model alone, for n wall points (device arrays; asynchronous on cuda_stream):
+ * utau[i] = friction velocity for tangential speed U[i] at wall distance h[i] and kinematic viscosity
+ * nu[i] -- the root of u+ y+(u+) = h U / nu for Spalding's y+(u+) (Sec. 3, Eq. (2)), by Newton from
+ * min(sqrt(h U / nu), 60), at most 100 iterations -- with U first mapped by the van Driest transform
+ * (Eq. (5)) when van_driest != 0. iters (nullable) receives the Newton iterations per point. */
+dg_status dg_wall_model(int n, const double *U, const double *h, const double *nu, double uinf, double mainf,
+                        double gamma, double Pr, int van_driest, double *utau, int *iters, void *cuda_stream);
 
 /* Self-check of the library's integer-pipe float<->double conversions (used by the FP32-bulk
  * epilogue) against the GPU's own conversions on `count` counter-generated bit patterns per

@@ -163,9 +163,10 @@ __global__ void k_scale(double *__restrict__ y, const double *__restrict__ x, do
 
 dg_status adjoint_supported(dg_ctx *c, const char *who) {
   const DgDevice &d = c->d;
-  if (d.precision != DG_FP64 || d.shock_capturing || (d.vflux != DG_VFLUX_KG && d.vflux != DG_VFLUX_PIROZZOLI))
-    return fail(c, DG_ERR_UNSUPPORTED,
-                std::string(who) + ": the adjoint needs DG_FP64, no shock capturing and the KG or Pirozzoli volume flux");
+  if (d.precision != DG_FP64 || d.shock_capturing || d.n_walls ||
+      (d.vflux != DG_VFLUX_KG && d.vflux != DG_VFLUX_PIROZZOLI))
+    return fail(c, DG_ERR_UNSUPPORTED, std::string(who) +
+                ": the adjoint needs DG_FP64, no shock capturing, no wall faces and the KG or Pirozzoli volume flux");
   return DG_OK;
 }
 
@@ -266,22 +267,38 @@ dg_status dg_init(const dg_mesh *mesh, int N, int nodes, const dg_params *prm, v
   if (!(prm->gamma > 1.0) || !(prm->R > 0.0) || !(prm->mu >= 0.0) || !(prm->Pr > 0.0)) return DG_ERR_ARG;
   if (!std::isfinite(prm->p_ref) || prm->p_ref < 0.0) return DG_ERR_ARG;
   const int nE = mesh->n_elems, nF = mesh->n_faces, n = N + 1, nn = n * n, nnn = nn * n;
-  if ((long long)nF * 2 != (long long)nE * 6) return DG_ERR_MESH;
 
-  // element-face connectivity: every (element, local face) slot used exactly once
+  // element-face connectivity: every (element, local face) slot used exactly once; a wall face
+  // (elemR = -1) fills one slot: (-1, boundary kind, 0, face id)
   std::vector<int> ef((size_t)nE * 24, -1);
+  std::vector<char> used((size_t)nE * 6, 0);
+  int n_walls = 0;
   for (int f = 0; f < nF; ++f) {
     const int *F = mesh->face + 5 * f;
     const int eL = F[0], fL = F[1], eR = F[2], fR = F[3], o = F[4];
+    if (eR == -1) {
+      if (eL < 0 || eL >= nE || fL < 0 || fL > 5 || fR != DG_BC_WALL_MODEL || used[(size_t)eL * 6 + fL])
+        return DG_ERR_MESH;
+      if (prm->wm_index < 1 || prm->wm_index > N) return DG_ERR_ARG;
+      used[(size_t)eL * 6 + fL] = 1;
+      int *sL = &ef[((size_t)eL * 6 + fL) * 4];
+      sL[0] = -1; sL[1] = fR; sL[2] = 0; sL[3] = f;
+      ++n_walls;
+      continue;
+    }
     if (eL < 0 || eL >= nE || eR < 0 || eR >= nE || fL < 0 || fL > 5 || fR < 0 || fR > 5 || o < 0 || o > 7)
       return DG_ERR_MESH;
     int *sL = &ef[((size_t)eL * 6 + fL) * 4], *sR = &ef[((size_t)eR * 6 + fR) * 4];
-    if (sL[0] >= 0 || sR[0] >= 0 || (eL == eR && fL == fR)) return DG_ERR_MESH;
+    if (used[(size_t)eL * 6 + fL] || used[(size_t)eR * 6 + fR] || (eL == eR && fL == fR)) return DG_ERR_MESH;
+    used[(size_t)eL * 6 + fL] = used[(size_t)eR * 6 + fR] = 1;
     // inverse orientation: a transposed map swaps the roles of the two flip bits
     const int inv = (o & 4) ? (4 | ((o & 1) << 1) | ((o & 2) >> 1)) : o;
     sL[0] = eR; sL[1] = fR; sL[2] = o; sL[3] = f;
     sR[0] = eL; sR[1] = fL; sR[2] = inv; sR[3] = f;
   }
+  for (char u : used)
+    if (!u) return DG_ERR_MESH;
+  if (n_walls && !(prm->wm_uinf >= 0.0 && prm->wm_mainf >= 0.0)) return DG_ERR_ARG;
 
   dg_ctx *c = new dg_ctx();
   c->N = N;
@@ -321,13 +338,24 @@ dg_status dg_init(const dg_mesh *mesh, int N, int nodes, const dg_params *prm, v
   d.href_f = (float)d.href;
   d.mu_f = (float)d.mu;
   d.kappa_f = (float)d.kappa;
+  d.n_walls = n_walls;
+  d.wm_index = prm->wm_index;
+  d.wm_vd = prm->wm_van_driest ? 1 : 0;
+  d.wm_uinf = prm->wm_uinf;
+  {
+    const double m = 0.5 * (prm->gamma - 1.0) * prm->wm_mainf * prm->wm_mainf * std::cbrt(prm->Pr);
+    d.wm_b = std::sqrt(m) / std::sqrt(1.0 + m);  // van Driest transform (Sec. 3, Eq. (5))
+  }
   c->n_state = (size_t)nE * 5 * nnn;
   const bool fp32 = prm->precision == DG_FP32_BULK;
 
   double *xyz = nullptr;
   int *face = nullptr;
   dg_status s = DG_OK;
-#define DG_ALLOC(p, cnt) if (s == DG_OK) s = dev_alloc(c, &(p), (size_t)(cnt))
+#define DG_ALLOC(p, cnt) \
+  do {                        \
+    if (s == DG_OK) s = dev_alloc(c, &(p), (size_t)(cnt)); \
+  } while (0)
   DG_ALLOC(xyz, (size_t)nE * 3 * nnn);
   DG_ALLOC(face, (size_t)nF * 5);
   DG_ALLOC(d.ef, (size_t)nE * 24);
@@ -350,6 +378,14 @@ dg_status dg_init(const dg_mesh *mesh, int N, int nodes, const dg_params *prm, v
     if (prm->equations == DG_NAVIER_STOKES) {
       DG_ALLOC(d.Wsurf, (size_t)nE * 6 * 4 * nn);
       DG_ALLOC(d.Fv, (size_t)nE * 12 * nnn);
+    }
+  }
+  if (n_walls && prm->equations == DG_NAVIER_STOKES) {  // wall model: exchange distances and wall fluxes
+    DG_ALLOC(d.hwm, (size_t)nF * nn);
+    if (fp32) {
+      DG_ALLOC(d.Fwall_f, (size_t)nF * 4 * nn);
+    } else {
+      DG_ALLOC(d.Fwall, (size_t)nF * 4 * nn);
     }
   }
   DG_ALLOC(d.alpha_raw, (size_t)nE);

@@ -29,6 +29,14 @@ struct DgDevice {
   // FP32 roundings
   double gm1, iR, href, eref;
   float gamma_f, gm1_f, iR_f, p_ref_f, href_f, mu_f, kappa_f;
+  // wall-modelled walls (faces with elemR = -1; Sec. 3): exchange node index, van Driest on/off
+  // with b = sqrt(r m)/sqrt(1 + r m), m = (gamma-1)/2 Ma_inf^2, r = Pr^(1/3), and freestream speed
+  int n_walls;         // number of wall faces (0: fully periodic)
+  int wm_index, wm_vd;
+  double wm_uinf, wm_b;
+  double *hwm;         // [nF][n^2] wall distance of the exchange node (wall faces only)
+  double *Fwall;       // [nF][4][n^2] outward wall-model viscous flux s F_v.n (momentum, energy), wall faces
+  float *Fwall_f;      // FP32-bulk version
   // geometry (built at init)
   const double *xyz;   // [nE][3][n^3]  (init only)
   double *Ja;          // [nE][3 d][3 c][n^3]

@@ -32,6 +32,7 @@
 
 #include "dg_convert.cuh"
 #include "dg_internal.h"
+#include "dg_wall.cuh"
 
 #ifndef DG_N
 #error "define DG_N before including dg_kernels.cuh"
@@ -104,6 +105,7 @@ template <> struct Buf<double> {
   static __device__ __forceinline__ double *Fsurf(const DgDevice &d) { return d.Fsurf; }
   static __device__ __forceinline__ double *Wsurf(const DgDevice &d) { return d.Wsurf; }
   static __device__ __forceinline__ double *Fv(const DgDevice &d) { return d.Fv; }
+  static __device__ __forceinline__ double *Fwall(const DgDevice &d) { return d.Fwall; }
   static __device__ __forceinline__ const double *Ja(const DgDevice &d) { return d.Ja; }
   static __device__ __forceinline__ const double *nrm(const DgDevice &d) { return d.nrm; }
 };
@@ -111,6 +113,7 @@ template <> struct Buf<float> {
   static __device__ __forceinline__ float *Fsurf(const DgDevice &d) { return d.Fsurf_f; }
   static __device__ __forceinline__ float *Wsurf(const DgDevice &d) { return d.Wsurf_f; }
   static __device__ __forceinline__ float *Fv(const DgDevice &d) { return d.Fv_f; }
+  static __device__ __forceinline__ float *Fwall(const DgDevice &d) { return d.Fwall_f; }
   static __device__ __forceinline__ const float *Ja(const DgDevice &d) { return d.Jaf; }
   static __device__ __forceinline__ const float *nrm(const DgDevice &d) { return d.nrm_f; }
 };
@@ -147,6 +150,16 @@ __device__ __forceinline__ int pidx(int node) {  // padded staging index of node
 
 __device__ __forceinline__ int face_node(int f, int p, int q) {
   const int b = (f & 1) ? N : 0;
+  switch (f >> 1) {
+    case 0: return b + n * (p + n * q);
+    case 1: return p + n * (b + n * q);
+    default: return p + n * (q + n * b);
+  }
+}
+
+// the wall-model exchange node: `k` nodes from face f along the element's line through face point (p, q)
+__device__ __forceinline__ int exchange_node(int f, int p, int q, int k) {
+  const int b = (f & 1) ? N - k : k;
   switch (f >> 1) {
     case 0: return b + n * (p + n * q);
     case 1: return p + n * (b + n * q);
@@ -387,6 +400,16 @@ __global__ void __launch_bounds__(256) k_face_normals(const DgDevice d) {
   o[nn] = a[1] * is;
   o[2 * nn] = a[2] * is;
   o[3 * nn] = s;
+  if (d.face[5 * f + 2] < 0 && d.hwm) {  // wall face: distance of the wall-model exchange node
+    const int xnode = exchange_node(fL, p, q, d.wm_index);
+    double h2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double dx = d.xyz[((size_t)eL * 3 + c) * nnn + xnode] - d.xyz[((size_t)eL * 3 + c) * nnn + node];
+      h2 += dx * dx;
+    }
+    d.hwm[(size_t)f * nn + pq] = sqrt(h2);
+  }
 }
 
 // FP32 roundings of the FP64 metric terms and face normals (FP32-bulk path)
@@ -401,6 +424,61 @@ __global__ void __launch_bounds__(256) k_round_geometry(const DgDevice d) {
 }
 
 // ---------------------------------------------------------------------------------------------
+// wall-modelled wall face point (Sec. 3): advective flux against the mirror state, BR1 jump to the
+// mirror state's face value, and the wall shear stress of the wall model as the viscous flux
+// ---------------------------------------------------------------------------------------------
+template <typename R, int SF>
+__device__ __forceinline__ void wall_face(const DgDevice &d, const double *__restrict__ U, int f, int pq, int eL,
+                                          int fL, R pref, R href, R gam) {
+  const int p = pq % n, q = pq / n;
+  const int node = face_node(fL, p, q);
+  R UL[5], UG[5], nv[3], Fs[5];
+  load_state<R>(d, U, eL, node, UL);
+  const R *nr = Buf<R>::nrm(d) + (size_t)f * 4 * nn + pq;
+  nv[0] = nr[0];
+  nv[1] = nr[nn];
+  nv[2] = nr[2 * nn];
+  const R s = nr[3 * nn];
+  const R mn = UL[1] * nv[0] + UL[2] * nv[1] + UL[3] * nv[2];
+  UG[0] = UL[0];
+  UG[4] = UL[4];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) UG[1 + c] = UL[1 + c] - R(2) * mn * nv[c];
+  riemann<R>(SF, UL, UG, nv, gam, pref, href, Fs);
+  R *oL = Buf<R>::Fsurf(d) + ((size_t)eL * 6 + fL) * 5 * nn + pq;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) oL[v * nn] = s * Fs[v];
+  if (d.equations != 1) return;
+  // BR1: w* - w = (w_ghost - w) / 2 = (-(u.n) n, 0)
+  const R un = mn / UL[0];
+  R *jL = Buf<R>::Wsurf(d) + ((size_t)eL * 6 + fL) * 4 * nn + pq;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) jL[c * nn] = -un * nv[c];
+  jL[3 * nn] = R(0);
+  // wall model at the exchange node
+  R Ux[5];
+  load_state<R>(d, U, eL, exchange_node(fL, p, q, d.wm_index), Ux);
+  const R irx = R(1) / Ux[0];
+  const R ux[3] = {Ux[1] * irx, Ux[2] * irx, Ux[3] * irx};
+  const R uxn = ux[0] * nv[0] + ux[1] * nv[1] + ux[2] * nv[2];
+  const R ut[3] = {ux[0] - uxn * nv[0], ux[1] - uxn * nv[1], ux[2] - uxn * nv[2]};
+  const R Ut = sqrt(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
+  R *fw = Buf<R>::Fwall(d) + (size_t)f * 4 * nn + pq;
+  R tw[3] = {R(0), R(0), R(0)};
+  if (Ut > R(0)) {
+    int it;
+    const R utau = wall_utau<R>(Ut, (R)d.hwm[(size_t)f * nn + pq], Cst<R>::mu(d) * irx, (R)d.wm_uinf, (R)d.wm_b,
+                                d.wm_vd, it);
+    const R tau = Ux[0] * utau * utau;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tw[c] = -tau * ut[c] / Ut;  // outward viscous flux: the wall's drag
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) fw[c * nn] = s * tw[c];
+  fw[3 * nn] = R(0);  // adiabatic wall at rest
+}
+
+// ---------------------------------------------------------------------------------------------
 // face kernel: Riemann flux once per face point, stored outward for both sides
 // ---------------------------------------------------------------------------------------------
 template <typename R, int SF>
@@ -410,11 +488,15 @@ __global__ void __launch_bounds__(256) k_face(const DgDevice d, const double *__
   const int f = (int)(t / nn), pq = (int)(t % nn), p = pq % n, q = pq / n;
   const int *F5 = d.face + 5 * f;
   const int eL = F5[0], fL = F5[1], eR = F5[2], fR = F5[3], o = F5[4];
+  const R pref = Cst<R>::pref(d), href = Cst<R>::href(d), gam = Cst<R>::gam(d);
+  if (eR < 0) {  // wall-modelled wall
+    wall_face<R, SF>(d, U, f, pq, eL, fL, pref, href, gam);
+    return;
+  }
   int p2, q2;
   orient_map(o, p, q, p2, q2);
   const int nodeL = face_node(fL, p, q), nodeR = face_node(fR, p2, q2);
   const int pqR = p2 + n * q2;
-  const R pref = Cst<R>::pref(d), href = Cst<R>::href(d), gam = Cst<R>::gam(d);
   R UL[5], UR[5], nv[3];
   load_state<R>(d, U, eL, nodeL, UL);
   load_state<R>(d, U, eR, nodeR, UR);
@@ -891,6 +973,14 @@ __global__ void __launch_bounds__(vol_threads<R, SC>(), vol_min_blocks<R, SC>())
           const int pp = dd == 0 ? ijk[1] : ijk[0], qq = dd == 2 ? ijk[1] : ijk[2];
           const int *ef = d.ef + ((size_t)e * 6 + f) * 4;
           const int nb = ef[0], fnb = ef[1], o = ef[2];
+          if (nb < 0) {  // wall: (1/w_b) (F*_wall - (+-) Fv_own / 2), the wall-model flux F*_wall outward
+            const R *fw = Buf<R>::Fwall(d) + (size_t)ef[3] * 4 * nn + pp + n * qq;
+            const R hs = (id == N) ? R(0.5) : R(-0.5);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              vis[q] += Tab<R>::invw(id) * (fw[q * nn] - hs * Fve[(dd * 4 + q) * nnn + node]);
+            continue;
+          }
           int p2, q2;
           orient_map(o, pp, qq, p2, q2);
           const int nbnode = face_node(fnb, p2, q2);
@@ -1063,6 +1153,14 @@ __global__ void __launch_bounds__(NODE_THREADS, 2) k_volume_f32(const DgDevice d
           const int pp = dd == 0 ? ijk[1] : ijk[0], qq = dd == 2 ? ijk[1] : ijk[2];
           const int *ef = d.ef + ((size_t)e * 6 + f) * 4;
           const int nb = ef[0], fnb = ef[1], o = ef[2];
+          if (nb < 0) {  // wall-model flux (see k_volume)
+            const float *fw = d.Fwall_f + (size_t)ef[3] * 4 * nn + pp + n * qq;
+            const float hs = (id == N) ? 0.5f : -0.5f;
+            const float *Fo = FS + (le * 12 + dd * 4) * PS + pn;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) s[1 + q] -= f_invw[id] * (fw[q * nn] - hs * Fo[q * PS]);
+            continue;
+          }
           int p2, q2;
           orient_map(o, pp, qq, p2, q2);
           const int nbnode = face_node(fnb, p2, q2);
@@ -1168,7 +1266,10 @@ __global__ void __launch_bounds__(256) k_spread(const DgDevice d, double *alpha_
   if (e >= d.nE) return;
   double a = d.alpha_raw[e];
 #pragma unroll
-  for (int f = 0; f < 6; ++f) a = fmax(a, 0.5 * d.alpha_raw[d.ef[(e * 6 + f) * 4]]);
+  for (int f = 0; f < 6; ++f) {
+    const int nb = d.ef[(e * 6 + f) * 4];
+    if (nb >= 0) a = fmax(a, 0.5 * d.alpha_raw[nb]);
+  }
   alpha_out[e] = a;
 }
 

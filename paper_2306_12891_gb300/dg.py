@@ -42,7 +42,8 @@ class _Params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("gamma", ctypes.c_double), ("R", ctypes.c_double),
                 ("mu", ctypes.c_double), ("Pr", ctypes.c_double), ("shock_capturing", ctypes.c_int),
                 ("alpha_min", ctypes.c_double), ("alpha_max", ctypes.c_double), ("sharpness", ctypes.c_double),
-                ("alpha_fixed", ctypes.c_double), ("p_ref", ctypes.c_double)]
+                ("alpha_fixed", ctypes.c_double), ("p_ref", ctypes.c_double), ("wm_index", ctypes.c_int),
+                ("wm_uinf", ctypes.c_double), ("wm_mainf", ctypes.c_double), ("wm_van_driest", ctypes.c_int)]
 
 
 _lib = None
@@ -89,6 +90,7 @@ def lib() -> ctypes.CDLL:
             "dg_kinetic_energy_grad": (i, [vp, vp, vp]),
             "dg_adjoint_memory_limit": (i, [vp, d]),
             "dg_check_conversions": (i, [vp, ctypes.c_longlong, vp]),
+            "dg_wall_model": (i, [i, vp, vp, vp, d, d, d, d, i, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -124,6 +126,24 @@ def probe_fma(kind: str = "fp64", stream=None) -> float:
     return out.value
 
 
+def wall_model(U, h, nu, uinf=1.0, mainf=0.0, gamma=1.4, Pr=0.72, van_driest=False, stream=None):
+    """(u_tau, Newton iterations) of the wall model for float64 CUDA tensors U, h, nu of one length."""
+    import torch
+
+    for t in (U, h, nu):
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.numel() != U.numel():
+            raise ValueError("U, h, nu must be contiguous float64 CUDA tensors of one length")
+    utau = torch.empty_like(U)
+    iters = torch.empty(U.numel(), dtype=torch.int32, device=U.device)
+    st = lib().dg_wall_model(U.numel(), ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(h.data_ptr()),
+                             ctypes.c_void_p(nu.data_ptr()), float(uinf), float(mainf), float(gamma), float(Pr),
+                             int(bool(van_driest)), ctypes.c_void_p(utau.data_ptr()),
+                             ctypes.c_void_p(iters.data_ptr()), _stream_ptr(stream))
+    if st != DG_OK:
+        raise DGError(st, "dg_wall_model")
+    return utau, iters
+
+
 def check_conversions(count: int = 1 << 24, stream=None):
     """(float->double, double->float) mismatches of the library's integer-pipe conversions against
     the GPU's own, on `count` generated bit patterns each."""
@@ -139,7 +159,8 @@ class DG:
 
     def __init__(self, N, xyz, faces, equations="euler", vflux="kg", sflux="llf", precision="fp64", gamma=1.4,
                  R=1.0, mu=0.0, Pr=0.72, shock_capturing=False, alpha_min=0.01, alpha_max=0.7,
-                 sharpness=DEFAULT_SHARPNESS, alpha_fixed=-1.0, p_ref=0.0, stream=None):
+                 sharpness=DEFAULT_SHARPNESS, alpha_fixed=-1.0, p_ref=0.0, wm_index=1, wm_uinf=1.0, wm_mainf=0.0,
+                 wm_van_driest=False, stream=None):
         import torch
 
         self.torch = torch
@@ -151,7 +172,8 @@ class DG:
         self.numel = int(np.prod(self.shape))
         mesh = _Mesh(self.nE, self.N, xyz.ctypes.data, faces.shape[0], faces.ctypes.data)
         prm = _Params(EQUATIONS[equations], VFLUX[vflux], SFLUX[sflux], PRECISION[precision], gamma, R, mu, Pr,
-                      int(bool(shock_capturing)), alpha_min, alpha_max, sharpness, float(alpha_fixed), float(p_ref))
+                      int(bool(shock_capturing)), alpha_min, alpha_max, sharpness, float(alpha_fixed), float(p_ref),
+                      int(wm_index), float(wm_uinf), float(wm_mainf), int(bool(wm_van_driest)))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         ctx = ctypes.c_void_p(None)
         st = lib().dg_init(ctypes.byref(mesh), self.N, 0, ctypes.byref(prm), ctypes.c_void_p(self.stream.cuda_stream),
