@@ -295,6 +295,44 @@ def run_adjoint(stream, peak_fp64: float, interval: int = 10) -> dict:
                         for k, v in kt.items() if v[1]}}
 
 
+WALL_WORKLOAD = "channel_wm_ns_n5_48x24x24"
+
+
+def run_wall_model(stream, steps: int = 5, warmup: int = 3) -> dict:
+    """Cost of the wall model (Sec. 3): LSERK steps of the wall-modelled channel against the same
+    mesh, state and physics with the walls replaced by periodic faces, FP64."""
+    import torch
+
+    from paper_2306_12891_gb300 import dg
+
+    out = {"workload": WALL_WORKLOAD}
+    for label, walls in (("walls", True), ("periodic", False)):
+        w = WORKLOADS[WALL_WORKLOAD].with_(z_walls=walls)
+        xyz, faces = w.mesh()
+        s = dg.DG(w.N, xyz, faces, stream=stream, **w.physics())
+        U = torch.from_numpy(WORKLOADS[WALL_WORKLOAD].initial_state(xyz)).cuda()
+        dt = s.max_dt(U, w.cfl)
+        s.lserk_steps(U, dt, warmup)
+        s.timing_enable(True)
+        s.timing_get()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.lserk_steps(U, dt, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kt = s.timing_get()
+        s.check()
+        ms = e0.elapsed_time(e1) / steps
+        out[label] = {"ms_per_step": ms, "value": w.dofs * STAGES / (ms * 1e-3), "unit": UNIT,
+                      "face_ms_per_launch": kt["face"][0] / kt["face"][1]}
+        if walls:
+            out["wall_faces"] = int((faces[:, 2] < 0).sum())
+        del s
+    out["overhead"] = out["walls"]["ms_per_step"] / out["periodic"]["ms_per_step"] - 1.0
+    return out
+
+
 def run_gpu(args):
     import torch
 
@@ -436,6 +474,8 @@ def run_gpu(args):
         line["fp32_bulk"] = fp32
     if args.adjoint and not args.nel and world == 1:
         line["adjoint"] = run_adjoint(stream, peak_fp64)
+    if args.wall and not args.nel and world == 1:
+        line["wall_model"] = run_wall_model(stream)
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -450,6 +490,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-fp32", dest="fp32", action="store_false", help="skip the FP32-bulk comparison")
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false", help="skip the adjoint (gradient) block")
+    ap.add_argument("--no-wall", dest="wall", action="store_false", help="skip the wall-model cost block")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk"])
     ap.add_argument("--nel", type=int, default=None, help="elements per direction (default: the workload's 32)")

@@ -19,7 +19,8 @@ from numpy.polynomial import legendre as _leg
 
 TWO_PI = 2.0 * math.pi
 BLAST_SEED = 20230622
-ADJOINT_SEED = 20230623  # perturbation of the Taylor-Green base state for the adjoint workload
+ADJOINT_SEED = 20230623
+CHANNEL_SEED = 20230624  # perturbation of the Taylor-Green base state for the adjoint workload
 
 
 def lgl_points(N: int) -> np.ndarray:
@@ -279,6 +280,19 @@ def tgv_perturbed(xyz, seed=ADJOINT_SEED, amp=1e-2, modes=4, gamma=1.4, mach=0.1
     return cons_from_prim(rho + d[0], u + d[1], v + d[2], w + d[3], p + d[4], gamma)
 
 
+def channel_flow(xyz, hz=2.0, ub=1.0, mach=0.3, gamma=1.4, seed=CHANNEL_SEED, amp=0.05):
+    """Channel between walls z = 0 and z = hz: a turbulent-like mean profile u = ub (2z'(2 - z'))^(1/7)
+    (z' = 2z/hz folded to [0, 1]) with a seeded smooth perturbation of all velocity components
+    (relative amplitude amp), rho = 1, p = 1/(gamma Ma^2)."""
+    zr = np.minimum(xyz[:, 2], hz - xyz[:, 2]) / (0.5 * hz)
+    base = ub * np.clip(zr * (2.0 - zr), 0.0, 1.0) ** (1.0 / 7.0)
+    rng = np.random.default_rng(seed)
+    du = [amp * ub * smooth_field(xyz, rng, modes=2) for _ in range(3)]
+    wall = np.sin(np.pi * xyz[:, 2] / hz)  # perturbations vanish at the walls
+    one = np.ones_like(xyz[:, 0])
+    return cons_from_prim(one, base + du[0] * wall, du[1] * wall, du[2] * wall, one / (gamma * mach ** 2), gamma)
+
+
 def random_smooth_state(xyz, seed, amp=0.05, gamma=1.4, modes=2):
     """Seeded smooth periodic perturbation of a rest state (for parity tests of generic fields)."""
     rng = np.random.default_rng(seed)
@@ -319,6 +333,8 @@ class Workload:
     precision: str = "fp64"  # "fp64" | "fp32_bulk"
     steps: int = 10
     cfl: float = 0.9
+    z_walls: bool = False   # z = lo and z = hi are wall-modelled walls (a channel)
+    wm_index: int = 1
 
     @property
     def n_elems(self) -> int:
@@ -332,7 +348,7 @@ class Workload:
         return dataclasses.replace(self, **kw)
 
     def mesh(self):
-        return box_mesh(self.N, self.nel, self.lo, self.hi, self.mapping)
+        return box_mesh(self.N, self.nel, self.lo, self.hi, self.mapping, z_walls=self.z_walls)
 
     def initial_state(self, xyz):
         if self.initial == "tgv":
@@ -345,11 +361,16 @@ class Workload:
             return density_wave(xyz, gamma=self.gamma)
         if self.initial == "tgv_perturbed":
             return tgv_perturbed(xyz, gamma=self.gamma)
+        if self.initial == "channel":
+            return channel_flow(xyz, hz=self.hi[2] - self.lo[2], gamma=self.gamma)
         raise ValueError(self.initial)
 
     def physics(self) -> dict:
-        return dict(equations=self.equations, vflux=self.vflux, sflux=self.sflux, gamma=self.gamma,
-                    R=self.R, mu=self.mu, Pr=self.Pr, shock_capturing=self.shock_capturing)
+        out = dict(equations=self.equations, vflux=self.vflux, sflux=self.sflux, gamma=self.gamma,
+                   R=self.R, mu=self.mu, Pr=self.Pr, shock_capturing=self.shock_capturing)
+        if self.z_walls:
+            out.update(wm_index=self.wm_index, wm_uinf=1.0, wm_mainf=0.3, wm_van_driest=True)
+        return out
 
 
 RE_TGV = 1600.0
@@ -375,4 +396,10 @@ WORKLOADS = {
     "tgv_ns_n5_24x24x24_adjoint": Workload("tgv_ns_n5_24x24x24_adjoint", 5, (24, 24, 24), "ns", "pirozzoli",
                                            "roe", "tgv_perturbed", mapping="sine_0.05", mu=1.0 / RE_TGV,
                                            steps=50, cfl=0.9),
+    # wall-modelled channel (Sec. 3): walls z = 0, 2; periodic 2pi x pi; N = 5, 48 x 24 x 24 elements;
+    # Navier-Stokes, Pirozzoli + Roe + BR1, Re_b = 1e5 (mu = 1e-5 at U_b = 1, half height 1), Ma 0.3,
+    # Spalding wall shear with the van Driest transform at the first interior node
+    "channel_wm_ns_n5_48x24x24": Workload("channel_wm_ns_n5_48x24x24", 5, (48, 24, 24), "ns", "pirozzoli", "roe",
+                                          "channel", lo=(0.0, 0.0, 0.0), hi=(TWO_PI, np.pi, 2.0), mu=1e-5,
+                                          steps=10, cfl=0.9, z_walls=True, wm_index=1),
 }
