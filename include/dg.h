@@ -107,7 +107,10 @@ dg_status dg_rhs(dg_ctx *ctx, const double *U, double *Ut, double t);
  * U <- U(t + dt), in place. The register g is library-owned. */
 dg_status dg_lserk_step(dg_ctx *ctx, double *U, double dt, double t);
 
-/* n_steps LSERK steps of size dt starting at time t (one graph-free launch sequence). */
+/* n_steps LSERK steps of size dt starting at time t. By default (dg_use_graphs) the launch sequence
+ * of one step is captured into a CUDA graph on the first call for a given (U, dt) and replayed
+ * for the remaining steps on a library stream ordered after and before the context stream by
+ * events (asynchronous as before; the first step runs directly). Kernel timing disables it. */
 dg_status dg_lserk_steps(dg_ctx *ctx, double *U, double dt, double t, int n_steps);
 
 /* The same step on a HOST array U_host: copies it to a library-owned device buffer, steps, and
@@ -188,11 +191,21 @@ dg_status dg_kinetic_energy_grad(dg_ctx *ctx, const double *U, double *grad);
 dg_status dg_max_dt(dg_ctx *ctx, const double *U, double cfl, double *dt);
 
 /* DG_OK, or DG_ERR_NONPHYSICAL if any kernel since the last call met rho <= 0, p <= 0 or a
- * non-finite state (clears the flag; synchronising). */
+ * non-finite state, or DG_ERR_CUDA if a kernel gave up waiting for a bulk copy (bounded waits;
+ * clears the flags; synchronising). */
 dg_status dg_check(dg_ctx *ctx);
 
 /* Copy the device metrics to caller device arrays Ja [n_elems][3 d][3 c][n]^3 and J [n_elems][n]^3. */
 dg_status dg_get_metrics(dg_ctx *ctx, double *Ja, double *J);
+
+/* 1 (default): the FP32-bulk volume operator without the blend runs as a persistent kernel whose
+ * per-element inputs arrive by TMA bulk copies one element ahead (N = 3, 5, 7, and 16-byte aligned
+ * U, Ut and g); 0: the plain node-per-thread kernel. Both give identical bits. */
+dg_status dg_use_tma(dg_ctx *ctx, int enable);
+
+/* 1 (default): multi-step calls replay a CUDA graph of one step; 0: every kernel is launched. Both
+ * run the same kernels and give identical bits. */
+dg_status dg_use_graphs(dg_ctx *ctx, int enable);
 
 /* Kernel timing on the context stream: when enabled, CUDA events bracket every launch and
  * per-kernel totals accumulate (ms, launches). Names: "face", "lift", "volume", "indicator",

@@ -72,6 +72,15 @@ struct dg_ctx {
   // adjoint: library-owned state buffers (stage states, gbar, checkpoints), allocated on first use
   std::vector<double *> adj_pool;
   size_t adj_limit = 0;        // bytes the adjoint's state buffers may use (0: free memory less 10%)
+  // CUDA graph of one LSERK step, replayed by the multi-step calls on a library stream that is
+  // ordered after (and before) the caller's stream with events
+  int use_graphs = 1;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+  cudaGraphExec_t step_graph = nullptr;
+  const double *graph_U = nullptr;
+  double graph_dt = 0.0;
+  long long graph_launches = 0;
 };
 
 namespace {
@@ -249,6 +258,10 @@ dg_status dg_basis(int N, double *xi, double *w, double *D) {
 
 void dg_free(dg_ctx *c) {
   if (!c) return;
+  if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
+  if (c->gev_in) cudaEventDestroy(c->gev_in);
+  if (c->gev_out) cudaEventDestroy(c->gev_out);
+  if (c->gstream) cudaStreamDestroy(c->gstream);
   for (void *p : c->allocs) cudaFree(p);
   for (auto &pr : c->ev_pool) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   if (c->flag_host) cudaFreeHost(c->flag_host);
@@ -338,6 +351,7 @@ dg_status dg_init(const dg_mesh *mesh, int N, int nodes, const dg_params *prm, v
   d.href_f = (float)d.href;
   d.mu_f = (float)d.mu;
   d.kappa_f = (float)d.kappa;
+  d.use_tma = 1;
   d.n_walls = n_walls;
   d.wm_index = prm->wm_index;
   d.wm_vd = prm->wm_van_driest ? 1 : 0;
@@ -432,10 +446,68 @@ dg_status refresh_shadow(dg_ctx *c, const double *U) {
   if (c->d.precision != DG_FP32_BULK) return DG_OK;
   return launch(c, KC_OTHER, [&] { c->K->shadow(c->d, U, c->stream); });
 }
-dg_status steps_impl(dg_ctx *c, double *U, double dt, int n_steps) {
-  DG_TRY(refresh_shadow(c, U));
+dg_status plain_steps(dg_ctx *c, double *U, double dt, int n_steps) {
   for (int k = 0; k < n_steps; ++k)
     for (int st = 0; st < 5; ++st) DG_TRY(stage(c, U, U, 1, st, dt));
+  return DG_OK;
+}
+
+// capture one LSERK step on U with step dt into c->step_graph (launches go to the library stream)
+dg_status capture_step(dg_ctx *c, double *U, double dt) {
+  if (c->step_graph) { cudaGraphExecDestroy(c->step_graph); c->step_graph = nullptr; }
+  cudaStream_t user = c->stream;
+  c->stream = c->gstream;
+  const long long l0 = c->launches;
+  cudaError_t e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal);
+  dg_status st = e ? DG_ERR_CUDA : DG_OK;
+  if (st == DG_OK) st = plain_steps(c, U, dt, 1);
+  cudaGraph_t g = nullptr;
+  if (!e) {
+    const cudaError_t e2 = cudaStreamEndCapture(c->gstream, &g);
+    if (!e && e2) e = e2;
+  }
+  c->graph_launches = c->launches - l0;
+  c->launches = l0;  // captured, not run
+  c->stream = user;
+  if (!e && st == DG_OK) e = cudaGraphInstantiate(&c->step_graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e) {
+    cudaGetLastError();
+    c->step_graph = nullptr;
+    return cuda_fail(c, e, "step graph");
+  }
+  if (st != DG_OK) return st;
+  c->graph_U = U;
+  c->graph_dt = dt;
+  return DG_OK;
+}
+
+// n_steps LSERK steps. With graphs on (and kernel timing off) the step's launch sequence is
+// captured once per (U, dt) and replayed: one graph launch per step instead of 10-20 kernel
+// launches, which is what bounds small meshes.
+dg_status steps_impl(dg_ctx *c, double *U, double dt, int n_steps) {
+  DG_TRY(refresh_shadow(c, U));
+  if (n_steps <= 0) return DG_OK;
+  if (!c->use_graphs || c->timing || n_steps < 2) return plain_steps(c, U, dt, n_steps);
+  cudaError_t e = cudaSuccess;
+  if (!c->gstream) {
+    e = cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking);
+    if (!e) e = cudaEventCreateWithFlags(&c->gev_in, cudaEventDisableTiming);
+    if (!e) e = cudaEventCreateWithFlags(&c->gev_out, cudaEventDisableTiming);
+    if (e) return cuda_fail(c, e, "graph stream");
+  }
+  if (!(c->step_graph && c->graph_U == U && c->graph_dt == dt)) {
+    DG_TRY(plain_steps(c, U, dt, 1));  // first step directly (also sets kernel attributes outside capture)
+    --n_steps;
+    DG_TRY(capture_step(c, U, dt));
+  }
+  e = cudaEventRecord(c->gev_in, c->stream);
+  if (!e) e = cudaStreamWaitEvent(c->gstream, c->gev_in, 0);
+  for (int k = 0; k < n_steps && !e; ++k) e = cudaGraphLaunch(c->step_graph, c->gstream);
+  if (!e) e = cudaEventRecord(c->gev_out, c->gstream);
+  if (!e) e = cudaStreamWaitEvent(c->stream, c->gev_out, 0);
+  if (e) return cuda_fail(c, e, "step graph launch");
+  c->launches += c->graph_launches * n_steps;
   return DG_OK;
 }
 }  // namespace
@@ -592,6 +664,7 @@ dg_status dg_check(dg_ctx *c) {
   const int f = *c->flag_host;
   e = cudaMemsetAsync(c->d.flag, 0, sizeof(int), c->stream);
   if (e) return cuda_fail(c, e, "dg_check");
+  if (f & 4) return fail(c, DG_ERR_CUDA, "a device-side wait for a bulk copy timed out");
   if (f & 1) return fail(c, DG_ERR_NONPHYSICAL, "a kernel met rho <= 0, p <= 0 or a non-finite state");
   return DG_OK;
 }
@@ -603,6 +676,19 @@ dg_status dg_get_metrics(dg_ctx *c, double *Ja, double *J) {
   cudaError_t e = cudaMemcpyAsync(Ja, c->d.Ja, sizeof(double) * c->d.nE * 9 * nnn, cudaMemcpyDeviceToDevice, c->stream);
   if (!e) e = cudaMemcpyAsync(J, c->d.J, sizeof(double) * c->d.nE * nnn, cudaMemcpyDeviceToDevice, c->stream);
   if (e) return cuda_fail(c, e, "dg_get_metrics");
+  return DG_OK;
+}
+
+dg_status dg_use_tma(dg_ctx *c, int enable) {
+  if (!c) return DG_ERR_ARG;
+  c->d.use_tma = enable != 0;
+  if (c->step_graph) { cudaGraphExecDestroy(c->step_graph); c->step_graph = nullptr; }  // kernels change
+  return DG_OK;
+}
+
+dg_status dg_use_graphs(dg_ctx *c, int enable) {
+  if (!c) return DG_ERR_ARG;
+  c->use_graphs = enable != 0;
   return DG_OK;
 }
 

@@ -31,6 +31,7 @@ struct DgDevice {
   float gamma_f, gm1_f, iR_f, p_ref_f, href_f, mu_f, kappa_f;
   // wall-modelled walls (faces with elemR = -1; Sec. 3): exchange node index, van Driest on/off
   // with b = sqrt(r m)/sqrt(1 + r m), m = (gamma-1)/2 Ma_inf^2, r = Pr^(1/3), and freestream speed
+  int use_tma;         // FP32-bulk volume operator through the TMA-fed persistent kernel (N = 3, 5, 7)
   int n_walls;         // number of wall faces (0: fully periodic)
   int wm_index, wm_vd;
   double wm_uinf, wm_b;

@@ -1024,35 +1024,156 @@ constexpr int NODE_THREADS = round32(NODE_EPB * nnn);
 constexpr int NODE_SLOTS = 7 + 9 + 12;  // staged primitives, metric terms, contravariant viscous flux
 
 
-// scaled two-point flux of the staged nodes a and b through the metric sums Sj (see line_fluxdiff)
+// scaled two-point flux of the staged nodes a and b through the metric sums Sj (see line_fluxdiff);
+// P holds the staged quantities [7][nnn] (node index, no padding)
 template <int VF>
 __device__ __forceinline__ void pair_flux_f(const float *__restrict__ P, int a, int b, float Sjx, float Sjy,
                                             float Sjz, float gam, float pref, float F[5]) {
-  const float ri = P[a], ui = P[PS + a], vi = P[2 * PS + a], wi = P[3 * PS + a];
-  const float rm = P[b], um = P[PS + b], vm = P[2 * PS + b], wm = P[3 * PS + b];
+  const float ri = P[a], ui = P[nnn + a], vi = P[2 * nnn + a], wi = P[3 * nnn + a];
+  const float rm = P[b], um = P[nnn + b], vm = P[2 * nnn + b], wm = P[3 * nnn + b];
   if (VF == VF_PIR || VF == VF_KG) {
     const float Su = ui + um, Sv = vi + vm, Sw = wi + wm;
     const float Vp = Su * Sjx + Sv * Sjy + Sw * Sjz;
     F[0] = (ri + rm) * Vp;
-    const float Sp = P[4 * PS + a] + P[4 * PS + b];
+    const float Sp = P[4 * nnn + a] + P[4 * nnn + b];
     F[1] = F[0] * Su + Sp * Sjx;
     F[2] = F[0] * Sv + Sp * Sjy;
     F[3] = F[0] * Sw + Sp * Sjz;
-    if (VF == VF_PIR) F[4] = F[0] * (P[5 * PS + a] + P[5 * PS + b]);
-    else F[4] = F[0] * (P[5 * PS + a] + P[5 * PS + b]) + (P[6 * PS + a] + P[6 * PS + b]) * Vp;
+    if (VF == VF_PIR) F[4] = F[0] * (P[5 * nnn + a] + P[5 * nnn + b]);
+    else F[4] = F[0] * (P[5 * nnn + a] + P[5 * nnn + b]) + (P[6 * nnn + a] + P[6 * nnn + b]) * Vp;
   } else {
     const float av[3] = {0.5f * Sjx, 0.5f * Sjy, 0.5f * Sjz};
     if (VF == VF_EC) {
-      ec_flux<float>(ri, ui, vi, wi, P[6 * PS + a], rm, um, vm, wm, P[6 * PS + b], av, gam, pref, F);
+      ec_flux<float>(ri, ui, vi, wi, P[6 * nnn + a], rm, um, vm, wm, P[6 * nnn + b], av, gam, pref, F);
     } else {
       const float Vi = ui * av[0] + vi * av[1] + wi * av[2], Vm = um * av[0] + vm * av[1] + wm * av[2];
-      const float pm2 = 0.125f * (P[4 * PS + a] + P[4 * PS + b]);
+      const float pm2 = 0.125f * (P[4 * nnn + a] + P[4 * nnn + b]);
       F[0] = 0.5f * (ri * Vi + rm * Vm);
       F[1] = 0.5f * (ri * ui * Vi + rm * um * Vm) + pm2 * av[0];
       F[2] = 0.5f * (ri * vi * Vi + rm * vm * Vm) + pm2 * av[1];
       F[3] = 0.5f * (ri * wi * Vi + rm * wm * Vm) + pm2 * av[2];
-      F[4] = 0.5f * (P[5 * PS + a] * Vi + P[5 * PS + b] * Vm);
+      F[4] = 0.5f * (P[5 * nnn + a] * Vi + P[5 * nnn + b] * Vm);
     }
+  }
+}
+
+// staged quantities of one node (rho, u, v, w, 4p', X, Y; see k_volume) from its FP32 shadow state;
+// Pn points at the node's entry of P [7][nnn]
+template <int VF>
+__device__ __forceinline__ void f32_stage(const DgDevice &d, const float Uv[5], float *Pn) {
+  const float gm1 = d.gm1_f, pref = d.p_ref_f;
+  const float r = Uv[0], ir = 1.0f / r;
+  const float u = Uv[1] * ir, v = Uv[2] * ir, w = Uv[3] * ir;
+  const float pm = gm1 * (Uv[4] - 0.5f * (Uv[1] * u + Uv[2] * v + Uv[3] * w));
+  const float p = pm + pref;
+  const float Et = Uv[4] + (float)d.eref;
+  if (!(r > 0.0f) || !(p > 0.0f) || !isfinite(Uv[4])) flag_set(d.flag, 1);
+  Pn[0] = r; Pn[nnn] = u; Pn[2 * nnn] = v; Pn[3 * nnn] = w; Pn[4 * nnn] = 4.0f * pm;
+  if (VF == VF_PIR) Pn[5 * nnn] = (Et + p) * ir;
+  else if (VF == VF_KG) { Pn[5 * nnn] = Et * ir; Pn[6 * nnn] = 2.0f * p; }
+  else if (VF == VF_EC) Pn[6 * nnn] = p;
+  else Pn[5 * nnn] = Et + p;
+}
+
+// the node's flux differencing, surface terms and (Navier-Stokes) viscous divergence with the
+// neighbour's or the wall's viscous trace, summed into s. P [7][nnn], J [9][nnn] (slot 3d + c),
+// F [12][nnn] (contravariant viscous flux of this element) staged; Fs = this element's face slots
+// [6][5][nn] (shared or global memory)
+template <int VF>
+__device__ __forceinline__ void f32_node_terms(const DgDevice &d, const float *__restrict__ P,
+                                               const float *__restrict__ J, const float *__restrict__ F,
+                                               const float *__restrict__ Fs, int e, int node, float s[5]) {
+  const float gam = d.gamma_f, pref = d.p_ref_f;
+  const bool ns = d.equations == 1;
+  const int ijk[3] = {node % n, (node / n) % n, node / nn};
+#pragma unroll
+  for (int v = 0; v < 5; ++v) s[v] = 0.0f;
+#pragma unroll
+  for (int dd = 0; dd < 3; ++dd) {
+    const int id = ijk[dd];
+    const int st = dd == 0 ? 1 : dd == 1 ? n : nn;
+    const int base = node - id * st;
+    const float jx = J[(3 * dd) * nnn + node], jy = J[(3 * dd + 1) * nnn + node], jz = J[(3 * dd + 2) * nnn + node];
+#pragma unroll
+    for (int m = 0; m < n; ++m) {  // m = id contributes 0 (zero diagonal of the scaled tables)
+      const int am = base + m * st;
+      float Fp[5];
+      pair_flux_f<VF>(P, node, am, jx + J[(3 * dd) * nnn + am], jy + J[(3 * dd + 1) * nnn + am],
+                      jz + J[(3 * dd + 2) * nnn + am], gam, pref, Fp);
+      if (VF == VF_PIR || VF == VF_KG) {
+        const float cq = f_Dq[id * n + m], ce = f_De[id * n + m];
+        s[0] += cq * Fp[0];
+#pragma unroll
+        for (int v = 1; v < 5; ++v) s[v] += ce * Fp[v];
+      } else {
+        const float c2 = f_D2[id * n + m];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) s[v] += c2 * Fp[v];
+      }
+    }
+    const bool face = id == 0 || id == N;
+    const int f = 2 * dd + (id == N ? 1 : 0);
+    const int pp = dd == 0 ? ijk[1] : ijk[0], qq = dd == 2 ? ijk[1] : ijk[2];
+    if (face) {  // surface term: (1/w_b) times the outward face flux
+      const float *fs = Fs + f * 5 * nn + pp + n * qq;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) s[v] += f_invw[id] * fs[v * nn];
+    }
+    if (ns) {
+      // viscous divergence along the line (zero diagonal: 2D/2 from the scaled table) and the
+      // neighbour's outward normal viscous flux -(1/(2 w_b)) phi_nb at the element faces
+      const float *Fvd = F + (dd * 4) * nnn + base;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int m = 0; m < n; ++m) acc += 0.5f * f_D2[id * n + m] * Fvd[q * nnn + m * st];
+        s[1 + q] -= acc;
+      }
+      if (face) {
+        const int *ef = d.ef + ((size_t)e * 6 + f) * 4;
+        const int nb = ef[0], fnb = ef[1], o = ef[2];
+        if (nb < 0) {  // wall-model flux: (1/w_b) (F*_wall - (+-) Fv_own / 2), see k_volume
+          const float *fw = d.Fwall_f + (size_t)ef[3] * 4 * nn + pp + n * qq;
+          const float hs = (id == N) ? 0.5f : -0.5f;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) s[1 + q] -= f_invw[id] * (fw[q * nn] - hs * F[(dd * 4 + q) * nnn + node]);
+        } else {
+          int p2, q2;
+          orient_map(o, pp, qq, p2, q2);
+          const int nbnode = face_node(fnb, p2, q2);
+          const float sg = (fnb & 1) ? 0.5f : -0.5f;
+          const float *Fvn = d.Fv_f + ((size_t)nb * 12 + (fnb >> 1) * 4) * nnn + nbnode;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) s[1 + q] += f_invw[id] * sg * Fvn[q * nnn];
+        }
+      }
+    }
+  }
+}
+
+// -1/J and the output / LSERK(5,4) stage in FP64 for one node; Ue, ge point at this element's state
+// and register slices [5][nnn] to read (shared or global memory), out and g are global
+__device__ __forceinline__ void f32_finish(const DgDevice &d, const double *Ue, const double *ge,
+                                           double *out, double *__restrict__ g, int e, int node,
+                                           const float s[5], int mode, int first, double dt, double A,
+                                           double B) {
+  const double miJ = -d.invJ[(size_t)e * nnn + node];
+  const size_t gi = (size_t)e * 5 * nnn + node;
+  if (mode == 0) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) out[gi + v * nnn] = miJ * f2d_int(s[v]);
+    return;
+  }
+  const double dtJ = dt * miJ, eref = d.eref;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const double du = dtJ * f2d_int(s[v]);
+    const double gv = first ? du : A * ge[node + v * nnn] + du;
+    g[gi + v * nnn] = gv;
+    const double un = Ue[node + v * nnn] + B * gv;
+    out[gi + v * nnn] = un;
+    d.Uf[gi + v * nnn] = d2f_int(v == 4 ? un - eref : un);
   }
 }
 
@@ -1061,134 +1182,155 @@ __global__ void __launch_bounds__(NODE_THREADS, 2) k_volume_f32(const DgDevice d
                                                                  double *__restrict__ g, int mode, int first,
                                                                  double dt, double A, double B) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  float *P = reinterpret_cast<float *>(sm_raw);  // [EPB][7][PS] staged primitives (as k_volume)
-  float *JS = P + NODE_EPB * 7 * PS;             // [EPB][9][PS] metric terms Ja^d_c, slot 3d + c
-  float *FS = JS + NODE_EPB * 9 * PS;            // [EPB][12][PS] contravariant viscous flux (NS)
+  float *P = reinterpret_cast<float *>(sm_raw);  // [EPB][7][nnn] staged primitives
+  float *JS = P + NODE_EPB * 7 * nnn;            // [EPB][9][nnn] metric terms Ja^d_c, slot 3d + c
+  float *FS = JS + NODE_EPB * 9 * nnn;           // [EPB][12][nnn] contravariant viscous flux (NS)
   const int e0 = blockIdx.x * NODE_EPB;
-  const float gam = d.gamma_f, gm1 = d.gm1_f, pref = d.p_ref_f;
-  const double eref = d.eref;
   for (int t = threadIdx.x; t < NODE_EPB * nnn; t += blockDim.x) {
     const int le = t / nnn, node = t % nnn, e = e0 + le;
     if (e >= d.nE) continue;
     float Uv[5];
     load_state<float>(d, U, e, node, Uv);
-    const float r = Uv[0], ir = 1.0f / r;
-    const float u = Uv[1] * ir, v = Uv[2] * ir, w = Uv[3] * ir;
-    const float pm = gm1 * (Uv[4] - 0.5f * (Uv[1] * u + Uv[2] * v + Uv[3] * w));
-    const float p = pm + pref;
-    const float Et = Uv[4] + (float)eref;
-    if (!(r > 0.0f) || !(p > 0.0f) || !isfinite(Uv[4])) flag_set(d.flag, 1);
-    const int pn = pidx(node);
-    float *Pe = P + le * 7 * PS + pn;
-    Pe[0] = r; Pe[PS] = u; Pe[2 * PS] = v; Pe[3 * PS] = w; Pe[4 * PS] = 4.0f * pm;
-    if (VF == VF_PIR) Pe[5 * PS] = (Et + p) * ir;
-    else if (VF == VF_KG) { Pe[5 * PS] = Et * ir; Pe[6 * PS] = 2.0f * p; }
-    else if (VF == VF_EC) Pe[6 * PS] = p;
-    else Pe[5 * PS] = Et + p;
+    f32_stage<VF>(d, Uv, P + le * 7 * nnn + node);
     const float *Jn = d.Jaf + (size_t)e * 9 * nnn + node;
-    float *Je = JS + le * 9 * PS + pn;
+    float *Je = JS + le * 9 * nnn + node;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Je[k * PS] = Jn[k * nnn];
+    for (int k = 0; k < 9; ++k) Je[k * nnn] = Jn[k * nnn];
     if (d.equations == 1) {
       const float *Fn = d.Fv_f + (size_t)e * 12 * nnn + node;
-      float *Fe = FS + le * 12 * PS + pn;
+      float *Fe = FS + le * 12 * nnn + node;
 #pragma unroll
-      for (int k = 0; k < 12; ++k) Fe[k * PS] = Fn[k * nnn];
+      for (int k = 0; k < 12; ++k) Fe[k * nnn] = Fn[k * nnn];
     }
   }
   __syncthreads();
-  const bool ns = d.equations == 1;
-  const float *Fvb = d.Fv_f, *Fsb = d.Fsurf_f;
   for (int t = threadIdx.x; t < NODE_EPB * nnn; t += blockDim.x) {
     const int le = t / nnn, node = t % nnn, e = e0 + le;
     if (e >= d.nE) continue;
-    const int ijk[3] = {node % n, (node / n) % n, node / nn};
-    const int pn = pidx(node);
-    const float *Pe = P + le * 7 * PS;
-    const float *Je = JS + le * 9 * PS;
-    float s[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-    for (int dd = 0; dd < 3; ++dd) {
-      const int id = ijk[dd];
-      const int sp = dd == 0 ? 1 : dd == 1 ? (n + 1) : (n + 1) * n;  // padded stride along the line
-      const int pb = pn - id * sp;
-      const float jx = Je[(3 * dd) * PS + pn], jy = Je[(3 * dd + 1) * PS + pn], jz = Je[(3 * dd + 2) * PS + pn];
-#pragma unroll
-      for (int m = 0; m < n; ++m) {  // m = id contributes 0 (zero diagonal of the scaled tables)
-        const int am = pb + m * sp;
-        float F[5];
-        pair_flux_f<VF>(Pe, pn, am, jx + Je[(3 * dd) * PS + am], jy + Je[(3 * dd + 1) * PS + am],
-                        jz + Je[(3 * dd + 2) * PS + am], gam, pref, F);
-        if (VF == VF_PIR || VF == VF_KG) {
-          const float cq = f_Dq[id * n + m], ce = f_De[id * n + m];
-          s[0] += cq * F[0];
-#pragma unroll
-          for (int v = 1; v < 5; ++v) s[v] += ce * F[v];
-        } else {
-          const float c2 = f_D2[id * n + m];
-#pragma unroll
-          for (int v = 0; v < 5; ++v) s[v] += c2 * F[v];
-        }
+    float s[5];
+    f32_node_terms<VF>(d, P + le * 7 * nnn, JS + le * 9 * nnn, FS + le * 12 * nnn,
+                       d.Fsurf_f + (size_t)e * 6 * 5 * nn, e, node, s);
+    const size_t ge0 = (size_t)e * 5 * nnn;
+    f32_finish(d, U + ge0, g + ge0, out, g, e, node, s, mode, first, dt, A, B);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// The same FP32-bulk volume operator as a persistent kernel fed by TMA bulk copies: one CTA per SM
+// (or two) walks its elements; each element's contiguous slices -- FP32 state, metric terms,
+// viscous flux, face slots and the FP64 state and LSERK register -- are copied into shared memory
+// with cp.async.bulk one element ahead (double buffer, one mbarrier per buffer), so the next
+// element's loads overlap this element's arithmetic. Needs element slices that are multiples of
+// 16 bytes (N = 3, 5, 7) and 16-byte aligned U, g and output.
+// ---------------------------------------------------------------------------------------------
+constexpr bool TMA_OK = (N == 3 || N == 5 || N == 7);
+constexpr int TMA_THREADS = round32(nnn);
+constexpr unsigned TB_UF = 5u * nnn * 4u, TB_JA = 9u * nnn * 4u, TB_FV = 12u * nnn * 4u, TB_FS = 30u * nn * 4u;
+constexpr unsigned TB_U = 5u * nnn * 8u, TB_G = 5u * nnn * 8u;
+constexpr unsigned TB_BUF = TB_UF + TB_JA + TB_FV + TB_FS + TB_U + TB_G;
+constexpr unsigned TB_P = 7u * nnn * 4u;
+constexpr unsigned TB_SMEM = 2u * TB_BUF + TB_P + 16u;
+static_assert(!TMA_OK || (TB_UF % 16 == 0 && TB_JA % 16 == 0 && TB_FV % 16 == 0 && TB_FS % 16 == 0 &&
+                          TB_U % 16 == 0 && TB_P % 16 == 0), "TMA slices must be multiples of 16 bytes");
+static_assert(!TMA_OK || TB_SMEM <= 232448, "TMA kernel exceeds the shared memory of one CTA");
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+// wait for the phase with the given parity, giving up after ~2^31 clock cycles (about a second)
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  const long long t0 = clock64();
+  while (true) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+}
+
+template <int VF>
+__global__ void __launch_bounds__(TMA_THREADS, 1) k_volume_f32_tma(const DgDevice d, const double *U, double *out,
+                                                                    double *g, int mode, int first, double dt,
+                                                                    double A, double B) {
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  float *P = reinterpret_cast<float *>(sm_raw + 2 * TB_BUF);
+  unsigned long long *bar = reinterpret_cast<unsigned long long *>(sm_raw + 2 * TB_BUF + TB_P);
+  __shared__ int s_ok;
+  const bool ns = d.equations == 1;
+  const bool needU = mode == 1, needG = mode == 1 && !first;
+  const unsigned bytes = TB_UF + TB_JA + TB_FS + (ns ? TB_FV : 0u) + (needU ? TB_U : 0u) + (needG ? TB_G : 0u);
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(smem_addr(&bar[0]));
+    mbar_init(smem_addr(&bar[1]));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // copies of element group k into buffer k & 1 (thread 0)
+  auto issue = [&](int k) {
+    const long long e = (long long)blockIdx.x + (long long)k * gridDim.x;
+    if (e >= d.nE) return;
+    unsigned char *b = sm_raw + (k & 1) * TB_BUF;
+    const unsigned mb = smem_addr(&bar[k & 1]);
+    mbar_expect_tx(mb, bytes);
+    bulk_g2s(smem_addr(b), d.Uf + e * 5 * nnn, TB_UF, mb);
+    bulk_g2s(smem_addr(b + TB_UF), d.Jaf + e * 9 * nnn, TB_JA, mb);
+    if (ns) bulk_g2s(smem_addr(b + TB_UF + TB_JA), d.Fv_f + e * 12 * nnn, TB_FV, mb);
+    bulk_g2s(smem_addr(b + TB_UF + TB_JA + TB_FV), d.Fsurf_f + e * 30 * nn, TB_FS, mb);
+    if (needU) bulk_g2s(smem_addr(b + TB_UF + TB_JA + TB_FV + TB_FS), U + e * 5 * nnn, TB_U, mb);
+    if (needG) bulk_g2s(smem_addr(b + TB_UF + TB_JA + TB_FV + TB_FS + TB_U), g + e * 5 * nnn, TB_G, mb);
+  };
+  if (tid == 0) {
+    issue(0);
+    issue(1);
+  }
+  for (int k = 0;; ++k) {
+    const long long e = (long long)blockIdx.x + (long long)k * gridDim.x;
+    if (e >= d.nE) break;
+    const unsigned mb = smem_addr(&bar[k & 1]), parity = (unsigned)((k >> 1) & 1);
+    if (tid == 0) s_ok = mbar_wait(mb, parity) ? 1 : 0;
+    __syncthreads();
+    if (!s_ok) {  // a copy never completed: report, wait (bounded) for the other buffer's copy, stop
+      if (tid == 0) {
+        flag_set(d.flag, 4);
+        if (e + gridDim.x < d.nE) mbar_wait(smem_addr(&bar[(k + 1) & 1]), (unsigned)(((k + 1) >> 1) & 1));
       }
-      if (id == 0 || id == N) {  // surface term: (1/w_b) times the outward face flux
-        const int f = 2 * dd + (id == N ? 1 : 0);
-        const int pp = dd == 0 ? ijk[1] : ijk[0], qq = dd == 2 ? ijk[1] : ijk[2];
-        const float *fs = Fsb + ((size_t)e * 6 + f) * 5 * nn + pp + n * qq;
-#pragma unroll
-        for (int v = 0; v < 5; ++v) s[v] += f_invw[id] * fs[v * nn];
-      }
-      if (ns) {
-        // viscous divergence along the line (zero diagonal: 2D/2 from the scaled table) and the
-        // neighbour's outward normal viscous flux -(1/(2 w_b)) phi_nb at the element faces
-        const float *Fvd = FS + (le * 12 + dd * 4) * PS + pb;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float acc = 0.0f;
-#pragma unroll
-          for (int m = 0; m < n; ++m) acc += 0.5f * f_D2[id * n + m] * Fvd[q * PS + m * sp];
-          s[1 + q] -= acc;
-        }
-        if (id == 0 || id == N) {
-          const int f = 2 * dd + (id == N ? 1 : 0);
-          const int pp = dd == 0 ? ijk[1] : ijk[0], qq = dd == 2 ? ijk[1] : ijk[2];
-          const int *ef = d.ef + ((size_t)e * 6 + f) * 4;
-          const int nb = ef[0], fnb = ef[1], o = ef[2];
-          if (nb < 0) {  // wall-model flux (see k_volume)
-            const float *fw = d.Fwall_f + (size_t)ef[3] * 4 * nn + pp + n * qq;
-            const float hs = (id == N) ? 0.5f : -0.5f;
-            const float *Fo = FS + (le * 12 + dd * 4) * PS + pn;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) s[1 + q] -= f_invw[id] * (fw[q * nn] - hs * Fo[q * PS]);
-            continue;
-          }
-          int p2, q2;
-          orient_map(o, pp, qq, p2, q2);
-          const int nbnode = face_node(fnb, p2, q2);
-          const float sg = (fnb & 1) ? 0.5f : -0.5f;
-          const float *Fvn = Fvb + ((size_t)nb * 12 + (fnb >> 1) * 4) * nnn + nbnode;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) s[1 + q] += f_invw[id] * sg * Fvn[q * nnn];
-        }
-      }
+      return;
     }
-    // Jacobian and output / LSERK(5,4) stage in FP64
-    const double miJ = -d.invJ[(size_t)e * nnn + node];
-    const size_t gi = (size_t)e * 5 * nnn + node;
-    if (mode == 0) {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) out[gi + v * nnn] = miJ * f2d_int(s[v]);
-    } else {
-      const double dtJ = dt * miJ;
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const double du = dtJ * f2d_int(s[v]);
-        const double gv = first ? du : A * g[gi + v * nnn] + du;
-        g[gi + v * nnn] = gv;
-        const double un = U[gi + v * nnn] + B * gv;
-        out[gi + v * nnn] = un;
-        d.Uf[gi + v * nnn] = d2f_int(v == 4 ? un - eref : un);
-      }
+    mbar_wait(mb, parity);  // completed: returns at once and orders this thread's reads after the copy
+    const unsigned char *b = sm_raw + (k & 1) * TB_BUF;
+    const float *Uf = reinterpret_cast<const float *>(b);
+    const float *Jb = reinterpret_cast<const float *>(b + TB_UF);
+    const float *Fb = reinterpret_cast<const float *>(b + TB_UF + TB_JA);
+    const float *Sb = reinterpret_cast<const float *>(b + TB_UF + TB_JA + TB_FV);
+    const double *Ub = reinterpret_cast<const double *>(b + TB_UF + TB_JA + TB_FV + TB_FS);
+    const double *Gb = reinterpret_cast<const double *>(b + TB_UF + TB_JA + TB_FV + TB_FS + TB_U);
+    if (tid < nnn) {
+      const float Uv[5] = {Uf[tid], Uf[nnn + tid], Uf[2 * nnn + tid], Uf[3 * nnn + tid], Uf[4 * nnn + tid]};
+      f32_stage<VF>(d, Uv, P + tid);
     }
+    __syncthreads();
+    if (tid < nnn) {
+      float s[5];
+      f32_node_terms<VF>(d, P, Jb, Fb, Sb, (int)e, tid, s);
+      f32_finish(d, Ub, Gb, out, g, (int)e, tid, s, mode, first, dt, A, B);
+    }
+    __syncthreads();  // buffer k & 1 and P are free again
+    if (tid == 0) issue(k + 2);
   }
 }
 
@@ -1449,7 +1591,22 @@ void launch_volume_t(const DgDevice &d, const double *U, double *out, double *g,
 template <int VF>
 void launch_volume_f32(const DgDevice &d, const double *U, double *out, double *g, int mode, int first, double dt,
                        double A, double B, cudaStream_t s) {
-  const size_t smem = sizeof(float) * NODE_EPB * NODE_SLOTS * PS;
+  const bool aligned = !(((uintptr_t)U | (uintptr_t)out | (uintptr_t)g) & 15u);
+  if (TMA_OK && d.use_tma && aligned) {
+    static int grid = 0;  // persistent: CTAs resident on all SMs at once
+    if (!grid) {
+      cudaFuncSetAttribute(k_volume_f32_tma<VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TB_SMEM);
+      int dev = 0, sms = 0, per_sm = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_volume_f32_tma<VF>, TMA_THREADS, TB_SMEM);
+      grid = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const int blocks = d.nE < grid ? d.nE : grid;
+    k_volume_f32_tma<VF><<<blocks, TMA_THREADS, TB_SMEM, s>>>(d, U, out, g, mode, first, dt, A, B);
+    return;
+  }
+  const size_t smem = sizeof(float) * NODE_EPB * NODE_SLOTS * nnn;
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_volume_f32<VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -91,6 +91,8 @@ def lib() -> ctypes.CDLL:
             "dg_adjoint_memory_limit": (i, [vp, d]),
             "dg_check_conversions": (i, [vp, ctypes.c_longlong, vp]),
             "dg_wall_model": (i, [i, vp, vp, vp, d, d, d, d, i, vp, vp, vp]),
+            "dg_use_graphs": (i, [vp, i]),
+            "dg_use_tma": (i, [vp, i]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -301,6 +303,12 @@ class DG:
         self._check(lib().dg_get_metrics(self._ctx, ctypes.c_void_p(Ja.data_ptr()), ctypes.c_void_p(J.data_ptr())),
                     "dg_get_metrics")
         return Ja, J
+
+    def use_tma(self, on=True):
+        self._check(lib().dg_use_tma(self._ctx, int(bool(on))), "dg_use_tma")
+
+    def use_graphs(self, on=True):
+        self._check(lib().dg_use_graphs(self._ctx, int(bool(on))), "dg_use_graphs")
 
     def timing_enable(self, on=True):
         self._check(lib().dg_timing_enable(self._ctx, int(bool(on))), "dg_timing_enable")
