@@ -36,10 +36,10 @@ UNIT = "DOF-stage/s"
 STAGES = 5
 P0_TGV = 1.0 / (1.4 * 0.1 ** 2)  # background pressure of the Ma 0.1 Taylor-Green vortex
 # DRAM bytes per element of one volume-kernel launch (dram__bytes_read.sum + dram__bytes_write.sum),
-# from an ncu capture of the current kernel on the 16^3 case (profiles/k_volume_tgv_ns_n7_16x16x16.md),
+# from an ncu capture of the current kernel on the 16^3 case (profiles/launch_list_tgv_ns_n7_32x32x32.md),
 # scaled to a launch by the element count (the kernel's traffic is per element). None once the kernel
 # has changed since that capture.
-VOLUME_DRAM_BYTES_PER_ELEMENT = 745.4e6 / 16 ** 3
+VOLUME_DRAM_BYTES_PER_ELEMENT = 661.0e6 / 16 ** 3
 
 
 def volume_kernel_flops_per_element(N: int, navier_stokes: bool) -> float:
@@ -295,6 +295,44 @@ def run_adjoint(stream, peak_fp64: float, interval: int = 10) -> dict:
                         for k, v in kt.items() if v[1]}}
 
 
+def run_other_workloads(stream) -> dict:
+    """Throughput of the other named workloads (the benchmark table's remaining rows): the small N=3
+    Euler case (launch bound; CUDA-graph replay on), the blast with DG/FV blending at 64^3 (as named)
+    and 40^3 (the size the quoted DOF count implies), and the FP32-bulk 48^3 form."""
+    import torch
+
+    from paper_2306_12891_gb300 import dg
+
+    cases = [("tgv_euler_n3_4x4x4", None, 200, {}), ("blast_euler_fv_n5_64x64x64", None, 5, {}),
+             ("blast_euler_fv_n5_64x64x64", 40, 5, {}),
+             ("tgv_ns_n7_48x48x48_curved_fp32", None, 5, dict(precision="fp32_bulk", p_ref=P0_TGV))]
+    out = {}
+    for name, nel, steps, extra in cases:
+        w = WORKLOADS[name] if nel is None else WORKLOADS[name].with_(nel=(nel,) * 3)
+        xyz, faces = w.mesh()
+        s = dg.DG(w.N, xyz, faces, stream=stream, **extra, **w.physics())
+        U = torch.from_numpy(w.initial_state(xyz)).cuda()
+        dt = s.max_dt(U, w.cfl)
+        s.lserk_steps(U, dt, 3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.lserk_steps(U, dt, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s.check()
+        ms = e0.elapsed_time(e1) / steps
+        key = name if nel is None else f"{name} at {nel}^3"
+        row = {"N": w.N, "elements": w.n_elems, "dofs": w.dofs, "steps": steps, "ms_per_step": ms,
+               "value": w.dofs * STAGES / (ms * 1e-3), "unit": UNIT, "precision": extra.get("precision", "fp64")}
+        if w.shock_capturing:
+            alpha = s.indicator(U)
+            row["troubled_fraction"] = float((alpha > 0).double().mean())
+        out[key] = row
+        del s
+    return out
+
+
 WALL_WORKLOAD = "channel_wm_ns_n5_48x24x24"
 
 
@@ -476,6 +514,8 @@ def run_gpu(args):
         line["adjoint"] = run_adjoint(stream, peak_fp64)
     if args.wall and not args.nel and world == 1:
         line["wall_model"] = run_wall_model(stream)
+    if args.others and not args.nel and world == 1:
+        line["other_workloads"] = run_other_workloads(stream)
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -491,6 +531,7 @@ def main():
     ap.add_argument("--no-fp32", dest="fp32", action="store_false", help="skip the FP32-bulk comparison")
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false", help="skip the adjoint (gradient) block")
     ap.add_argument("--no-wall", dest="wall", action="store_false", help="skip the wall-model cost block")
+    ap.add_argument("--no-others", dest="others", action="store_false", help="skip the other workloads' throughput")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk"])
     ap.add_argument("--nel", type=int, default=None, help="elements per direction (default: the workload's 32)")
