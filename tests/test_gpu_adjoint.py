@@ -270,6 +270,43 @@ def test_kinetic_energy_gradient_full_size_finite_differences(env):
     gpu.check()
 
 
+def test_full_size_vjp_sampled_columns(env):
+    """The adjoint at the differentiation workload's full size (N = 5, 24^3, 3.0M DOF): sampled entries
+    of (dL/dU)^T lambda against complex-step columns of the oracle. Column j of dL/dU is nonzero only
+    on the element of node j and its first and second face neighbours (BR1 reaches across two faces),
+    so the oracle evaluates the right-hand side on those elements alone."""
+    dg, orc, torch = env
+    w = W.WORKLOADS["tgv_ns_n5_24x24x24_adjoint"]
+    xyz, faces = w.mesh()
+    U = w.initial_state(xyz)
+    lam = np.random.default_rng(24).standard_normal(U.shape)
+    gpu = _gpu(env, w.N, xyz, faces, **w.physics())
+    got = gpu.rhs_vjp(torch.from_numpy(U).cuda(), torch.from_numpy(lam).cuda()).cpu().numpy().reshape(-1)
+    gpu.check()
+    oc = orc.Oracle(w.N, xyz, faces, complex_step=True, **w.physics())
+    nbr = {}
+    for eL, fL, eR, fR, o in faces:
+        nbr.setdefault(int(eL), set()).add(int(eR))
+        nbr.setdefault(int(eR), set()).add(int(eL))
+    nnn = (w.N + 1) ** 3
+    cols = np.sort(np.random.default_rng(25).choice(U.size, size=12, replace=False))
+    ref, scl = np.zeros(len(cols)), np.zeros(len(cols))
+    Z = U.astype(np.complex128)
+    for k, j in enumerate(cols):
+        e = int(j // (5 * nnn))
+        mask = {e} | nbr[e]
+        for m in list(mask):
+            mask |= nbr[m]
+        mask = sorted(mask)
+        flat = Z.reshape(-1)
+        flat[j] += 1j * CS_H
+        col = oc.rhs(Z, mask=mask).imag[mask] / CS_H
+        flat[j] = U.reshape(-1)[j]
+        ref[k] = (col * lam[mask]).sum()
+        scl[k] = (np.abs(col) * np.abs(lam[mask])).sum()
+    _compare(got[cols], U, cols, ref, scl, "full size 24^3 sampled columns")
+
+
 def test_conservation_of_the_adjoint_full_size(env):
     """Periodic meshes conserve sum_i J_i w_i Ut_i for every U, so lambda = J w e_v is in the left
     null space of dL/dU: its VJP vanishes (benchmark workload, N = 7, 32^3, curved)."""

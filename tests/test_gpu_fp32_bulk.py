@@ -191,3 +191,24 @@ def test_tma_kernel_with_walls(env):
         res.append(s.rhs(U0))
         s.check()
     assert torch.equal(res[0], res[1])
+
+
+def test_full_size_fp32_rhs_sampled(env):
+    """The FP32-bulk form at its full size (N = 7, 48^3 curved, 56.6M DOF, the launch configuration
+    bench.py times) against the FP64 oracle on a sample of elements (box corners and random ones)."""
+    dg, orc, torch = env
+    w = W.WORKLOADS["tgv_ns_n7_48x48x48_curved_fp32"]
+    xyz, faces = w.mesh()
+    U0 = w.initial_state(xyz)
+    gpu = dg.DG(w.N, xyz, faces, precision="fp32_bulk", p_ref=P0_TGV, **w.physics())
+    Ut = gpu.rhs(torch.from_numpy(U0).cuda()).cpu().numpy()
+    gpu.check()
+    nx, ny, nz = w.nel
+    corners = [0, nx - 1, nx * ny - 1, nx * ny * nz - 1]
+    sample = sorted(set(corners + list(np.random.default_rng(48).choice(w.n_elems, 8, replace=False))))
+    ref = orc.Oracle(w.N, xyz, faces, **w.physics())
+    Ur = ref.rhs(U0, mask=sample)
+    scale = flux_scale(U0[sample], ref.Ja[sample], ref.J[sample], orc.dmatrix(w.N))
+    err = parity(Ut[sample], Ur[sample], scale)
+    print(f"PARITY32 full size 48^3: {err}")
+    assert (err <= TOL32).all(), err
