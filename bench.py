@@ -185,6 +185,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+THROTTLE_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
+
+
+def throttled(clk: dict) -> bool:
+    """Clock record of a timed region that must not be reported: a hardware or thermal slowdown, or
+    SM clocks held well below their maximum with no reason given (a leftover clock lock)."""
+    if any(r in THROTTLE_REASONS for r in clk.get("reasons", [])):
+        return True
+    sm, smax = clk.get("sm_mhz"), clk.get("sm_max_mhz")
+    return bool(sm and smax and sm < 0.8 * smax and not clk.get("reasons"))
+
+
 def cpu_baseline(steps_budget_s: float = 15.0) -> dict:
     """The FP64 oracle, as it stands, single-threaded on the host: LSERK(5,4) stages of the same
     physics on a 6^3-element sub-box of the workload (110,592 DOF), until ~steps_budget_s."""
@@ -397,26 +409,33 @@ def run_gpu(args):
     # device-resident timed region
     solver.lserk_steps(U, dt, args.warmup)
     solver.check()
-    torch.cuda.synchronize()
-    barrier(world)
-    clocks = ClockSampler(local)
-    solver.timing_enable(True)
-    solver.timing_get()  # reset
-    l0 = solver.launch_count()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    solver.lserk_steps(U, dt, args.steps, t=args.warmup * dt)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    ms = e0.elapsed_time(e1)
-    clk = clocks.stop()
-    launches = solver.launch_count() - l0
-    ktimes = solver.timing_get()
-    solver.timing_enable(False)
-    solver.check()
-    ms = max_over_ranks(world, ms)
+
+    def timed_region():
+        torch.cuda.synchronize()
+        barrier(world)
+        clocks = ClockSampler(local)
+        solver.timing_enable(True)
+        solver.timing_get()  # reset
+        l0 = solver.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        solver.lserk_steps(U, dt, args.steps, t=args.warmup * dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms_ = e0.elapsed_time(e1)
+        clk_ = clocks.stop()
+        launches_ = solver.launch_count() - l0
+        ktimes_ = solver.timing_get()
+        solver.timing_enable(False)
+        solver.check()
+        return max_over_ranks(world, ms_), clk_, launches_, ktimes_
+
+    ms, clk, launches, ktimes = timed_region()
+    if throttled(clk) and world == 1:  # a throttled region is measured once more (same step count)
+        ms, clk, launches, ktimes = timed_region()
+        clk["remeasured"] = True
 
     # end to end through the host-buffer entry point: copies in and out every step
     Uh = torch.from_numpy(U.cpu().numpy()).pin_memory()

@@ -44,3 +44,15 @@ def test_two_replicas_gloo():
         assert p.exitcode == 0
     assert [r[1] for r in res] == [2.0, 2.0]            # both ranks see the slowest rank's time
     assert [r[2] for r in res] == [1000.0, 1000.0]      # 2 x 1000 units / 2 s
+
+
+def test_throttle_rule():
+    """Timed regions whose clock record shows a hardware/thermal slowdown, or SM clocks held well
+    below their maximum with no reason (a leftover lock), are measured again; a power cap is kept."""
+    import bench
+
+    assert bench.throttled({"reasons": ["hw_thermal_slowdown"], "sm_mhz": 2070, "sm_max_mhz": 2070})
+    assert bench.throttled({"reasons": [], "sm_mhz": 1100.0, "sm_max_mhz": 2070.0})
+    assert not bench.throttled({"reasons": ["sw_power_cap"], "sm_mhz": 1500.0, "sm_max_mhz": 2070.0})
+    assert not bench.throttled({"reasons": [], "sm_mhz": 2070.0, "sm_max_mhz": 2070.0})
+    assert not bench.throttled({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]})
