@@ -59,6 +59,23 @@ def volume_kernel_flops_per_element(N: int, navier_stokes: bool) -> float:
     return 45.0 * pairs + per_node * n ** 3 + per_face_pt * 6 * n * n
 
 
+def lift_kernel_flops_per_element(N: int) -> float:
+    """Algorithmic FP64 flops of one BR1 lifting launch per element (FMA = 2), from the kernel's
+    statements: primitives and T 15 per node; per direction and lifted variable a D sweep of n FMA
+    and the metric contraction 3 FMA (12 (2n + 6) per node); surface terms 4 x (1 mul + 3 FMA) = 28
+    per (node, face) pair, 6 n^2 pairs per element; 1/J 12; viscous flux 43; contravariant flux
+    12 x (mul + 2 FMA) = 60."""
+    n = N + 1
+    return (15 + 12 * (2 * n + 6) + 12 + 43 + 60) * n ** 3 + 28 * 6 * n * n
+
+
+def face_kernel_flops_per_point() -> float:
+    """Algorithmic FP64 flops per face point of the face kernel for Roe + Navier-Stokes, from its
+    statements: two Euler fluxes 2 x 29, Roe averages, wave strengths and dissipation 149, the two
+    outward slot values 10, the BR1 jumps of (u, v, w, T) 40."""
+    return 58.0 + 149.0 + 10.0 + 40.0
+
+
 def adjoint_volume_flops_per_element(N: int, navier_stokes: bool) -> float:
     """Algorithmic FP64 flops of one adjoint-volume launch per element (FMA = 2 flops), counted from
     the statements of the kernel:
@@ -250,6 +267,20 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def step_roofline(N: int, dof_stage_per_s: float, peak_fp64: float) -> dict:
+    """Whole-step FP64 roofline of the Navier-Stokes step (Pirozzoli, Roe, BR1, periodic box): the
+    algorithmic flops of the volume, lifting and face kernels per DOF and stage against the measured
+    FP64 peak; PID_roof = flops / peak and frac = PID_roof / PID_measured."""
+    n = N + 1
+    nodes = n ** 3
+    flops = (volume_kernel_flops_per_element(N, True) + lift_kernel_flops_per_element(N) +
+             face_kernel_flops_per_point() * 3 * n * n) / nodes
+    pid = 1.0 / dof_stage_per_s
+    return {"bound": "alu", "flops_per_dof_stage": flops, "pid_roof_s": flops / peak_fp64, "pid_s": pid,
+            "frac": flops / peak_fp64 / pid, "peak": peak_fp64 / 1e12, "unit": "TFLOP/s",
+            "peak_source": "measured FP64 FMA probe (dg_probe_fma), live"}
 
 
 ADJOINT_WORKLOAD = "tgv_ns_n5_24x24x24_adjoint"
@@ -520,6 +551,7 @@ def run_gpu(args):
                    "l2": f"inputs larger than L2 (state {state_bytes / 1e6:.0f} MB, working set > 5 GB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "pid_s_per_dof_stage": 1.0 / (value / world),
+        "step_roofline": step_roofline(w.N, value / world, peak_fp64) if not fp32_main else None,
         "roofline": roofline,
         "kernels": breakdown,
         "gpu_launches": launches,
