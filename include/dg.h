@@ -184,6 +184,20 @@ dg_status dg_lserk_steps_vjp(dg_ctx *ctx, const double *U0, double *Ubar, double
  * already allocated are kept. */
 dg_status dg_adjoint_memory_limit(dg_ctx *ctx, double bytes);
 
+/* The forward run recorded for a later reverse sweep (what an autograd framework does): advances U
+ * by n_steps LSERK steps like dg_lserk_steps and keeps, in library buffers, every stage state when
+ * 5 n_steps state buffers fit in the adjoint's memory budget (dg_adjoint_memory_limit), else the
+ * state every `interval` steps. *tape identifies the recording; a new recording invalidates the
+ * previous one. */
+dg_status dg_lserk_steps_record(dg_ctx *ctx, double *U, double dt, double t, int n_steps, int interval,
+                                long long *tape);
+
+/* Reverse of a recorded run: Ubar (cotangent of the final state) -> cotangent of the initial state.
+ * With every stage state recorded this is 5 n_steps vector-Jacobian products and no recomputation;
+ * from checkpoints, each segment is recomputed once (as dg_lserk_steps_vjp). DG_ERR_ARG if the tape
+ * has been recorded over. */
+dg_status dg_lserk_steps_vjp_recorded(dg_ctx *ctx, long long tape, double *Ubar);
+
 /* grad = d/dU of the kinetic-energy integral sum J w rho|u|^2/2 (out[6] of dg_invariants). */
 dg_status dg_kinetic_energy_grad(dg_ctx *ctx, const double *U, double *grad);
 

@@ -6,8 +6,10 @@ against central finite differences of the forward solver, with timings.
 
 Workload: Navier-Stokes (Pirozzoli split form, Roe, BR1) at N = 5 on the curved 24^3 mesh, a
 Taylor-Green base state with a seeded perturbation from its lowest four Fourier modes (amplitude
-1e-2); objective J(U0) = sum J w rho|u|^2/2 at step K. The gradient comes from
-dg_kinetic_energy_grad at U_K followed by dg_lserk_steps_vjp (checkpoints every `interval` steps).
+1e-2); objective J(U0) = sum J w rho|u|^2/2 at step K. The gradient comes from a recorded forward
+run (dg_lserk_steps_record), dg_kinetic_energy_grad at U_K and dg_lserk_steps_vjp_recorded; the
+same gradient from U0 alone (checkpoints every `interval` steps, dg_lserk_steps_vjp) is timed too
+and must agree bit for bit.
 Each of the seeded smooth directions v is checked against (J(U0 + eps v) - J(U0 - eps v)) / (2 eps)
 computed with dg_lserk_steps.
 """
@@ -42,15 +44,27 @@ def run(steps: int = 50, interval: int = 10, directions: int = 20, eps: float = 
         UK = s.lserk_steps(U.clone(), dt, steps)
         return s.invariants(UK, UK)[6]
 
-    def gradient():
+    def gradient():  # recorded forward run, then the reverse sweep (no recomputation when HBM holds the tape)
+        UK = U0.clone()
+        tape = s.lserk_steps_record(UK, dt, steps, interval)
+        g = s.kinetic_energy_grad(UK)
+        s.lserk_steps_vjp_recorded(tape, g)
+        return g
+
+    def gradient_from_u0():  # checkpoints every `interval` steps, each segment recomputed once
         UK = s.lserk_steps(U0.clone(), dt, steps)
         g = s.kinetic_energy_grad(UK)
         s.lserk_steps_vjp(U0, g, dt, steps, interval)
         return g
 
-    gradient()  # warm-up (allocates the checkpoint buffers)
+    gradient()  # warm-up (allocates the tape and work buffers)
+    gradient_from_u0()
     torch.cuda.synchronize()
     free1 = torch.cuda.mem_get_info()[0]
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record()
+    g_ckpt = gradient_from_u0()
+    c1.record()
     e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     e[0].record()
     J0 = objective(U0)
@@ -64,6 +78,8 @@ def run(steps: int = 50, interval: int = 10, directions: int = 20, eps: float = 
     kt = s.timing_get()
     s.timing_enable(False)
     fwd_ms, grad_ms = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+    ckpt_ms = c0.elapsed_time(c1)
+    assert torch.equal(g, g_ckpt), "recorded and checkpointed gradients differ"
     # one plain VJP of the right-hand side (kernel throughput)
     lam = torch.randn_like(U0)
     s.rhs_vjp(U0, lam)
@@ -93,7 +109,8 @@ def run(steps: int = 50, interval: int = 10, directions: int = 20, eps: float = 
     return {"workload": workload if not nel else f"{workload} reduced to {nel}^3", "N": w.N,
             "elements": w.n_elems, "dofs": w.dofs, "steps": steps, "interval": interval, "dt": dt,
             "objective": J0, "eps": eps, "forward_ms": fwd_ms, "gradient_ms": grad_ms,
-            "gradient_over_forward": grad_ms / fwd_ms, "rhs_ms": rhs_ms, "rhs_vjp_ms": vjp_ms,
+            "gradient_over_forward": grad_ms / fwd_ms, "gradient_from_u0_checkpointed_ms": ckpt_ms,
+            "rhs_ms": rhs_ms, "rhs_vjp_ms": vjp_ms,
             "vjp_over_rhs": vjp_ms / rhs_ms,
             "library_memory_gb": (free0 - free1) / 1e9,
             "gradient_kernels": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in kt.items() if v[1]},

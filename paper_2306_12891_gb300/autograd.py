@@ -1,8 +1,9 @@
 """torch.autograd bindings of the solver's discrete adjoint (argument marshalling only).
 
     Ut = rhs(dg, U)                              backward: dg_rhs_vjp
-    UK = lserk_steps(dg, U0, dt, K, interval)    backward: dg_lserk_steps_vjp (two-level checkpointing:
-                                                 recomputes from U0, keeps ceil(K/interval) + interval states)
+    UK = lserk_steps(dg, U0, dt, K, interval)    forward: dg_lserk_steps_record (every stage state in HBM
+                                                 when it fits, else checkpoints every `interval` steps);
+                                                 backward: dg_lserk_steps_vjp_recorded
     KE = kinetic_energy(dg, U)                   sum J w rho|u|^2/2; backward: dg_kinetic_energy_grad
 
 `dg` is a paper_2306_12891_gb300.dg.DG context (FP64, no shock capturing, KG or Pirozzoli volume
@@ -33,13 +34,20 @@ class _Steps(torch.autograd.Function):
         U0 = U0.detach().contiguous()
         ctx.dg, ctx.dt, ctx.n_steps, ctx.interval = dg, float(dt), int(n_steps), int(interval)
         ctx.save_for_backward(U0)
-        return dg.lserk_steps(U0.clone(), dt, n_steps)
+        UK = U0.clone()
+        if ctx.n_steps > 0:  # record the run (every stage state if it fits, else checkpoints)
+            ctx.tape = dg.lserk_steps_record(UK, dt, n_steps, interval)
+        return UK
 
     @staticmethod
     def backward(ctx, grad_out):
         (U0,) = ctx.saved_tensors
         Ubar = grad_out.detach().contiguous().clone()
-        ctx.dg.lserk_steps_vjp(U0, Ubar, ctx.dt, ctx.n_steps, ctx.interval)
+        if ctx.n_steps > 0:
+            try:
+                ctx.dg.lserk_steps_vjp_recorded(ctx.tape, Ubar)
+            except Exception:  # the tape was recorded over by a later forward: recompute from U0
+                ctx.dg.lserk_steps_vjp(U0, Ubar, ctx.dt, ctx.n_steps, ctx.interval)
         return Ubar, None, None, None, None
 
 

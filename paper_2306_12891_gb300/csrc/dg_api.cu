@@ -72,6 +72,12 @@ struct dg_ctx {
   // adjoint: library-owned state buffers (stage states, gbar, checkpoints), allocated on first use
   std::vector<double *> adj_pool;
   size_t adj_limit = 0;        // bytes the adjoint's state buffers may use (0: free memory less 10%)
+  // recorded forward run (dg_lserk_steps_record): every stage state, or checkpoints
+  std::vector<double *> tape_pool;
+  long long tape_id = 0, tape_serial = 0;
+  int tape_steps = 0, tape_interval = 0;
+  bool tape_all = false;
+  double tape_dt = 0.0;
   // CUDA graph of one LSERK step, replayed by the multi-step calls on a library stream that is
   // ordered after (and before) the caller's stream with events
   int use_graphs = 1;
@@ -219,12 +225,72 @@ dg_status reverse_stages(dg_ctx *c, double *const S[5], double *Ubar, double dt)
   return DG_OK;
 }
 
+dg_status steps_impl(dg_ctx *c, double *U, double dt, int n_steps);
+
+// whether `buffers` state buffers fit in the adjoint's memory budget, counting `have` already held
+bool budget_allows(dg_ctx *c, size_t buffers, size_t have) {
+  const size_t state_bytes = sizeof(double) * c->n_state;
+  if (c->adj_limit) return buffers * state_bytes <= c->adj_limit;
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const size_t extra = buffers > have ? (buffers - have) * state_bytes : 0;
+  return extra + total_b / 10 < free_b;
+}
+
+// at least `count` library-owned state buffers in `pool`
+dg_status pool_fill(dg_ctx *c, std::vector<double *> &pool, size_t count) {
+  while (pool.size() < count) {
+    double *p = nullptr;
+    DG_TRY(dev_alloc(c, &p, c->n_state));
+    pool.push_back(p);
+  }
+  return DG_OK;
+}
+
 // reverse of one LSERK step from U, recomputing its four inner stage states into pool[0..3]
 dg_status step_vjp(dg_ctx *c, const double *U, double *Ubar, double dt) {
   DG_TRY(adj_pool(c, 5));
   double *S[5] = {const_cast<double *>(U), c->adj_pool[0], c->adj_pool[1], c->adj_pool[2], c->adj_pool[3]};
   for (int st = 0; st < 4; ++st) DG_TRY(stage(c, S[st], S[st + 1], 1, st, dt));
   return reverse_stages(c, S, Ubar, dt);
+}
+
+// Reverse sweep over n_steps from checkpoints cp[j] = state at step j * interval: each segment is
+// recomputed once from its checkpoint and reversed step by step. When the budget allows, the
+// recomputation keeps all five stage states of the segment (5 interval buffers); otherwise the step
+// start states only (interval - 1 buffers) and each step's stages are recomputed before reversal.
+// Segment buffers live in the adjoint pool from index `first` on.
+dg_status reverse_from_checkpoints(dg_ctx *c, const std::vector<double *> &cp, int interval, int n_steps,
+                                   double *Ubar, double dt, size_t first) {
+  const int ncp = (int)cp.size();
+  const bool store = budget_allows(c, first + 5 * (size_t)interval, c->adj_pool.size() + c->tape_pool.size());
+  DG_TRY(adj_pool(c, first + (store ? 5 * (size_t)interval : (size_t)interval - 1)));
+  double **seg = c->adj_pool.data() + first;
+  for (int j = ncp - 1; j >= 0; --j) {
+    const int len = std::min(interval, n_steps - j * interval);
+    if (store) {
+      // S(i, s): input state of stage s of step i of the segment; S(0, 0) is the checkpoint
+      auto S = [&](int i, int st) { return (i == 0 && st == 0) ? cp[j] : seg[5 * i + st]; };
+      for (int i = 0; i < len; ++i)
+        for (int st = 0; st < 5; ++st) {
+          if (i == len - 1 && st == 4) break;  // the segment's end state is not needed
+          double *out = st < 4 ? S(i, st + 1) : S(i + 1, 0);
+          DG_TRY(stage(c, S(i, st), out, 1, st, dt));
+        }
+      for (int i = len - 1; i >= 0; --i) {
+        double *st5[5] = {S(i, 0), S(i, 1), S(i, 2), S(i, 3), S(i, 4)};
+        DG_TRY(reverse_stages(c, st5, Ubar, dt));
+      }
+    } else {
+      auto state = [&](int i) { return i == 0 ? cp[j] : seg[i - 1]; };
+      for (int i = 1; i < len; ++i) {
+        DG_TRY(copy_state(c, state(i), state(i - 1)));
+        DG_TRY(steps_impl(c, state(i), dt, 1));
+      }
+      for (int i = len - 1; i >= 0; --i) DG_TRY(step_vjp(c, state(i), Ubar, dt));
+    }
+  }
+  return DG_OK;
 }
 }  // namespace
 
@@ -440,6 +506,8 @@ dg_status dg_init(const dg_mesh *mesh, int N, int nodes, const dg_params *prm, v
   return DG_OK;
 }
 
+}  // extern "C"
+
 namespace {
 // FP32-bulk: refresh the FP32 shadow of a caller state (the volume kernel keeps it current afterwards)
 dg_status refresh_shadow(dg_ctx *c, const double *U) {
@@ -512,6 +580,8 @@ dg_status steps_impl(dg_ctx *c, double *U, double dt, int n_steps) {
 }
 }  // namespace
 
+extern "C" {
+
 dg_status dg_rhs(dg_ctx *c, const double *U, double *Ut, double t) {
   (void)t;
   if (!c || !U || !Ut || U == Ut) return fail(c, DG_ERR_ARG, "dg_rhs: null or aliased arrays");
@@ -568,54 +638,73 @@ dg_status dg_lserk_steps_vjp(dg_ctx *c, const double *U0, double *Ubar, double d
   if (n_steps == 0) return DG_OK;
   if (interval > n_steps) interval = n_steps;
   const int ncp = (n_steps + interval - 1) / interval;
-  // Keep all five stage states of a segment when they fit (HBM is large): the segment's
-  // recomputation then yields every state the reverse sweep needs. Otherwise keep only the step
-  // start states and recompute each step's stages before reversing it.
-  const size_t state_bytes = sizeof(double) * c->n_state;
-  const size_t have = c->adj_pool.size();
-  const size_t want_store = 5 + (size_t)ncp + 5 * (size_t)interval;
-  bool store;
-  if (c->adj_limit) {
-    store = want_store * state_bytes <= c->adj_limit;
-  } else {
-    size_t free_b = 0, total_b = 0;
-    cudaMemGetInfo(&free_b, &total_b);
-    const size_t extra = want_store > have ? (want_store - have) * state_bytes : 0;
-    store = extra + total_b / 10 < free_b;
-  }
-  DG_TRY(adj_pool(c, store ? want_store : 5 + (size_t)ncp + (size_t)interval - 1));
-  double **cp = c->adj_pool.data() + 5, **seg = cp + ncp;
+  DG_TRY(adj_pool(c, 5 + (size_t)ncp));
+  double **cp = c->adj_pool.data() + 5;
   // forward sweep: checkpoints every `interval` steps
   DG_TRY(copy_state(c, cp[0], U0));
   for (int j = 1; j < ncp; ++j) {
     DG_TRY(copy_state(c, cp[j], cp[j - 1]));
     DG_TRY(steps_impl(c, cp[j], dt, interval));
   }
-  for (int j = ncp - 1; j >= 0; --j) {
-    const int len = std::min(interval, n_steps - j * interval);
-    if (store) {
-      // S(i, s): input state of stage s of step i of the segment; S(0, 0) is the checkpoint
-      auto S = [&](int i, int st) { return (i == 0 && st == 0) ? cp[j] : seg[5 * i + st]; };
-      for (int i = 0; i < len; ++i)
-        for (int st = 0; st < 5; ++st) {
-          if (i == len - 1 && st == 4) break;  // the segment's end state is not needed
-          double *out = st < 4 ? S(i, st + 1) : S(i + 1, 0);
-          DG_TRY(stage(c, S(i, st), out, 1, st, dt));
-        }
-      for (int i = len - 1; i >= 0; --i) {
-        double *st5[5] = {S(i, 0), S(i, 1), S(i, 2), S(i, 3), S(i, 4)};
-        DG_TRY(reverse_stages(c, st5, Ubar, dt));
+  std::vector<double *> cps(cp, cp + ncp);  // (the pool may grow below)
+  return reverse_from_checkpoints(c, cps, interval, n_steps, Ubar, dt, 5 + ncp);
+}
+
+dg_status dg_lserk_steps_record(dg_ctx *c, double *U, double dt, double t, int n_steps, int interval,
+                                long long *tape) {
+  (void)t;
+  if (!c || !U || !tape || n_steps < 1 || interval < 1 || !std::isfinite(dt))
+    return fail(c, DG_ERR_ARG, "dg_lserk_steps_record: bad argument");
+  DG_TRY(adjoint_supported(c, "dg_lserk_steps_record"));
+  c->tape_id = 0;  // any earlier tape is invalid from here on
+  if (interval > n_steps) interval = n_steps;
+  const size_t full = 5 * (size_t)n_steps, ncp = (size_t)((n_steps + interval - 1) / interval);
+  // every stage state when the budget holds them (and the reverse sweep's 5 scratch buffers), else
+  // checkpoints every `interval` steps
+  const bool store_all = budget_allows(c, full + 5, c->tape_pool.size() + c->adj_pool.size());
+  DG_TRY(pool_fill(c, c->tape_pool, store_all ? full : ncp));
+  double **T = c->tape_pool.data();
+  if (store_all) {
+    DG_TRY(copy_state(c, T[0], U));
+    for (int k = 0; k < n_steps; ++k)
+      for (int st = 0; st < 5; ++st) {
+        double *out = st < 4 ? T[5 * k + st + 1] : (k + 1 < n_steps ? T[5 * (k + 1)] : U);
+        DG_TRY(stage(c, T[5 * k + st], out, 1, st, dt));
       }
-    } else {
-      auto state = [&](int i) { return i == 0 ? cp[j] : seg[i - 1]; };
-      for (int i = 1; i < len; ++i) {
-        DG_TRY(copy_state(c, state(i), state(i - 1)));
-        DG_TRY(steps_impl(c, state(i), dt, 1));
-      }
-      for (int i = len - 1; i >= 0; --i) DG_TRY(step_vjp(c, state(i), Ubar, dt));
+  } else {
+    for (int j = 0; j < (int)ncp; ++j) {
+      DG_TRY(copy_state(c, T[j], U));
+      DG_TRY(steps_impl(c, U, dt, std::min(interval, n_steps - j * interval)));
     }
   }
+  c->tape_steps = n_steps;
+  c->tape_interval = interval;
+  c->tape_all = store_all;
+  c->tape_dt = dt;
+  c->tape_id = ++c->tape_serial;
+  *tape = c->tape_id;
   return DG_OK;
+}
+
+dg_status dg_lserk_steps_vjp_recorded(dg_ctx *c, long long tape, double *Ubar) {
+  if (!c || !Ubar) return fail(c, DG_ERR_ARG, "dg_lserk_steps_vjp_recorded: bad argument");
+  if (tape <= 0 || tape != c->tape_id)
+    return fail(c, DG_ERR_ARG, "dg_lserk_steps_vjp_recorded: no such tape (recorded over or never recorded)");
+  DG_TRY(adjoint_supported(c, "dg_lserk_steps_vjp_recorded"));
+  const int n_steps = c->tape_steps;
+  const double dt = c->tape_dt;
+  if (c->tape_all) {
+    DG_TRY(adj_pool(c, 5));  // gbar
+    double **T = c->tape_pool.data();
+    for (int k = n_steps - 1; k >= 0; --k) {
+      double *S[5] = {T[5 * k], T[5 * k + 1], T[5 * k + 2], T[5 * k + 3], T[5 * k + 4]};
+      DG_TRY(reverse_stages(c, S, Ubar, dt));
+    }
+    return DG_OK;
+  }
+  const int ncp = (n_steps + c->tape_interval - 1) / c->tape_interval;
+  std::vector<double *> cps(c->tape_pool.begin(), c->tape_pool.begin() + ncp);
+  return reverse_from_checkpoints(c, cps, c->tape_interval, n_steps, Ubar, dt, 5);
 }
 
 dg_status dg_adjoint_memory_limit(dg_ctx *c, double bytes) {

@@ -92,6 +92,8 @@ def lib() -> ctypes.CDLL:
             "dg_check_conversions": (i, [vp, ctypes.c_longlong, vp]),
             "dg_wall_model": (i, [i, vp, vp, vp, d, d, d, d, i, vp, vp, vp]),
             "dg_use_graphs": (i, [vp, i]),
+            "dg_lserk_steps_record": (i, [vp, vp, d, d, i, i, ctypes.POINTER(ctypes.c_longlong)]),
+            "dg_lserk_steps_vjp_recorded": (i, [vp, ctypes.c_longlong, vp]),
             "dg_use_tma": (i, [vp, i]),
         }
         for name, (res, args) in sig.items():
@@ -265,6 +267,20 @@ class DG:
     def adjoint_memory_limit(self, nbytes: float = 0.0):
         """Budget for the checkpointed adjoint's state buffers (0: default)."""
         self._check(lib().dg_adjoint_memory_limit(self._ctx, float(nbytes)), "dg_adjoint_memory_limit")
+
+    def lserk_steps_record(self, U, dt, n_steps, interval=10, t=0.0) -> int:
+        """Advance U in place by n_steps and record the run for lserk_steps_vjp_recorded; returns
+        the tape id."""
+        tape = ctypes.c_longlong(0)
+        self._check(lib().dg_lserk_steps_record(self._ctx, self._state(U), float(dt), float(t), int(n_steps),
+                                                int(interval), ctypes.byref(tape)), "dg_lserk_steps_record")
+        return tape.value
+
+    def lserk_steps_vjp_recorded(self, tape: int, Ubar):
+        """In place: Ubar (cotangent of the recorded run's final state) -> cotangent of its initial state."""
+        self._check(lib().dg_lserk_steps_vjp_recorded(self._ctx, int(tape), self._state(Ubar, "Ubar")),
+                    "dg_lserk_steps_vjp_recorded")
+        return Ubar
 
     def kinetic_energy_grad(self, U, grad=None):
         if grad is None:

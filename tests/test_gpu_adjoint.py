@@ -199,6 +199,38 @@ def test_checkpoint_schedules_agree(env):
     gpu.check()
 
 
+def test_recorded_run_reverses_to_the_same_bits(env):
+    """dg_lserk_steps_record + dg_lserk_steps_vjp_recorded (every stage state kept, or checkpoints
+    under a small memory budget) give the same final state as dg_lserk_steps and the same cotangent
+    as dg_lserk_steps_vjp; a new recording invalidates the old tape."""
+    dg, orc, torch = env
+    w = W.WORKLOADS["tgv_ns_n5_24x24x24_adjoint"].with_(nel=(3, 3, 3))
+    xyz, faces = w.mesh()
+    gpu = _gpu(env, w.N, xyz, faces, **w.physics())
+    U0 = torch.from_numpy(w.initial_state(xyz)).cuda()
+    dt = gpu.max_dt(U0, w.cfl)
+    K = 7
+    UK = gpu.lserk_steps(U0.clone(), dt, K)
+    seed = gpu.kinetic_energy_grad(UK)
+    want = seed.clone()
+    gpu.lserk_steps_vjp(U0, want, dt, K, 3)
+    for limit in (0.0, 1.0):  # default budget: all stage states; 1 byte: checkpoints every 3 steps
+        gpu.adjoint_memory_limit(limit)
+        V = U0.clone()
+        tape = gpu.lserk_steps_record(V, dt, K, 3)
+        assert torch.equal(V, UK)
+        Ub = seed.clone()
+        gpu.lserk_steps_vjp_recorded(tape, Ub)
+        assert torch.equal(Ub, want)
+    gpu.adjoint_memory_limit(0.0)
+    t1 = gpu.lserk_steps_record(U0.clone(), dt, 2, 2)
+    gpu.lserk_steps_record(U0.clone(), dt, 2, 2)
+    with pytest.raises(dg.DGError) as ei:
+        gpu.lserk_steps_vjp_recorded(t1, seed.clone())
+    assert ei.value.status == -1
+    gpu.check()
+
+
 def _ke_complex(U, J, w):
     """Kinetic-energy integral of a complex state (analytic continuation, no conjugation)."""
     wq = np.einsum("k,j,i->kji", w, w, w)[None] * J
