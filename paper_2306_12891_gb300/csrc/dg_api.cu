@@ -567,7 +567,11 @@ dg_status steps_impl(dg_ctx *c, double *U, double dt, int n_steps) {
   if (!(c->step_graph && c->graph_U == U && c->graph_dt == dt)) {
     DG_TRY(plain_steps(c, U, dt, 1));  // first step directly (also sets kernel attributes outside capture)
     --n_steps;
-    DG_TRY(capture_step(c, U, dt));
+    if (capture_step(c, U, dt) != DG_OK) {  // no graph on this stream: launch the kernels directly
+      c->use_graphs = 0;
+      c->err.clear();
+      return plain_steps(c, U, dt, n_steps);
+    }
   }
   e = cudaEventRecord(c->gev_in, c->stream);
   if (!e) e = cudaStreamWaitEvent(c->gstream, c->gev_in, 0);
