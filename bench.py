@@ -96,12 +96,18 @@ def volume_kernel_bytes_per_element(N: int, navier_stokes: bool, real_bytes: int
     """Algorithmic DRAM bytes of one volume-kernel launch per element in an LSERK stage after the
     first: U and the LSERK register g read and written (FP64), the metric terms Ja (real type),
     1/J (FP64), the element's six face slots of outward flux (real type) and, for Navier-Stokes,
-    the contravariant viscous flux (12 per node) plus the neighbours' face traces (4 per face point)."""
+    the contravariant viscous flux (12 per node). The FP64 kernel also reads the neighbours' face
+    traces (4 per face point, Navier-Stokes); the FP32-bulk kernel instead reads and writes the FP32
+    shadow of U (5 floats per node each way)."""
     n = N + 1
     nodes, fpts = n ** 3, 6 * n * n
     b = nodes * (4 * 5 * 8 + 8) + nodes * 9 * real_bytes + fpts * 5 * real_bytes
     if navier_stokes:
-        b += nodes * 12 * real_bytes + fpts * 4 * real_bytes
+        b += nodes * 12 * real_bytes
+    if real_bytes == 4:
+        b += nodes * 5 * 4 * 2
+    elif navier_stokes:
+        b += fpts * 4 * real_bytes
     return float(b)
 
 
@@ -530,6 +536,13 @@ def run_gpu(args):
                 "linf_err_rel_to_change": (d / change).tolist(),
                 "p_ref": p_ref,
                 "kernels": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in kt32.items() if v[1]}}
+        v32_ms, v32_n = kt32.get("volume", (0.0, 0))
+        if v32_n:  # the FP32 volume kernel against the copy bandwidth (algorithmic bytes per launch)
+            b32 = volume_kernel_bytes_per_element(w.N, True, 4) * w.n_elems
+            gbs = b32 / (v32_ms / v32_n * 1e-3) / 1e9
+            fp32["roofline"] = {"bound": "hbm", "kernel": "volume (FP32-bulk)", "achieved": gbs, "peak": HBM_GBS,
+                                "unit": "GB/s", "frac": gbs / HBM_GBS, "bytes_per_launch": b32,
+                                "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
         del s32
 
     dofs = w.dofs

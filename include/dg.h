@@ -212,10 +212,12 @@ dg_status dg_check(dg_ctx *ctx);
 /* Copy the device metrics to caller device arrays Ja [n_elems][3 d][3 c][n]^3 and J [n_elems][n]^3. */
 dg_status dg_get_metrics(dg_ctx *ctx, double *Ja, double *J);
 
-/* 1 (default): the FP32-bulk volume operator without the blend runs as a persistent kernel whose
- * per-element inputs arrive by TMA bulk copies one element ahead (N = 3, 5, 7, and 16-byte aligned
- * U, Ut and g); 0: the plain node-per-thread kernel. Both give identical bits. */
-dg_status dg_use_tma(dg_ctx *ctx, int enable);
+/* The FP32-bulk volume operator without the blend (N = 3, 5, 7 and 16-byte aligned U, Ut, g):
+ * 2 (default): a persistent kernel whose per-element inputs arrive by TMA bulk copies one element
+ * ahead, with separate warps for the FP32 sums and for the FP64 epilogue of the previous element;
+ * 1: the same without warp specialisation; 0: the plain node-per-thread kernel. All give identical
+ * bits. */
+dg_status dg_use_tma(dg_ctx *ctx, int mode);
 
 /* 1 (default): multi-step calls replay a CUDA graph of one step; 0: every kernel is launched. Both
  * run the same kernels and give identical bits. */

@@ -1155,25 +1155,27 @@ __device__ __forceinline__ void f32_node_terms(const DgDevice &d, const float *_
 // -1/J and the output / LSERK(5,4) stage in FP64 for one node; Ue, ge point at this element's state
 // and register slices [5][nnn] to read (shared or global memory), out and g are global
 __device__ __forceinline__ void f32_finish(const DgDevice &d, const double *Ue, const double *ge,
-                                           double *out, double *__restrict__ g, int e, int node,
-                                           const float s[5], int mode, int first, double dt, double A,
-                                           double B) {
-  const double miJ = -d.invJ[(size_t)e * nnn + node];
+                                           const double *iJe, double *out, double *__restrict__ g, int e,
+                                           int node, const float s[5], int mode, int first, double dt,
+                                           double A, double B) {
+  // explicit roundings (no compiler contraction), so every kernel variant gives the same bits;
+  // Ue, ge, iJe: this element's U, g and 1/J (global memory or a shared-memory copy)
+  const double miJ = -iJe[node];
   const size_t gi = (size_t)e * 5 * nnn + node;
   if (mode == 0) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) out[gi + v * nnn] = miJ * f2d_int(s[v]);
+    for (int v = 0; v < 5; ++v) out[gi + v * nnn] = __dmul_rn(miJ, f2d_int(s[v]));
     return;
   }
-  const double dtJ = dt * miJ, eref = d.eref;
+  const double dtJ = __dmul_rn(dt, miJ), eref = d.eref;
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    const double du = dtJ * f2d_int(s[v]);
-    const double gv = first ? du : A * ge[node + v * nnn] + du;
+    const double du = __dmul_rn(dtJ, f2d_int(s[v]));
+    const double gv = first ? du : __fma_rn(A, ge[node + v * nnn], du);
     g[gi + v * nnn] = gv;
-    const double un = Ue[node + v * nnn] + B * gv;
+    const double un = __fma_rn(B, gv, Ue[node + v * nnn]);
     out[gi + v * nnn] = un;
-    d.Uf[gi + v * nnn] = d2f_int(v == 4 ? un - eref : un);
+    d.Uf[gi + v * nnn] = d2f_int(v == 4 ? __dsub_rn(un, eref) : un);
   }
 }
 
@@ -1211,7 +1213,7 @@ __global__ void __launch_bounds__(NODE_THREADS, 2) k_volume_f32(const DgDevice d
     f32_node_terms<VF>(d, P + le * 7 * nnn, JS + le * 9 * nnn, FS + le * 12 * nnn,
                        d.Fsurf_f + (size_t)e * 6 * 5 * nn, e, node, s);
     const size_t ge0 = (size_t)e * 5 * nnn;
-    f32_finish(d, U + ge0, g + ge0, out, g, e, node, s, mode, first, dt, A, B);
+    f32_finish(d, U + ge0, g + ge0, d.invJ + (size_t)e * nnn, out, g, e, node, s, mode, first, dt, A, B);
   }
 }
 
@@ -1226,12 +1228,12 @@ __global__ void __launch_bounds__(NODE_THREADS, 2) k_volume_f32(const DgDevice d
 constexpr bool TMA_OK = (N == 3 || N == 5 || N == 7);
 constexpr int TMA_THREADS = round32(nnn);
 constexpr unsigned TB_UF = 5u * nnn * 4u, TB_JA = 9u * nnn * 4u, TB_FV = 12u * nnn * 4u, TB_FS = 30u * nn * 4u;
-constexpr unsigned TB_U = 5u * nnn * 8u, TB_G = 5u * nnn * 8u;
-constexpr unsigned TB_BUF = TB_UF + TB_JA + TB_FV + TB_FS + TB_U + TB_G;
+constexpr unsigned TB_U = 5u * nnn * 8u, TB_G = 5u * nnn * 8u, TB_IJ = nnn * 8u;
+constexpr unsigned TB_BUF = TB_UF + TB_JA + TB_FV + TB_FS + TB_U + TB_G + TB_IJ;
 constexpr unsigned TB_P = 7u * nnn * 4u;
 constexpr unsigned TB_SMEM = 2u * TB_BUF + TB_P + 16u;
 static_assert(!TMA_OK || (TB_UF % 16 == 0 && TB_JA % 16 == 0 && TB_FV % 16 == 0 && TB_FS % 16 == 0 &&
-                          TB_U % 16 == 0 && TB_P % 16 == 0), "TMA slices must be multiples of 16 bytes");
+                          TB_U % 16 == 0 && TB_IJ % 16 == 0 && TB_P % 16 == 0), "TMA slices must be multiples of 16 bytes");
 static_assert(!TMA_OK || TB_SMEM <= 232448, "TMA kernel exceeds the shared memory of one CTA");
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -1266,13 +1268,14 @@ template <int VF>
 __global__ void __launch_bounds__(TMA_THREADS, 1) k_volume_f32_tma(const DgDevice d, const double *U, double *out,
                                                                     double *g, int mode, int first, double dt,
                                                                     double A, double B) {
-  extern __shared__ __align__(128) unsigned char sm_raw[];
-  float *P = reinterpret_cast<float *>(sm_raw + 2 * TB_BUF);
-  unsigned long long *bar = reinterpret_cast<unsigned long long *>(sm_raw + 2 * TB_BUF + TB_P);
+  extern __shared__ __align__(128) unsigned char sm_tma[];
+  float *P = reinterpret_cast<float *>(sm_tma + 2 * TB_BUF);
+  unsigned long long *bar = reinterpret_cast<unsigned long long *>(sm_tma + 2 * TB_BUF + TB_P);
   __shared__ int s_ok;
   const bool ns = d.equations == 1;
   const bool needU = mode == 1, needG = mode == 1 && !first;
-  const unsigned bytes = TB_UF + TB_JA + TB_FS + (ns ? TB_FV : 0u) + (needU ? TB_U : 0u) + (needG ? TB_G : 0u);
+  const unsigned bytes =
+      TB_UF + TB_JA + TB_FS + TB_IJ + (ns ? TB_FV : 0u) + (needU ? TB_U : 0u) + (needG ? TB_G : 0u);
   const int tid = threadIdx.x;
   if (tid == 0) {
     mbar_init(smem_addr(&bar[0]));
@@ -1284,7 +1287,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) k_volume_f32_tma(const DgDevic
   auto issue = [&](int k) {
     const long long e = (long long)blockIdx.x + (long long)k * gridDim.x;
     if (e >= d.nE) return;
-    unsigned char *b = sm_raw + (k & 1) * TB_BUF;
+    unsigned char *b = sm_tma + (k & 1) * TB_BUF;
     const unsigned mb = smem_addr(&bar[k & 1]);
     mbar_expect_tx(mb, bytes);
     bulk_g2s(smem_addr(b), d.Uf + e * 5 * nnn, TB_UF, mb);
@@ -1293,6 +1296,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) k_volume_f32_tma(const DgDevic
     bulk_g2s(smem_addr(b + TB_UF + TB_JA + TB_FV), d.Fsurf_f + e * 30 * nn, TB_FS, mb);
     if (needU) bulk_g2s(smem_addr(b + TB_UF + TB_JA + TB_FV + TB_FS), U + e * 5 * nnn, TB_U, mb);
     if (needG) bulk_g2s(smem_addr(b + TB_UF + TB_JA + TB_FV + TB_FS + TB_U), g + e * 5 * nnn, TB_G, mb);
+    bulk_g2s(smem_addr(b + TB_UF + TB_JA + TB_FV + TB_FS + TB_U + TB_G), d.invJ + e * nnn, TB_IJ, mb);
   };
   if (tid == 0) {
     issue(0);
@@ -1312,13 +1316,14 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) k_volume_f32_tma(const DgDevic
       return;
     }
     mbar_wait(mb, parity);  // completed: returns at once and orders this thread's reads after the copy
-    const unsigned char *b = sm_raw + (k & 1) * TB_BUF;
+    const unsigned char *b = sm_tma + (k & 1) * TB_BUF;
     const float *Uf = reinterpret_cast<const float *>(b);
     const float *Jb = reinterpret_cast<const float *>(b + TB_UF);
     const float *Fb = reinterpret_cast<const float *>(b + TB_UF + TB_JA);
     const float *Sb = reinterpret_cast<const float *>(b + TB_UF + TB_JA + TB_FV);
     const double *Ub = reinterpret_cast<const double *>(b + TB_UF + TB_JA + TB_FV + TB_FS);
     const double *Gb = reinterpret_cast<const double *>(b + TB_UF + TB_JA + TB_FV + TB_FS + TB_U);
+    const double *Ib = reinterpret_cast<const double *>(b + TB_UF + TB_JA + TB_FV + TB_FS + TB_U + TB_G);
     if (tid < nnn) {
       const float Uv[5] = {Uf[tid], Uf[nnn + tid], Uf[2 * nnn + tid], Uf[3 * nnn + tid], Uf[4 * nnn + tid]};
       f32_stage<VF>(d, Uv, P + tid);
@@ -1327,10 +1332,166 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) k_volume_f32_tma(const DgDevic
     if (tid < nnn) {
       float s[5];
       f32_node_terms<VF>(d, P, Jb, Fb, Sb, (int)e, tid, s);
-      f32_finish(d, Ub, Gb, out, g, (int)e, tid, s, mode, first, dt, A, B);
+      f32_finish(d, Ub, Gb, Ib, out, g, (int)e, tid, s, mode, first, dt, A, B);
     }
     __syncthreads();  // buffer k & 1 and P are free again
     if (tid == 0) issue(k + 2);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Warp-specialised form of the TMA kernel: 16 compute warps stage the primitives and form the
+// per-node sums of element k while 4 epilogue warps apply -1/J and the FP64 LSERK update to element
+// k-1, so the FP64 epilogue overlaps the FP32 flux arithmetic instead of following it. The sums
+// pass through shared memory (two buffers); hand-offs use mbarriers: full[b] (the compute threads
+// arrive when sums are written) and empty[b] (the epilogue threads arrive when they are consumed).
+// Every wait is bounded; the compute warps leave their loop together after a block-level barrier
+// among themselves.
+// ---------------------------------------------------------------------------------------------
+constexpr int WS_COMPUTE = TMA_THREADS;
+constexpr int WS_EPI = 128;
+constexpr int WS_THREADS = WS_COMPUTE + WS_EPI;
+constexpr unsigned WS_CBUF = TB_UF + TB_JA + TB_FV + TB_FS;  // per-element TMA slices (no U, g)
+constexpr unsigned WS_S = 5u * nnn * 4u;                      // per-node sums of one element
+constexpr unsigned WS_UG = TB_U + TB_G + TB_IJ;              // FP64 state, register and 1/J of one element
+constexpr unsigned WS_SMEM = 2u * WS_CBUF + TB_P + 2u * WS_S + WS_UG + 64u;
+static_assert(!TMA_OK || WS_SMEM <= 232448, "warp-specialised kernel exceeds the shared memory of one CTA");
+
+__device__ __forceinline__ void mbar_init_n(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+template <int VF>
+__global__ void __launch_bounds__(WS_THREADS, 1) k_volume_f32_ws(const DgDevice d, const double *U, double *out,
+                                                                  double *g, int mode, int first, double dt,
+                                                                  double A, double B) {
+  extern __shared__ __align__(128) unsigned char sm_tma[];
+  float *P = reinterpret_cast<float *>(sm_tma + 2 * WS_CBUF);
+  float *S = reinterpret_cast<float *>(sm_tma + 2 * WS_CBUF + TB_P);  // [2][5][nnn]
+  unsigned char *UG = sm_tma + 2 * WS_CBUF + TB_P + 2 * WS_S;  // U [5][nnn], g [5][nnn], 1/J [nnn] (FP64)
+  unsigned long long *bar = reinterpret_cast<unsigned long long *>(UG + WS_UG);
+  // bar[0..1]: TMA arrival per buffer; bar[2..3]: sums full; bar[4..5]: sums empty; bar[6]: U, g arrival
+  __shared__ int s_abort, s_abort_e;
+  const bool ns = d.equations == 1;
+  const unsigned bytes = TB_UF + TB_JA + TB_FS + (ns ? TB_FV : 0u);
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(smem_addr(&bar[0]));
+    mbar_init(smem_addr(&bar[1]));
+    mbar_init_n(smem_addr(&bar[2]), WS_COMPUTE);
+    mbar_init_n(smem_addr(&bar[3]), WS_COMPUTE);
+    mbar_init_n(smem_addr(&bar[4]), WS_EPI);
+    mbar_init_n(smem_addr(&bar[5]), WS_EPI);
+    mbar_init(smem_addr(&bar[6]));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+    s_abort_e = 0;
+  }
+  __syncthreads();
+  auto issue = [&](int k) {
+    const long long e = (long long)blockIdx.x + (long long)k * gridDim.x;
+    if (e >= d.nE) return;
+    unsigned char *b = sm_tma + (k & 1) * WS_CBUF;
+    const unsigned mb = smem_addr(&bar[k & 1]);
+    mbar_expect_tx(mb, bytes);
+    bulk_g2s(smem_addr(b), d.Uf + e * 5 * nnn, TB_UF, mb);
+    bulk_g2s(smem_addr(b + TB_UF), d.Jaf + e * 9 * nnn, TB_JA, mb);
+    if (ns) bulk_g2s(smem_addr(b + TB_UF + TB_JA), d.Fv_f + e * 12 * nnn, TB_FV, mb);
+    bulk_g2s(smem_addr(b + TB_UF + TB_JA + TB_FV), d.Fsurf_f + e * 30 * nn, TB_FS, mb);
+  };
+  if (tid < WS_COMPUTE) {
+    if (tid == 0) {
+      issue(0);
+      issue(1);
+    }
+    int k = 0;
+    for (;; ++k) {
+      const long long e = (long long)blockIdx.x + (long long)k * gridDim.x;
+      if (e >= d.nE) break;
+      const int b = k & 1;
+      const unsigned parity = (unsigned)((k >> 1) & 1);
+      if (!mbar_wait(smem_addr(&bar[b]), parity)) s_abort = 1;
+      const unsigned char *buf = sm_tma + b * WS_CBUF;
+      const float *Uf = reinterpret_cast<const float *>(buf);
+      if (tid < nnn && !s_abort) {
+        const float Uv[5] = {Uf[tid], Uf[nnn + tid], Uf[2 * nnn + tid], Uf[3 * nnn + tid], Uf[4 * nnn + tid]};
+        f32_stage<VF>(d, Uv, P + tid);
+      }
+      named_sync(1, WS_COMPUTE);
+      if (s_abort) break;
+      float sv[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      if (tid < nnn)
+        f32_node_terms<VF>(d, P, reinterpret_cast<const float *>(buf + TB_UF),
+                           reinterpret_cast<const float *>(buf + TB_UF + TB_JA),
+                           reinterpret_cast<const float *>(buf + TB_UF + TB_JA + TB_FV), (int)e, tid, sv);
+      // the sums buffer b is free once the epilogue has consumed element k - 2
+      if (k >= 2 && !mbar_wait(smem_addr(&bar[4 + b]), (unsigned)(((k >> 1) - 1) & 1))) s_abort = 1;
+      if (tid < nnn) {
+        float *Sb = S + b * 5 * nnn + tid;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Sb[v * nnn] = sv[v];
+      }
+      mbar_arrive(smem_addr(&bar[2 + b]));
+      named_sync(1, WS_COMPUTE);  // buffer b and P are free again
+      if (s_abort) break;
+      if (tid == 0) issue(k + 2);
+    }
+    if (s_abort && tid == 0) {  // report; wait (bounded) for the next element's copy still in flight
+      flag_set(d.flag, 4);
+      if ((long long)blockIdx.x + (long long)(k + 1) * gridDim.x < d.nE)
+        mbar_wait(smem_addr(&bar[(k + 1) & 1]), (unsigned)(((k + 1) >> 1) & 1));
+    }
+  } else {
+    // epilogue warps: the FP64 state, register and 1/J of each element arrive by TMA one element
+    // ahead (issued by the group's first thread once the whole group has finished with the buffer)
+    const int et = tid - WS_COMPUTE;
+    const bool needU = mode == 1, needG = mode == 1 && !first;
+    const unsigned ug_bytes = TB_IJ + (needU ? TB_U : 0u) + (needG ? TB_G : 0u);
+    auto issue_ug = [&](int k) {
+      const long long e = (long long)blockIdx.x + (long long)k * gridDim.x;
+      if (e >= d.nE) return;
+      const unsigned mb = smem_addr(&bar[6]);
+      mbar_expect_tx(mb, ug_bytes);
+      if (needU) bulk_g2s(smem_addr(UG), U + e * 5 * nnn, TB_U, mb);
+      if (needG) bulk_g2s(smem_addr(UG + TB_U), g + e * 5 * nnn, TB_G, mb);
+      bulk_g2s(smem_addr(UG + TB_U + TB_G), d.invJ + e * nnn, TB_IJ, mb);
+    };
+    if (et == 0) issue_ug(0);
+    int k = 0;
+    for (;; ++k) {
+      const long long e = (long long)blockIdx.x + (long long)k * gridDim.x;
+      if (e >= d.nE) break;
+      const int b = k & 1;
+      if (!mbar_wait(smem_addr(&bar[2 + b]), (unsigned)((k >> 1) & 1))) s_abort_e = 1;
+      if (!mbar_wait(smem_addr(&bar[6]), (unsigned)(k & 1))) s_abort_e = 1;
+      if (!s_abort_e) {
+        const float *Sb = S + b * 5 * nnn;
+        const double *Ue = reinterpret_cast<const double *>(UG), *ge = reinterpret_cast<const double *>(UG + TB_U),
+                     *iJe = reinterpret_cast<const double *>(UG + TB_U + TB_G);
+        for (int node = et; node < nnn; node += WS_EPI) {
+          const float sv[5] = {Sb[node], Sb[nnn + node], Sb[2 * nnn + node], Sb[3 * nnn + node],
+                               Sb[4 * nnn + node]};
+          f32_finish(d, Ue, ge, iJe, out, g, (int)e, node, sv, mode, first, dt, A, B);
+        }
+      }
+      mbar_arrive(smem_addr(&bar[4 + b]));
+      named_sync(2, WS_EPI);  // the group is done with the U, g buffer
+      if (s_abort_e) break;
+      if (et == 0) issue_ug(k + 1);
+    }
+    if (s_abort_e && et == 0) {  // report; wait (bounded) for this element's copy, the one in flight
+      flag_set(d.flag, 4);
+      mbar_wait(smem_addr(&bar[6]), (unsigned)(k & 1));
+    }
   }
 }
 
@@ -1592,6 +1753,20 @@ template <int VF>
 void launch_volume_f32(const DgDevice &d, const double *U, double *out, double *g, int mode, int first, double dt,
                        double A, double B, cudaStream_t s) {
   const bool aligned = !(((uintptr_t)U | (uintptr_t)out | (uintptr_t)g) & 15u);
+  if (TMA_OK && d.use_tma == 2 && aligned) {  // warp-specialised persistent kernel
+    static int grid_ws = 0;
+    if (!grid_ws) {
+      cudaFuncSetAttribute(k_volume_f32_ws<VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WS_SMEM);
+      int dev = 0, sms = 0, per_sm = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_volume_f32_ws<VF>, WS_THREADS, WS_SMEM);
+      grid_ws = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const int blocks = d.nE < grid_ws ? d.nE : grid_ws;
+    k_volume_f32_ws<VF><<<blocks, WS_THREADS, WS_SMEM, s>>>(d, U, out, g, mode, first, dt, A, B);
+    return;
+  }
   if (TMA_OK && d.use_tma && aligned) {
     static int grid = 0;  // persistent: CTAs resident on all SMs at once
     if (!grid) {

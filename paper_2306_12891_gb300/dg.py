@@ -320,8 +320,9 @@ class DG:
                     "dg_get_metrics")
         return Ja, J
 
-    def use_tma(self, on=True):
-        self._check(lib().dg_use_tma(self._ctx, int(bool(on))), "dg_use_tma")
+    def use_tma(self, mode=2):
+        """FP32-bulk volume kernel: 2 warp-specialised TMA (default), 1 TMA, 0 plain."""
+        self._check(lib().dg_use_tma(self._ctx, int(mode)), "dg_use_tma")
 
     def use_graphs(self, on=True):
         self._check(lib().dg_use_graphs(self._ctx, int(bool(on))), "dg_use_graphs")

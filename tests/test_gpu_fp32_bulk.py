@@ -168,15 +168,16 @@ def test_tma_kernel_matches_plain_kernel(env, N, phys):
     xyz, faces = W.box_mesh(N, (3, 2, 3), mapping=_generic_map)
     U0 = torch.from_numpy(W.random_smooth_state(xyz, seed=N, amp=0.1)).cuda()
     res = []
-    for tma in (False, True):
+    for mode in (0, 1, 2):
         s = dg.DG(N, xyz, faces, precision="fp32_bulk", p_ref=1.0 / 1.4, **phys)
-        s.use_tma(tma)
+        s.use_tma(mode)
         Ut = s.rhs(U0)
         U = U0.clone()
         s.lserk_steps(U, 1e-3, 3)
         s.check()
         res.append((Ut, U))
-    assert torch.equal(res[0][0], res[1][0]) and torch.equal(res[0][1], res[1][1])
+    for r in res[1:]:
+        assert torch.equal(res[0][0], r[0]) and torch.equal(res[0][1], r[1])
 
 
 def test_tma_kernel_with_walls(env):
@@ -184,13 +185,13 @@ def test_tma_kernel_with_walls(env):
     xyz, faces = W.box_mesh(5, (3, 2, 3), lo=(0, 0, 0), hi=(2 * np.pi, np.pi, 2.0), z_walls=True)
     U0 = torch.from_numpy(W.random_smooth_state(xyz, seed=3, amp=0.1)).cuda()
     res = []
-    for tma in (False, True):
+    for mode in (0, 1, 2):
         s = dg.DG(5, xyz, faces, precision="fp32_bulk", p_ref=1.0 / 1.4, equations="ns", vflux="pirozzoli",
                   sflux="roe", mu=1e-3)
-        s.use_tma(tma)
+        s.use_tma(mode)
         res.append(s.rhs(U0))
         s.check()
-    assert torch.equal(res[0], res[1])
+    assert torch.equal(res[0], res[1]) and torch.equal(res[0], res[2])
 
 
 def test_full_size_fp32_rhs_sampled(env):
