@@ -96,18 +96,16 @@ def volume_kernel_bytes_per_element(N: int, navier_stokes: bool, real_bytes: int
     """Algorithmic DRAM bytes of one volume-kernel launch per element in an LSERK stage after the
     first: U and the LSERK register g read and written (FP64), the metric terms Ja (real type),
     1/J (FP64), the element's six face slots of outward flux (real type) and, for Navier-Stokes,
-    the contravariant viscous flux (12 per node). The FP64 kernel also reads the neighbours' face
-    traces (4 per face point, Navier-Stokes); the FP32-bulk kernel instead reads and writes the FP32
-    shadow of U (5 floats per node each way)."""
+    the contravariant viscous flux (12 per node) and the neighbours' normal viscous flux at the faces
+    (4 per face point). The FP32-bulk kernel also reads and writes the FP32 shadow of U (5 floats per
+    node each way)."""
     n = N + 1
     nodes, fpts = n ** 3, 6 * n * n
     b = nodes * (4 * 5 * 8 + 8) + nodes * 9 * real_bytes + fpts * 5 * real_bytes
     if navier_stokes:
-        b += nodes * 12 * real_bytes
+        b += nodes * 12 * real_bytes + fpts * 4 * real_bytes
     if real_bytes == 4:
         b += nodes * 5 * 4 * 2
-    elif navier_stokes:
-        b += fpts * 4 * real_bytes
     return float(b)
 
 

@@ -1075,61 +1075,68 @@ __device__ __forceinline__ void f32_stage(const DgDevice &d, const float Uv[5], 
   else Pn[5 * nnn] = Et + p;
 }
 
+// D_im with a zero diagonal, rows padded to n + 1 floats, in shared memory: the node-per-thread
+// kernels index it by the thread's own node, which would serialise a constant-memory load
+constexpr int DZ_STRIDE = n + 1;
+__device__ __forceinline__ void fill_dz(float *Dz, int tid, int nthreads) {
+  for (int t = tid; t < nn; t += nthreads) Dz[(t / n) * DZ_STRIDE + t % n] = 0.5f * f_D2[t];  // exact
+}
+
 // the node's flux differencing, surface terms and (Navier-Stokes) viscous divergence with the
 // neighbour's or the wall's viscous trace, summed into s. P [7][nnn], J [9][nnn] (slot 3d + c),
 // F [12][nnn] (contravariant viscous flux of this element) staged; Fs = this element's face slots
-// [6][5][nn] (shared or global memory)
+// [6][5][nn] (shared or global memory); Dz from fill_dz.
+// The line sums skip the zero diagonal (partner m = mm or mm + 1) and take D itself; the split-form
+// scalings D/4 (mass), D/8 (momentum, energy) or 2D (EC, central) are powers of two, applied once at
+// the end, so the flux-differencing sums are those of the scaled tables bit for bit.
 template <int VF>
 __device__ __forceinline__ void f32_node_terms(const DgDevice &d, const float *__restrict__ P,
                                                const float *__restrict__ J, const float *__restrict__ F,
-                                               const float *__restrict__ Fs, int e, int node, float s[5]) {
+                                               const float *__restrict__ Fs, const float *__restrict__ Dz,
+                                               int e, int node, float s[5]) {
   const float gam = d.gamma_f, pref = d.p_ref_f;
   const bool ns = d.equations == 1;
   const int ijk[3] = {node % n, (node / n) % n, node / nn};
+  float a[5];  // flux differencing with D
 #pragma unroll
-  for (int v = 0; v < 5; ++v) s[v] = 0.0f;
+  for (int v = 0; v < 5; ++v) a[v] = s[v] = 0.0f;
 #pragma unroll
   for (int dd = 0; dd < 3; ++dd) {
     const int id = ijk[dd];
     const int st = dd == 0 ? 1 : dd == 1 ? n : nn;
     const int base = node - id * st;
+    const float *Dr = Dz + id * DZ_STRIDE;
+    const float *Fvd = F + (dd * 4) * nnn;
     const float jx = J[(3 * dd) * nnn + node], jy = J[(3 * dd + 1) * nnn + node], jz = J[(3 * dd + 2) * nnn + node];
+    float vq[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int m = 0; m < n; ++m) {  // m = id contributes 0 (zero diagonal of the scaled tables)
+    for (int mm = 0; mm < N; ++mm) {
+      const int m = mm + (mm >= id ? 1 : 0);
       const int am = base + m * st;
+      const float c = Dr[m];
       float Fp[5];
       pair_flux_f<VF>(P, node, am, jx + J[(3 * dd) * nnn + am], jy + J[(3 * dd + 1) * nnn + am],
                       jz + J[(3 * dd + 2) * nnn + am], gam, pref, Fp);
-      if (VF == VF_PIR || VF == VF_KG) {
-        const float cq = f_Dq[id * n + m], ce = f_De[id * n + m];
-        s[0] += cq * Fp[0];
 #pragma unroll
-        for (int v = 1; v < 5; ++v) s[v] += ce * Fp[v];
-      } else {
-        const float c2 = f_D2[id * n + m];
+      for (int v = 0; v < 5; ++v) a[v] += c * Fp[v];
+      if (ns) {  // viscous divergence along the line
 #pragma unroll
-        for (int v = 0; v < 5; ++v) s[v] += c2 * Fp[v];
+        for (int q = 0; q < 4; ++q) vq[q] += c * Fvd[q * nnn + am];
       }
     }
     const bool face = id == 0 || id == N;
     const int f = 2 * dd + (id == N ? 1 : 0);
     const int pp = dd == 0 ? ijk[1] : ijk[0], qq = dd == 2 ? ijk[1] : ijk[2];
+    const float iw = id == 0 ? f_invw[0] : f_invw[N];  // two uniform constant loads
     if (face) {  // surface term: (1/w_b) times the outward face flux
       const float *fs = Fs + f * 5 * nn + pp + n * qq;
 #pragma unroll
-      for (int v = 0; v < 5; ++v) s[v] += f_invw[id] * fs[v * nn];
+      for (int v = 0; v < 5; ++v) s[v] += iw * fs[v * nn];
     }
     if (ns) {
-      // viscous divergence along the line (zero diagonal: 2D/2 from the scaled table) and the
-      // neighbour's outward normal viscous flux -(1/(2 w_b)) phi_nb at the element faces
-      const float *Fvd = F + (dd * 4) * nnn + base;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int m = 0; m < n; ++m) acc += 0.5f * f_D2[id * n + m] * Fvd[q * nnn + m * st];
-        s[1 + q] -= acc;
-      }
+      for (int q = 0; q < 4; ++q) s[1 + q] -= vq[q];
+      // the neighbour's outward normal viscous flux -(1/(2 w_b)) phi_nb at the element faces
       if (face) {
         const int *ef = d.ef + ((size_t)e * 6 + f) * 4;
         const int nb = ef[0], fnb = ef[1], o = ef[2];
@@ -1137,7 +1144,7 @@ __device__ __forceinline__ void f32_node_terms(const DgDevice &d, const float *_
           const float *fw = d.Fwall_f + (size_t)ef[3] * 4 * nn + pp + n * qq;
           const float hs = (id == N) ? 0.5f : -0.5f;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) s[1 + q] -= f_invw[id] * (fw[q * nn] - hs * F[(dd * 4 + q) * nnn + node]);
+          for (int q = 0; q < 4; ++q) s[1 + q] -= iw * (fw[q * nn] - hs * F[(dd * 4 + q) * nnn + node]);
         } else {
           int p2, q2;
           orient_map(o, pp, qq, p2, q2);
@@ -1145,10 +1152,18 @@ __device__ __forceinline__ void f32_node_terms(const DgDevice &d, const float *_
           const float sg = (fnb & 1) ? 0.5f : -0.5f;
           const float *Fvn = d.Fv_f + ((size_t)nb * 12 + (fnb >> 1) * 4) * nnn + nbnode;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) s[1 + q] += f_invw[id] * sg * Fvn[q * nnn];
+          for (int q = 0; q < 4; ++q) s[1 + q] += iw * sg * Fvn[q * nnn];
         }
       }
     }
+  }
+  if (VF == VF_PIR || VF == VF_KG) {
+    s[0] += 0.25f * a[0];
+#pragma unroll
+    for (int v = 1; v < 5; ++v) s[v] += 0.125f * a[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) s[v] += 2.0f * a[v];
   }
 }
 
@@ -1187,6 +1202,8 @@ __global__ void __launch_bounds__(NODE_THREADS, 2) k_volume_f32(const DgDevice d
   float *P = reinterpret_cast<float *>(sm_raw);  // [EPB][7][nnn] staged primitives
   float *JS = P + NODE_EPB * 7 * nnn;            // [EPB][9][nnn] metric terms Ja^d_c, slot 3d + c
   float *FS = JS + NODE_EPB * 9 * nnn;           // [EPB][12][nnn] contravariant viscous flux (NS)
+  __shared__ float s_Dz[n * DZ_STRIDE];
+  fill_dz(s_Dz, threadIdx.x, blockDim.x);
   const int e0 = blockIdx.x * NODE_EPB;
   for (int t = threadIdx.x; t < NODE_EPB * nnn; t += blockDim.x) {
     const int le = t / nnn, node = t % nnn, e = e0 + le;
@@ -1211,7 +1228,7 @@ __global__ void __launch_bounds__(NODE_THREADS, 2) k_volume_f32(const DgDevice d
     if (e >= d.nE) continue;
     float s[5];
     f32_node_terms<VF>(d, P + le * 7 * nnn, JS + le * 9 * nnn, FS + le * 12 * nnn,
-                       d.Fsurf_f + (size_t)e * 6 * 5 * nn, e, node, s);
+                       d.Fsurf_f + (size_t)e * 6 * 5 * nn, s_Dz, e, node, s);
     const size_t ge0 = (size_t)e * 5 * nnn;
     f32_finish(d, U + ge0, g + ge0, d.invJ + (size_t)e * nnn, out, g, e, node, s, mode, first, dt, A, B);
   }
@@ -1272,6 +1289,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) k_volume_f32_tma(const DgDevic
   float *P = reinterpret_cast<float *>(sm_tma + 2 * TB_BUF);
   unsigned long long *bar = reinterpret_cast<unsigned long long *>(sm_tma + 2 * TB_BUF + TB_P);
   __shared__ int s_ok;
+  __shared__ float s_Dz[n * DZ_STRIDE];
   const bool ns = d.equations == 1;
   const bool needU = mode == 1, needG = mode == 1 && !first;
   const unsigned bytes =
@@ -1282,6 +1300,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) k_volume_f32_tma(const DgDevic
     mbar_init(smem_addr(&bar[1]));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  fill_dz(s_Dz, tid, blockDim.x);
   __syncthreads();
   // copies of element group k into buffer k & 1 (thread 0)
   auto issue = [&](int k) {
@@ -1331,7 +1350,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) k_volume_f32_tma(const DgDevic
     __syncthreads();
     if (tid < nnn) {
       float s[5];
-      f32_node_terms<VF>(d, P, Jb, Fb, Sb, (int)e, tid, s);
+      f32_node_terms<VF>(d, P, Jb, Fb, Sb, s_Dz, (int)e, tid, s);
       f32_finish(d, Ub, Gb, Ib, out, g, (int)e, tid, s, mode, first, dt, A, B);
     }
     __syncthreads();  // buffer k & 1 and P are free again
@@ -1381,6 +1400,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_volume_f32_ws(const DgDevice 
   unsigned long long *bar = reinterpret_cast<unsigned long long *>(UG + WS_UG);
   // bar[0..1]: TMA arrival per buffer; bar[2..3]: sums full; bar[4..5]: sums empty; bar[6]: U, g arrival
   __shared__ int s_abort, s_abort_e;
+  __shared__ float s_Dz[n * DZ_STRIDE];
   const bool ns = d.equations == 1;
   const unsigned bytes = TB_UF + TB_JA + TB_FS + (ns ? TB_FV : 0u);
   const int tid = threadIdx.x;
@@ -1396,6 +1416,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_volume_f32_ws(const DgDevice 
     s_abort = 0;
     s_abort_e = 0;
   }
+  fill_dz(s_Dz, tid, blockDim.x);
   __syncthreads();
   auto issue = [&](int k) {
     const long long e = (long long)blockIdx.x + (long long)k * gridDim.x;
@@ -1432,7 +1453,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_volume_f32_ws(const DgDevice 
       if (tid < nnn)
         f32_node_terms<VF>(d, P, reinterpret_cast<const float *>(buf + TB_UF),
                            reinterpret_cast<const float *>(buf + TB_UF + TB_JA),
-                           reinterpret_cast<const float *>(buf + TB_UF + TB_JA + TB_FV), (int)e, tid, sv);
+                           reinterpret_cast<const float *>(buf + TB_UF + TB_JA + TB_FV), s_Dz, (int)e, tid, sv);
       // the sums buffer b is free once the epilogue has consumed element k - 2
       if (k >= 2 && !mbar_wait(smem_addr(&bar[4 + b]), (unsigned)(((k >> 1) - 1) & 1))) s_abort = 1;
       if (tid < nnn) {
