@@ -213,10 +213,12 @@ dg_status dg_check(dg_ctx *ctx);
 dg_status dg_get_metrics(dg_ctx *ctx, double *Ja, double *J);
 
 /* The FP32-bulk volume operator without the blend (N = 3, 5, 7 and 16-byte aligned U, Ut, g):
- * 2 (default): a persistent kernel whose per-element inputs arrive by TMA bulk copies one element
- * ahead, with separate warps for the FP32 sums and for the FP64 epilogue of the previous element;
- * 1: the same without warp specialisation; 0: the plain node-per-thread kernel. All give identical
- * bits. */
+ * 3 (default; N = 7, other N take mode 2): a persistent kernel whose line threads form each
+ * two-point flux once for both of its nodes (pair symmetry) while separate warps apply the FP64
+ * epilogue to the previous element; inputs arrive by TMA bulk copies one element ahead.
+ * 2: the same pipeline with one thread per node; 1: mode 2 without warp specialisation; 0: the
+ * plain node-per-thread kernel. Modes 0-2 give identical bits; mode 3 sums in another order, so it
+ * agrees with them to FP32 rounding. DG_ERR_ARG for other values. */
 dg_status dg_use_tma(dg_ctx *ctx, int mode);
 
 /* 1 (default): multi-step calls replay a CUDA graph of one step; 0: every kernel is launched. Both

@@ -417,7 +417,7 @@ dg_status dg_init(const dg_mesh *mesh, int N, int nodes, const dg_params *prm, v
   d.href_f = (float)d.href;
   d.mu_f = (float)d.mu;
   d.kappa_f = (float)d.kappa;
-  d.use_tma = 2;
+  d.use_tma = 3;  // N = 7: pair-symmetric line kernel; other N: warp-specialised node kernel
   d.n_walls = n_walls;
   d.wm_index = prm->wm_index;
   d.wm_vd = prm->wm_van_driest ? 1 : 0;
@@ -774,7 +774,7 @@ dg_status dg_get_metrics(dg_ctx *c, double *Ja, double *J) {
 
 dg_status dg_use_tma(dg_ctx *c, int enable) {
   if (!c) return DG_ERR_ARG;
-  if (enable < 0 || enable > 2) return fail(c, DG_ERR_ARG, "dg_use_tma: mode 0, 1 or 2");
+  if (enable < 0 || enable > 3) return fail(c, DG_ERR_ARG, "dg_use_tma: mode 0, 1, 2 or 3");
   c->d.use_tma = enable;
   if (c->step_graph) { cudaGraphExecDestroy(c->step_graph); c->step_graph = nullptr; }  // kernels change
   return DG_OK;

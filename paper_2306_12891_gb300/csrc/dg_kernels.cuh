@@ -1173,19 +1173,24 @@ __device__ __forceinline__ void f32_finish(const DgDevice &d, const double *Ue, 
                                            const double *iJe, double *out, double *__restrict__ g, int e,
                                            int node, const float s[5], int mode, int first, double dt,
                                            double A, double B) {
-  // explicit roundings (no compiler contraction), so every kernel variant gives the same bits;
-  // Ue, ge, iJe: this element's U, g and 1/J (global memory or a shared-memory copy)
+  // Ue, ge, iJe: this element's U, g and 1/J (global memory or a shared-memory copy).
+  // The right-hand side -s/J, or the stage increment dt (-1/J) s, is one FP32 product of the FP32 sum
+  // s with the factor -1/J or dt (-1/J), formed in FP64 and rounded once (GB300 issues FP64 at 1/64
+  // of the FP32 rate, and this epilogue bounds the kernel); the LSERK register and the state
+  // accumulate in FP64. Explicit roundings (no compiler contraction) keep every kernel variant's bits.
   const double miJ = -iJe[node];
   const size_t gi = (size_t)e * 5 * nnn + node;
   if (mode == 0) {
+    const float c = d2f_int(miJ);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) out[gi + v * nnn] = __dmul_rn(miJ, f2d_int(s[v]));
+    for (int v = 0; v < 5; ++v) out[gi + v * nnn] = f2d_int(__fmul_rn(s[v], c));
     return;
   }
-  const double dtJ = __dmul_rn(dt, miJ), eref = d.eref;
+  const float c = d2f_int(__dmul_rn(dt, miJ));
+  const double eref = d.eref;
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    const double du = __dmul_rn(dtJ, f2d_int(s[v]));
+    const double du = f2d_int(__fmul_rn(s[v], c));
     const double gv = first ? du : __fma_rn(A, ge[node + v * nnn], du);
     g[gi + v * nnn] = gv;
     const double un = __fma_rn(B, gv, Ue[node + v * nnn]);
@@ -1498,10 +1503,15 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_volume_f32_ws(const DgDevice 
         const float *Sb = S + b * 5 * nnn;
         const double *Ue = reinterpret_cast<const double *>(UG), *ge = reinterpret_cast<const double *>(UG + TB_U),
                      *iJe = reinterpret_cast<const double *>(UG + TB_U + TB_G);
-        for (int node = et; node < nnn; node += WS_EPI) {
-          const float sv[5] = {Sb[node], Sb[nnn + node], Sb[2 * nnn + node], Sb[3 * nnn + node],
-                               Sb[4 * nnn + node]};
-          f32_finish(d, Ue, ge, iJe, out, g, (int)e, node, sv, mode, first, dt, A, B);
+        // all of the thread's nodes at once (unrolled): their conversion and FP64 chains overlap
+#pragma unroll
+        for (int r = 0; r < (nnn + WS_EPI - 1) / WS_EPI; ++r) {
+          const int node = et + r * WS_EPI;
+          if (node < nnn) {
+            const float sv[5] = {Sb[node], Sb[nnn + node], Sb[2 * nnn + node], Sb[3 * nnn + node],
+                                 Sb[4 * nnn + node]};
+            f32_finish(d, Ue, ge, iJe, out, g, (int)e, node, sv, mode, first, dt, A, B);
+          }
         }
       }
       mbar_arrive(smem_addr(&bar[4 + b]));
@@ -1512,6 +1522,317 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_volume_f32_ws(const DgDevice 
     if (s_abort_e && et == 0) {  // report; wait (bounded) for this element's copy, the one in flight
       flag_set(d.flag, 4);
       mbar_wait(smem_addr(&bar[6]), (unsigned)(k & 1));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// FP32-bulk volume operator with pair symmetry (N = 7). 192 line threads (one per x, y or z line of
+// the element) form each two-point flux once, for both of its nodes, and keep the sums of their
+// line's eight nodes in registers. The per-direction sums go to shared memory, where 8 epilogue
+// warps add the three directions and apply -1/J and the FP64 LSERK update to element k-1 while the
+// line threads work on element k. The FP32 state, metric terms and viscous flux arrive by TMA bulk
+// copies one element ahead (as in k_volume_f32_ws); the face slots and the neighbours' viscous
+// traces at a line's two end nodes come from global memory at the start of its line phase. Staged
+// primitives and the sums use an XOR-swizzled node order (ln_sw), so that x, y and z lines and
+// node-consecutive warps all access them without shared-memory bank conflicts.
+// The sums are kept unscaled: the split-form factors (1/4 mass, 1/8 momentum and energy for KG and
+// Pirozzoli; 2 for EC and central) are powers of two, applied once by the epilogue, and the surface
+// and viscous terms enter divided by them (exact).
+// ---------------------------------------------------------------------------------------------
+constexpr bool LN_OK = (N == 7);
+constexpr int LN_COMPUTE = 3 * nn;  // line threads
+constexpr int LN_EPI = 256;
+constexpr int LN_THREADS = LN_COMPUTE + LN_EPI;
+constexpr unsigned LN_CBUF = TB_UF + TB_JA + TB_FV;  // per-element TMA slices of the line phase
+constexpr unsigned LN_ACC = 15u * nnn * 4u;          // [3 d][5][nnn] per-direction sums
+constexpr unsigned LN_SMEM = 2u * LN_CBUF + TB_P + 2u * LN_ACC + WS_UG + 64u;
+static_assert(!LN_OK || LN_SMEM <= 232448 - 256, "line kernel exceeds the shared memory of one CTA");
+static_assert(!LN_OK || (LN_CBUF % 16 == 0 && LN_ACC % 16 == 0), "shared-memory regions must stay 16-byte aligned");
+static_assert(!LN_OK || nnn % LN_EPI == 0, "the epilogue threads take whole nodes");
+
+// bijective swizzle of node (i, j, k) = i + 8 j + 64 k for N = 7 (identity otherwise): the five
+// low bits (the bank) are (i ^ j, (j ^ k) mod 4), which differ across the 32 lanes of an x, y or z
+// line warp and of a warp of consecutive nodes
+__device__ __forceinline__ int ln_sw(int node) {
+  if (N != 7) return node;
+  const int i = node & 7, j = (node >> 3) & 7, k = node >> 6;
+  return ((i ^ j) & 7) | (((j ^ k) & 3) << 3) | ((j >> 2) << 5) | (k << 6);
+}
+
+// two-point flux of staged values held in registers (slots as in f32_stage); Sj = Ja_i + Ja_m
+template <int VF>
+__device__ __forceinline__ void pair_flux_reg(float ri, float ui, float vi, float wi, float p4i, float xi, float yi,
+                                              float rm, float um, float vm, float wm, float p4m, float xm, float ym,
+                                              float Sjx, float Sjy, float Sjz, float gam, float pref, float F[5]) {
+  if (VF == VF_PIR || VF == VF_KG) {
+    const float Su = ui + um, Sv = vi + vm, Sw = wi + wm;
+    const float Vp = Su * Sjx + Sv * Sjy + Sw * Sjz;
+    F[0] = (ri + rm) * Vp;
+    const float Sp = p4i + p4m;
+    F[1] = F[0] * Su + Sp * Sjx;
+    F[2] = F[0] * Sv + Sp * Sjy;
+    F[3] = F[0] * Sw + Sp * Sjz;
+    if (VF == VF_PIR) F[4] = F[0] * (xi + xm);
+    else F[4] = F[0] * (xi + xm) + (yi + ym) * Vp;
+  } else {
+    const float av[3] = {0.5f * Sjx, 0.5f * Sjy, 0.5f * Sjz};
+    if (VF == VF_EC) {
+      ec_flux<float>(ri, ui, vi, wi, yi, rm, um, vm, wm, ym, av, gam, pref, F);
+    } else {
+      const float Vi = ui * av[0] + vi * av[1] + wi * av[2], Vm = um * av[0] + vm * av[1] + wm * av[2];
+      const float pm2 = 0.125f * (p4i + p4m);
+      F[0] = 0.5f * (ri * Vi + rm * Vm);
+      F[1] = 0.5f * (ri * ui * Vi + rm * um * Vm) + pm2 * av[0];
+      F[2] = 0.5f * (ri * vi * Vi + rm * vm * Vm) + pm2 * av[1];
+      F[3] = 0.5f * (ri * wi * Vi + rm * wm * Vm) + pm2 * av[2];
+      F[4] = 0.5f * (xi * Vi + xm * Vm);
+    }
+  }
+}
+
+// the line's values and sums (registers); pairs (I, M), I < M, visited by template recursion so
+// that every array index is a compile-time constant
+struct LineRegs {
+  float r[n], u[n], v[n], w[n], p4[n], x[n], y[n], jx[n], jy[n], jz[n];
+  float acc[n][5];
+};
+template <int VF, int I, int M>
+__device__ __forceinline__ void line_pairs(LineRegs &R, float gam, float pref) {
+  if constexpr (I < n - 1) {
+    float F[5];
+    pair_flux_reg<VF>(R.r[I], R.u[I], R.v[I], R.w[I], R.p4[I], R.x[I], R.y[I], R.r[M], R.u[M], R.v[M], R.w[M],
+                      R.p4[M], R.x[M], R.y[M], R.jx[I] + R.jx[M], R.jy[I] + R.jy[M], R.jz[I] + R.jz[M], gam, pref, F);
+    const float ci = f_D[I * n + M], cm = f_D[M * n + I];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      R.acc[I][v] += ci * F[v];
+      R.acc[M][v] += cm * F[v];
+    }
+    if constexpr (M + 1 < n) line_pairs<VF, I, M + 1>(R, gam, pref);
+    else line_pairs<VF, I + 1, I + 2>(R, gam, pref);
+  }
+}
+
+template <int VF>
+__global__ void __launch_bounds__(LN_THREADS, 1) k_volume_f32_line(const DgDevice d, const double *U, double *out,
+                                                                    double *g, int mode, int first, double dt,
+                                                                    double A, double B) {
+  if constexpr (LN_OK) {
+    extern __shared__ __align__(128) unsigned char sm_tma[];
+    float *P = reinterpret_cast<float *>(sm_tma + 2 * LN_CBUF);            // [7][nnn], swizzled
+    float *ACC = reinterpret_cast<float *>(sm_tma + 2 * LN_CBUF + TB_P);  // [2][3][5][nnn], swizzled
+    unsigned char *UG = sm_tma + 2 * LN_CBUF + TB_P + 2 * LN_ACC;          // U, g, 1/J (FP64)
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(UG + WS_UG);
+    // bar[0..1]: TMA arrival per buffer; bar[2..3]: sums full; bar[4..5]: sums empty; bar[6]: U, g, 1/J
+    __shared__ int s_abort, s_abort_e;
+    constexpr bool SPLIT = (VF == VF_PIR || VF == VF_KG);
+    // 1 / (split-form factor) per variable: the sums are unscaled (see above)
+    constexpr float ISC0 = SPLIT ? 4.0f : 0.5f, ISC1 = SPLIT ? 8.0f : 0.5f;
+    const bool ns = d.equations == 1;
+    const unsigned bytes = TB_UF + TB_JA + (ns ? TB_FV : 0u);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+      mbar_init(smem_addr(&bar[0]));
+      mbar_init(smem_addr(&bar[1]));
+      mbar_init_n(smem_addr(&bar[2]), LN_COMPUTE);
+      mbar_init_n(smem_addr(&bar[3]), LN_COMPUTE);
+      mbar_init_n(smem_addr(&bar[4]), LN_EPI);
+      mbar_init_n(smem_addr(&bar[5]), LN_EPI);
+      mbar_init(smem_addr(&bar[6]));
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      s_abort = 0;
+      s_abort_e = 0;
+    }
+    __syncthreads();
+    auto issue = [&](int k) {
+      const long long e = (long long)blockIdx.x + (long long)k * gridDim.x;
+      if (e >= d.nE) return;
+      unsigned char *b = sm_tma + (k & 1) * LN_CBUF;
+      const unsigned mb = smem_addr(&bar[k & 1]);
+      mbar_expect_tx(mb, bytes);
+      bulk_g2s(smem_addr(b), d.Uf + e * 5 * nnn, TB_UF, mb);
+      bulk_g2s(smem_addr(b + TB_UF), d.Jaf + e * 9 * nnn, TB_JA, mb);
+      if (ns) bulk_g2s(smem_addr(b + TB_UF + TB_JA), d.Fv_f + e * 12 * nnn, TB_FV, mb);
+    };
+    if (tid < LN_COMPUTE) {
+      if (tid == 0) {
+        issue(0);
+        issue(1);
+      }
+      // this thread's line: direction dd (warp-uniform), position (la, lb) on the faces 2dd, 2dd+1
+      const int dd = tid / nn, L = tid % nn, la = L % n, lb = L / n;
+      const int st = dd == 0 ? 1 : dd == 1 ? n : nn;
+      const int base = dd == 0 ? n * la + nn * lb : dd == 1 ? la + nn * lb : la + n * lb;
+      const float gam = d.gamma_f, pref = d.p_ref_f;
+      const float iw0 = f_invw[0], iwN = f_invw[N];
+      // face records of the line's two faces, loaded one element ahead (a warp issues in order: an
+      // address computed from a just-loaded record would stall it for a full memory latency)
+      int4 rec_next[2] = {make_int4(0, 0, 0, 0), make_int4(0, 0, 0, 0)};
+      if (ns && blockIdx.x < d.nE) {
+        rec_next[0] = *reinterpret_cast<const int4 *>(d.ef + ((size_t)blockIdx.x * 6 + 2 * dd) * 4);
+        rec_next[1] = *reinterpret_cast<const int4 *>(d.ef + ((size_t)blockIdx.x * 6 + 2 * dd + 1) * 4);
+      }
+      int k = 0;
+      for (;; ++k) {
+        const long long e = (long long)blockIdx.x + (long long)k * gridDim.x;
+        if (e >= d.nE) break;
+        const int b = k & 1;
+        const int4 rec[2] = {rec_next[0], rec_next[1]};
+        if (ns && e + gridDim.x < d.nE) {
+          rec_next[0] = *reinterpret_cast<const int4 *>(d.ef + ((size_t)(e + gridDim.x) * 6 + 2 * dd) * 4);
+          rec_next[1] = *reinterpret_cast<const int4 *>(d.ef + ((size_t)(e + gridDim.x) * 6 + 2 * dd + 1) * 4);
+        }
+        if (!mbar_wait(smem_addr(&bar[b]), (unsigned)((k >> 1) & 1))) s_abort = 1;
+        const unsigned char *buf = sm_tma + b * LN_CBUF;
+        const float *Uf = reinterpret_cast<const float *>(buf);
+        const float *Jb = reinterpret_cast<const float *>(buf + TB_UF);
+        const float *Fb = reinterpret_cast<const float *>(buf + TB_UF + TB_JA);
+        if (!s_abort)
+          for (int t = tid; t < nnn; t += LN_COMPUTE) {
+            const float Uv[5] = {Uf[t], Uf[nnn + t], Uf[2 * nnn + t], Uf[3 * nnn + t], Uf[4 * nnn + t]};
+            f32_stage<VF>(d, Uv, P + ln_sw(t));
+          }
+        named_sync(1, LN_COMPUTE);
+        if (s_abort) break;
+        // end-node data from global memory, loaded before the pair sums so that its latency overlaps them
+        float fs[2][5], fnb[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+        int wall[2] = {0, 0};
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          const int f = 2 * dd + side;
+          const float *Fs = d.Fsurf_f + ((size_t)e * 6 + f) * 5 * nn + L;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) fs[side][v] = Fs[v * nn];
+          if (ns) {
+            const int4 r4 = rec[side];
+            if (r4.x >= 0) {
+              int p2, q2;
+              orient_map(r4.z, la, lb, p2, q2);
+              const float *Fvn = d.Fv_f + ((size_t)r4.x * 12 + (r4.y >> 1) * 4) * nnn + face_node(r4.y, p2, q2);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) fnb[side][q] = Fvn[q * nnn];
+            } else {  // wall: the wall-model flux, combined with the own trace below
+              const float *fw = d.Fwall_f + (size_t)r4.w * 4 * nn + L;
+#pragma unroll
+              for (int q = 0; q < 4; ++q) fnb[side][q] = fw[q * nn];
+              wall[side] = 1;
+            }
+          }
+        }
+        // the line's staged values and metric terms Ja^dd
+        LineRegs R;
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+          const int nd = base + i * st, sw = ln_sw(nd);
+          R.r[i] = P[sw]; R.u[i] = P[nnn + sw]; R.v[i] = P[2 * nnn + sw]; R.w[i] = P[3 * nnn + sw];
+          R.p4[i] = P[4 * nnn + sw];
+          R.x[i] = (VF == VF_EC) ? 0.0f : P[5 * nnn + sw];
+          R.y[i] = (VF == VF_KG || VF == VF_EC) ? P[6 * nnn + sw] : 0.0f;
+          R.jx[i] = Jb[(3 * dd) * nnn + nd];
+          R.jy[i] = Jb[(3 * dd + 1) * nnn + nd];
+          R.jz[i] = Jb[(3 * dd + 2) * nnn + nd];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) R.acc[i][v] = 0.0f;
+        }
+        // each pair (i, m), i < m, once: node i takes D_im F, node m takes D_mi F (F is symmetric)
+        line_pairs<VF, 0, 1>(R, gam, pref);
+        float (&acc)[n][5] = R.acc;
+        // surface terms: (1/w_b) times the outward face flux at the end nodes
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          const float isc = v == 0 ? ISC0 : ISC1;
+          acc[0][v] += (isc * iw0) * fs[0][v];
+          acc[N][v] += (isc * iwN) * fs[1][v];
+        }
+        if (ns) {
+          // viscous divergence along the line, then the neighbour's normal viscous flux or the wall
+          // term at the end nodes (see k_volume)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float fv[n];
+#pragma unroll
+            for (int m = 0; m < n; ++m) fv[m] = Fb[(dd * 4 + q) * nnn + base + m * st];
+#pragma unroll
+            for (int i = 0; i < n; ++i) {
+              float t = 0.0f;
+#pragma unroll
+              for (int m = 0; m < n; ++m)
+                if (m != i) t += f_D[i * n + m] * fv[m];
+              acc[i][1 + q] -= ISC1 * t;
+            }
+            const float sg0 = (rec[0].y & 1) ? 0.5f : -0.5f, sg1 = (rec[1].y & 1) ? 0.5f : -0.5f;
+            acc[0][1 + q] += wall[0] ? -(ISC1 * iw0) * (fnb[0][q] + 0.5f * fv[0]) : (ISC1 * iw0 * sg0) * fnb[0][q];
+            acc[N][1 + q] += wall[1] ? -(ISC1 * iwN) * (fnb[1][q] - 0.5f * fv[N]) : (ISC1 * iwN * sg1) * fnb[1][q];
+          }
+        }
+        // the sums buffer b is free once the epilogue has consumed element k - 2
+        if (k >= 2 && !mbar_wait(smem_addr(&bar[4 + b]), (unsigned)(((k >> 1) - 1) & 1))) s_abort = 1;
+        float *Ab = ACC + (b * 3 + dd) * 5 * nnn;
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+          const int sw = ln_sw(base + i * st);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) Ab[v * nnn + sw] = acc[i][v];
+        }
+        mbar_arrive(smem_addr(&bar[2 + b]));
+        named_sync(1, LN_COMPUTE);  // buffer b and P are free again
+        if (s_abort) break;
+        if (tid == 0) issue(k + 2);
+      }
+      if (s_abort && tid == 0) {  // report; wait (bounded) for the next element's copy still in flight
+        flag_set(d.flag, 4);
+        if ((long long)blockIdx.x + (long long)(k + 1) * gridDim.x < d.nE)
+          mbar_wait(smem_addr(&bar[(k + 1) & 1]), (unsigned)(((k + 1) >> 1) & 1));
+      }
+    } else {
+      // epilogue warps: sum the three directions, scale, -1/J and the FP64 LSERK stage; the FP64
+      // state, register and 1/J arrive by TMA one element ahead (issued once the group is done)
+      const int et = tid - LN_COMPUTE;
+      const bool needU = mode == 1, needG = mode == 1 && !first;
+      const unsigned ug_bytes = TB_IJ + (needU ? TB_U : 0u) + (needG ? TB_G : 0u);
+      auto issue_ug = [&](int k) {
+        const long long e = (long long)blockIdx.x + (long long)k * gridDim.x;
+        if (e >= d.nE) return;
+        const unsigned mb = smem_addr(&bar[6]);
+        mbar_expect_tx(mb, ug_bytes);
+        if (needU) bulk_g2s(smem_addr(UG), U + e * 5 * nnn, TB_U, mb);
+        if (needG) bulk_g2s(smem_addr(UG + TB_U), g + e * 5 * nnn, TB_G, mb);
+        bulk_g2s(smem_addr(UG + TB_U + TB_G), d.invJ + e * nnn, TB_IJ, mb);
+      };
+      if (et == 0) issue_ug(0);
+      constexpr float SC0 = SPLIT ? 0.25f : 2.0f, SC1 = SPLIT ? 0.125f : 2.0f;
+      int k = 0;
+      for (;; ++k) {
+        const long long e = (long long)blockIdx.x + (long long)k * gridDim.x;
+        if (e >= d.nE) break;
+        const int b = k & 1;
+        if (!mbar_wait(smem_addr(&bar[2 + b]), (unsigned)((k >> 1) & 1))) s_abort_e = 1;
+        if (!mbar_wait(smem_addr(&bar[6]), (unsigned)(k & 1))) s_abort_e = 1;
+        if (!s_abort_e) {
+          const float *A0 = ACC + (b * 3) * 5 * nnn, *A1 = A0 + 5 * nnn, *A2 = A1 + 5 * nnn;
+          const double *Ue = reinterpret_cast<const double *>(UG), *ge = reinterpret_cast<const double *>(UG + TB_U),
+                       *iJe = reinterpret_cast<const double *>(UG + TB_U + TB_G);
+          // all of the thread's nodes at once (unrolled): their conversion and FP64 chains overlap
+#pragma unroll
+          for (int r = 0; r < nnn / LN_EPI; ++r) {
+            const int node = et + r * LN_EPI, sw = ln_sw(node);
+            float sv[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v)
+              sv[v] = (v == 0 ? SC0 : SC1) * ((A0[v * nnn + sw] + A1[v * nnn + sw]) + A2[v * nnn + sw]);
+            f32_finish(d, Ue, ge, iJe, out, g, (int)e, node, sv, mode, first, dt, A, B);
+          }
+        }
+        mbar_arrive(smem_addr(&bar[4 + b]));
+        named_sync(2, LN_EPI);  // the group is done with the U, g, 1/J buffer
+        if (s_abort_e) break;
+        if (et == 0) issue_ug(k + 1);
+      }
+      if (s_abort_e && et == 0) {  // report; wait (bounded) for this element's copy, the one in flight
+        flag_set(d.flag, 4);
+        mbar_wait(smem_addr(&bar[6]), (unsigned)(k & 1));
+      }
     }
   }
 }
@@ -1774,7 +2095,21 @@ template <int VF>
 void launch_volume_f32(const DgDevice &d, const double *U, double *out, double *g, int mode, int first, double dt,
                        double A, double B, cudaStream_t s) {
   const bool aligned = !(((uintptr_t)U | (uintptr_t)out | (uintptr_t)g) & 15u);
-  if (TMA_OK && d.use_tma == 2 && aligned) {  // warp-specialised persistent kernel
+  if (LN_OK && d.use_tma == 3 && aligned) {  // pair-symmetric line kernel, warp-specialised
+    static int grid_ln = 0;
+    if (!grid_ln) {
+      cudaFuncSetAttribute(k_volume_f32_line<VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM);
+      int dev = 0, sms = 0, per_sm = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_volume_f32_line<VF>, LN_THREADS, LN_SMEM);
+      grid_ln = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const int blocks = d.nE < grid_ln ? d.nE : grid_ln;
+    k_volume_f32_line<VF><<<blocks, LN_THREADS, LN_SMEM, s>>>(d, U, out, g, mode, first, dt, A, B);
+    return;
+  }
+  if (TMA_OK && d.use_tma >= 2 && aligned) {  // warp-specialised persistent kernel
     static int grid_ws = 0;
     if (!grid_ws) {
       cudaFuncSetAttribute(k_volume_f32_ws<VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WS_SMEM);

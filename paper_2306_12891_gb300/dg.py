@@ -320,8 +320,9 @@ class DG:
                     "dg_get_metrics")
         return Ja, J
 
-    def use_tma(self, mode=2):
-        """FP32-bulk volume kernel: 2 warp-specialised TMA (default), 1 TMA, 0 plain."""
+    def use_tma(self, mode=3):
+        """FP32-bulk volume kernel: 3 pair-symmetric line kernel (default; N = 7, else mode 2),
+        2 warp-specialised node kernel, 1 TMA node kernel, 0 plain node kernel."""
         self._check(lib().dg_use_tma(self._ctx, int(mode)), "dg_use_tma")
 
     def use_graphs(self, on=True):

@@ -1,8 +1,9 @@
 """FP32-bulk precision form against the FP64 oracle.
 
 Volume, surface and lifting arithmetic run in FP32 with FP32 accumulation; U is read as FP64,
-metrics and Jacobian are computed in FP64, and the 1/J scaling, the LSERK register/state update and
-the reductions stay FP64. The error of each result against the FP64 oracle is stated (printed as
+metrics and Jacobian are computed in FP64, and the LSERK register/state accumulation and the
+reductions stay FP64 (the stage increment is the FP32 sum times the factor dt (-1/J), formed in FP64
+and rounded once). The error of each result against the FP64 oracle is stated (printed as
 PARITY32 lines) and bounded: relative to the flux scale of tests/helpers.py the right-hand side
 must agree to TOL32 = 64 * 2^-24 (~3.8e-6) -- FP32 rounding of the O(3(N+1)) flux-difference terms
 -- and time-stepped states relative to dt * scale per stage.
@@ -213,3 +214,84 @@ def test_full_size_fp32_rhs_sampled(env):
     err = parity(Ut[sample], Ur[sample], scale)
     print(f"PARITY32 full size 48^3: {err}")
     assert (err <= TOL32).all(), err
+
+
+def _line_pair(env, xyz, faces, U0, mode, p_ref=1.0 / 1.4, **phys):
+    dg, orc, torch = env
+    gpu = dg.DG(7, xyz, faces, precision="fp32_bulk", p_ref=p_ref, **phys)
+    gpu.use_tma(mode)
+    Ut = gpu.rhs(torch.from_numpy(U0).cuda()).cpu().numpy()
+    gpu.check()
+    return gpu, Ut
+
+
+@pytest.mark.parametrize("vf,sf,eq", [("kg", "llf", "euler"), ("pirozzoli", "roe", "ns"), ("kg", "roe", "ns"),
+                                      ("ec", "ec", "euler"), ("central", "llf", "ns")])
+def test_line_kernel_rhs(env, vf, sf, eq):
+    """The pair-symmetric FP32 line kernel (dg_use_tma(3), N = 7) against the FP64 oracle on a curved
+    mesh. Its sums run in another order than the node kernels', so it is held to the FP32 tolerance,
+    not to their bits."""
+    dg, orc, torch = env
+    xyz, faces = W.box_mesh(7, (2, 3, 2), mapping=_generic_map)
+    U0 = W.random_smooth_state(xyz, seed=21, amp=0.1)
+    U0 = U0 * (1.0 + 0.01 * np.random.default_rng(22).uniform(-1, 1, U0.shape))
+    phys = dict(equations=eq, vflux=vf, sflux=sf, mu=0.02)
+    _, Ut = _line_pair(env, xyz, faces, U0, 3, **phys)
+    ref = orc.Oracle(7, xyz, faces, **phys)
+    Ur = ref.rhs(U0)
+    scale = flux_scale(U0, ref.Ja, ref.J, orc.dmatrix(7))
+    err = parity(Ut, Ur, scale)
+    _, Ut0 = _line_pair(env, xyz, faces, U0, 0, **phys)
+    err0 = parity(Ut0, Ur, scale)
+    print(f"PARITY32 line kernel {vf}/{sf}/{eq}: {err} (node kernel {err0})")
+    assert (err <= TOL32).all(), (err, normwise(Ut, Ur))
+
+
+def test_line_kernel_rotated_elements_and_walls(env):
+    dg, orc, torch = env
+    phys = dict(equations="ns", vflux="pirozzoli", sflux="roe", mu=0.02)
+    xyz, faces, _ = W.rotated_box_mesh(7, (3, 2, 2), seed=9, mapping=_generic_map)
+    U0 = W.random_smooth_state(xyz, seed=23, amp=0.1)
+    _, Ut = _line_pair(env, xyz, faces, U0, 3, **phys)
+    ref = orc.Oracle(7, xyz, faces, **phys)
+    err = parity(Ut, ref.rhs(U0), flux_scale(U0, ref.Ja, ref.J, orc.dmatrix(7)))
+    print(f"PARITY32 line kernel rotated elements: {err}")
+    assert (err <= TOL32).all(), err
+    xyz, faces = W.box_mesh(7, (2, 2, 3), lo=(0, 0, 0), hi=(2 * np.pi, np.pi, 2.0), z_walls=True)
+    U0 = W.random_smooth_state(xyz, seed=24, amp=0.1)
+    phys = dict(phys, mu=1e-3, wm_index=2)
+    _, Ut = _line_pair(env, xyz, faces, U0, 3, **phys)
+    ref = orc.Oracle(7, xyz, faces, **phys)
+    err = parity(Ut, ref.rhs(U0), flux_scale(U0, ref.Ja, ref.J, orc.dmatrix(7)))
+    print(f"PARITY32 line kernel wall-modelled channel: {err}")
+    assert (err <= TOL32).all(), err
+
+
+def test_line_kernel_steps(env):
+    """Ten LSERK steps through the line kernel's fused FP64 epilogue against the FP64 oracle, and the
+    graph-replayed steps bit for bit against directly launched ones."""
+    dg, orc, torch = env
+    w = W.WORKLOADS["tgv_ns_n7_48x48x48_curved_fp32"].with_(nel=(3, 3, 3))
+    xyz, faces = w.mesh()
+    U0 = w.initial_state(xyz)
+    ref = orc.Oracle(w.N, xyz, faces, **w.physics())
+    dt = ref.max_dt(U0, w.cfl)
+    K = 10
+    outs = []
+    for graphs in (True, False):
+        gpu = dg.DG(w.N, xyz, faces, precision="fp32_bulk", p_ref=P0_TGV, **w.physics())
+        gpu.use_tma(3)
+        gpu.use_graphs(graphs)
+        U = torch.from_numpy(U0).cuda()
+        gpu.lserk_steps(U, dt, K)
+        gpu.check()
+        outs.append(U)
+    assert torch.equal(outs[0], outs[1])
+    Ur = U0.copy()
+    for _ in range(K):
+        Ur = ref.lserk_step(Ur, dt)
+    d = (outs[0].cpu().numpy() - Ur).reshape(Ur.shape[0], 5, -1)
+    linf = np.abs(d).max(axis=(0, 2))
+    scale = flux_scale(U0, ref.Ja, ref.J, orc.dmatrix(w.N))
+    print(f"PARITY32 line kernel after {K} steps: Linf {linf}")
+    assert (linf <= 5 * K * TOL32 * dt * scale).all(), (linf, dt * scale)
