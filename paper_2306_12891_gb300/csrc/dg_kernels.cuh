@@ -567,7 +567,11 @@ __global__ void __launch_bounds__(LIFT_THREADS, lift_min_blocks<R>()) k_lift(con
   }
   __syncthreads();
   const R mu = Cst<R>::mu(d), kappa = Cst<R>::kappa(d);
-  for (int t = threadIdx.x; t < LIFT_EPB * nnn; t += blockDim.x) {
+  // the thread's nodes unrolled, so that their metric loads are in flight together
+#pragma unroll
+  for (int rr = 0; rr < (LIFT_EPB * nnn + LIFT_THREADS - 1) / LIFT_THREADS; ++rr) {
+    const int t = threadIdx.x + rr * LIFT_THREADS;
+    if (t >= LIFT_EPB * nnn) continue;
     const int le = t / nnn, node = t % nnn, e = e0 + le;
     if (e >= d.nE) continue;
     const int ijk[3] = {node % n, (node / n) % n, node / nn};
