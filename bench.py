@@ -218,27 +218,92 @@ def throttled(clk: dict) -> bool:
     return bool(sm and smax and sm < 0.8 * smax and not clk.get("reasons"))
 
 
-def cpu_baseline(steps_budget_s: float = 15.0) -> dict:
-    """The FP64 oracle, as it stands, single-threaded on the host: LSERK(5,4) stages of the same
-    physics on a 6^3-element sub-box of the workload (110,592 DOF), until ~steps_budget_s."""
+def _oracle_worker(kind: str, nel: int, seconds: float, warmup: int, steps: int, barrier, queue) -> None:
+    """One host process of the oracle timing: the same physics on an nel^3-element sub-box of the
+    workload; after a common start (barrier), right-hand sides for `seconds` (kind "rhs") or `steps`
+    LSERK(5,4) steps after `warmup` untimed ones (kind "steps"). Puts (DOF-stages, seconds)."""
     import oracle
 
-    oracle.build()
-    w = WORKLOADS[WORKLOAD].with_(nel=(6, 6, 6))
+    w = WORKLOADS[WORKLOAD].with_(nel=(nel,) * 3)
     xyz, faces = w.mesh()
     U = w.initial_state(xyz)
     ref = oracle.Oracle(w.N, xyz, faces, **w.physics())
+    dt = ref.max_dt(U, w.cfl)
+    if kind == "rhs":
+        ref.rhs(U)
+    for _ in range(warmup if kind == "steps" else 0):
+        U = ref.lserk_step(U, dt)
+    barrier.wait()
     t0 = time.perf_counter()
     stages = 0
-    while True:
-        ref.rhs(U)
-        stages += 1
-        if time.perf_counter() - t0 > steps_budget_s:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": w.dofs * stages / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{stages} right-hand sides of the same physics on a 6x6x6-element sub-box "
-                      f"({w.dofs} DOF), single-threaded FP64 C oracle, {dt:.1f} s"}
+    if kind == "rhs":
+        while time.perf_counter() - t0 < seconds:
+            ref.rhs(U)
+            stages += 1
+    else:
+        for _ in range(steps):
+            U = ref.lserk_step(U, dt)
+            stages += STAGES
+    queue.put((w.dofs * stages, time.perf_counter() - t0))
+
+
+def oracle_parallel(kind: str, nel: int, procs: int, seconds: float = 0.0, warmup: int = 0, steps: int = 0):
+    """The oracle, as it stands, in `procs` host processes at once (spawned, so no GPU context is
+    inherited), each on its own sub-box; returns the total DOF-stages per second over the slowest
+    process's time and the per-process results."""
+    import multiprocessing
+
+    import oracle
+
+    oracle.build()
+    ctx = multiprocessing.get_context("spawn")
+    barrier, queue = ctx.Barrier(procs), ctx.Queue()
+    ps = [ctx.Process(target=_oracle_worker, args=(kind, nel, seconds, warmup, steps, barrier, queue))
+          for _ in range(procs)]
+    for p in ps:
+        p.start()
+    res = [queue.get(timeout=600) for _ in ps]
+    for p in ps:
+        p.join()
+    return sum(r[0] for r in res) / max(max(r[1] for r in res), 1e-9), res
+
+
+def host_cpu() -> dict:
+    """Host core count and CPU model name (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+def cpu_baseline(seconds: float = 12.0) -> dict:
+    """The FP64 oracle, as it stands, on the host cores: right-hand sides of the same physics on a
+    6^3-element sub-box of the workload (110,592 DOF) per process, for ~`seconds`; one process per
+    host core at once, and the single-process rate beside it."""
+    cpu = host_cpu()
+    procs = cpu["nproc"] or 1
+    value, res = oracle_parallel("rhs", 6, procs, seconds=seconds)
+    single, _ = oracle_parallel("rhs", 6, 1, seconds=seconds / 2)
+    stages = sum(r[0] for r in res) // WORKLOADS[WORKLOAD].with_(nel=(6, 6, 6)).dofs
+    return {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"{stages} right-hand sides of the same physics on 6x6x6-element sub-boxes (110592 DOF each), "
+                      f"FP64 C oracle in {procs} processes at once, {max(r[1] for r in res):.1f} s",
+            "single_core_value": single, "host": cpu}
 
 
 def run_reference(args):
@@ -247,28 +312,19 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import oracle
-
-    oracle.build()
     w = WORKLOADS[WORKLOAD].with_(nel=(3, 3, 3))
-    xyz, faces = w.mesh()
-    U = w.initial_state(xyz)
-    ref = oracle.Oracle(w.N, xyz, faces, **w.physics())
-    dt = ref.max_dt(U, w.cfl)
-    for _ in range(args.warmup):
-        U = ref.lserk_step(U, dt)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        U = ref.lserk_step(U, dt)
-    el = time.perf_counter() - t0
-    value = w.dofs * STAGES * args.steps / el
-    sample = (f"each step: one LSERK(5,4) step of the same physics on a 3x3x3-element sub-box ({w.dofs} DOF), "
-              f"single-threaded FP64 C oracle")
+    cpu = host_cpu()
+    procs = cpu["nproc"] or 1
+    value, res = oracle_parallel("steps", 3, procs, warmup=args.warmup, steps=args.steps)
+    el = max(r[1] for r in res)
+    sample = (f"each step: one LSERK(5,4) step of the same physics on a 3x3x3-element sub-box ({w.dofs} DOF) "
+              f"in each of {procs} processes at once (FP64 C oracle, one process per host core)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "sample_elements": w.n_elems, "N": w.N},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample,
+                             "host": cpu},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -360,13 +416,15 @@ def run_adjoint(stream, peak_fp64: float, interval: int = 10) -> dict:
 
 def run_other_workloads(stream) -> dict:
     """Throughput of the other named workloads (the benchmark table's remaining rows): the small N=3
-    Euler case (launch bound; CUDA-graph replay on), the blast with DG/FV blending at 64^3 (as named)
+    Euler case (launch bound; CUDA-graph replay on), the paper's free-stream benchmark case (N=7, 32^3
+    Cartesian, Navier-Stokes), the blast with DG/FV blending at 64^3 (as named)
     and 40^3 (the size the quoted DOF count implies), and the FP32-bulk 48^3 form."""
     import torch
 
     from paper_2306_12891_gb300 import dg
 
-    cases = [("tgv_euler_n3_4x4x4", None, 200, {}), ("blast_euler_fv_n5_64x64x64", None, 5, {}),
+    cases = [("tgv_euler_n3_4x4x4", None, 200, {}), ("freestream_ns_n7_32x32x32", None, 5, {}),
+             ("blast_euler_fv_n5_64x64x64", None, 5, {}),
              ("blast_euler_fv_n5_64x64x64", 40, 5, {}),
              ("tgv_ns_n7_48x48x48_curved_fp32", None, 5, dict(precision="fp32_bulk", p_ref=P0_TGV))]
     out = {}

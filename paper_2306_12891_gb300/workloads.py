@@ -383,6 +383,10 @@ WORKLOADS = {
     "tgv_ns_n7_32x32x32_curved": Workload("tgv_ns_n7_32x32x32_curved", 7, (32, 32, 32), "ns", "pirozzoli",
                                           "roe", "tgv", mapping="sine_0.05", mu=1.0 / RE_TGV,
                                           steps=100, cfl=0.9),
+    # the paper's performance benchmark case (Sec. 2): Navier-Stokes, N=7, 32^3 periodic Cartesian
+    # [0,2pi]^3, Pirozzoli + Roe + BR1, free stream
+    "freestream_ns_n7_32x32x32": Workload("freestream_ns_n7_32x32x32", 7, (32, 32, 32), "ns", "pirozzoli", "roe",
+                                          "freestream", mu=1.0 / RE_TGV, steps=100, cfl=0.9),
     # Euler + FV subcell blending, N=5, 64^3 on the unit cube, Pirozzoli + LLF, blast + 1% noise
     "blast_euler_fv_n5_64x64x64": Workload("blast_euler_fv_n5_64x64x64", 5, (64, 64, 64), "euler",
                                            "pirozzoli", "llf", "blast", lo=(0.0, 0.0, 0.0),

@@ -56,3 +56,17 @@ def test_throttle_rule():
     assert not bench.throttled({"reasons": ["sw_power_cap"], "sm_mhz": 1500.0, "sm_max_mhz": 2070.0})
     assert not bench.throttled({"reasons": [], "sm_mhz": 2070.0, "sm_max_mhz": 2070.0})
     assert not bench.throttled({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]})
+
+
+def test_oracle_timing_in_parallel_processes():
+    """The CPU baseline's parallel oracle timing: spawned processes, each on its own sub-box, start
+    together and report their DOF-stages and time; the total rate is the sum over the slowest time."""
+    import bench
+
+    value, res = bench.oracle_parallel("steps", 2, 2, warmup=0, steps=1)
+    assert len(res) == 2
+    dofs = bench.WORKLOADS[bench.WORKLOAD].with_(nel=(2, 2, 2)).dofs
+    assert all(r[0] == dofs * bench.STAGES for r in res)
+    assert value == pytest.approx(2 * dofs * bench.STAGES / max(r[1] for r in res))
+    cpu = bench.host_cpu()
+    assert cpu["nproc"] and cpu["nproc"] >= 1
