@@ -626,7 +626,8 @@ def run_gpu(args):
     breakdown = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / max(1e-9, sum(x[0] for x in ktimes.values())), 4)}
                  for k, v in ktimes.items() if v[1]}
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC if not fp32_main else METRIC.replace("FP64", "FP32-bulk"), "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if fp32_main else "f64", "data": "synthetic",
         "config": {"workload": args.workload if not args.nel else f"{args.workload} reduced to {args.nel}^3",
