@@ -1173,16 +1173,16 @@ __device__ __forceinline__ void f32_node_terms(const DgDevice &d, const float *_
 
 // -1/J and the output / LSERK(5,4) stage in FP64 for one node; Ue, ge point at this element's state
 // and register slices [5][nnn] to read (shared or global memory), out and g are global
-__device__ __forceinline__ void f32_finish(const DgDevice &d, const double *Ue, const double *ge,
-                                           const double *iJe, double *out, double *__restrict__ g, int e,
-                                           int node, const float s[5], int mode, int first, double dt,
-                                           double A, double B) {
-  // Ue, ge, iJe: this element's U, g and 1/J (global memory or a shared-memory copy).
+__device__ __forceinline__ void f32_finish_reg(const DgDevice &d, const double Uv[5], const double gv0[5],
+                                               double iJ, double *out, double *__restrict__ g, int e, int node,
+                                               const float s[5], int mode, int first, double dt, double A,
+                                               double B) {
+  // Uv, gv0, iJ: this node's U, g and 1/J.
   // The right-hand side -s/J, or the stage increment dt (-1/J) s, is one FP32 product of the FP32 sum
   // s with the factor -1/J or dt (-1/J), formed in FP64 and rounded once (GB300 issues FP64 at 1/64
   // of the FP32 rate, and this epilogue bounds the kernel); the LSERK register and the state
   // accumulate in FP64. Explicit roundings (no compiler contraction) keep every kernel variant's bits.
-  const double miJ = -iJe[node];
+  const double miJ = -iJ;
   const size_t gi = (size_t)e * 5 * nnn + node;
   if (mode == 0) {
     const float c = d2f_int(miJ);
@@ -1195,12 +1195,28 @@ __device__ __forceinline__ void f32_finish(const DgDevice &d, const double *Ue, 
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     const double du = f2d_int(__fmul_rn(s[v], c));
-    const double gv = first ? du : __fma_rn(A, ge[node + v * nnn], du);
+    const double gv = first ? du : __fma_rn(A, gv0[v], du);
     g[gi + v * nnn] = gv;
-    const double un = __fma_rn(B, gv, Ue[node + v * nnn]);
+    const double un = __fma_rn(B, gv, Uv[v]);
     out[gi + v * nnn] = un;
     d.Uf[gi + v * nnn] = d2f_int(v == 4 ? __dsub_rn(un, eref) : un);
   }
+}
+
+// the same with this element's U, g and 1/J read from global memory or a shared-memory copy
+__device__ __forceinline__ void f32_finish(const DgDevice &d, const double *Ue, const double *ge,
+                                           const double *iJe, double *out, double *__restrict__ g, int e,
+                                           int node, const float s[5], int mode, int first, double dt,
+                                           double A, double B) {
+  double Uv[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, gv0[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (mode == 1) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      Uv[v] = Ue[node + v * nnn];
+      if (!first) gv0[v] = ge[node + v * nnn];
+    }
+  }
+  f32_finish_reg(d, Uv, gv0, iJe[node], out, g, e, node, s, mode, first, dt, A, B);
 }
 
 template <int VF>
@@ -1545,15 +1561,23 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_volume_f32_ws(const DgDevice 
 // and viscous terms enter divided by them (exact).
 // ---------------------------------------------------------------------------------------------
 constexpr bool LN_OK = (N == 7);
-constexpr int LN_COMPUTE = 3 * nn;  // line threads
+// four warp groups: two of epilogue warps (threads 0-255), two of line warps (256-511: 192 line
+// threads, 64 that only help staging); setmaxnreg moves registers from the epilogue groups to the
+// line groups, whose eight nodes' values and sums need ~168 per thread
 constexpr int LN_EPI = 256;
-constexpr int LN_THREADS = LN_COMPUTE + LN_EPI;
+constexpr int LN_GROUP = 256;       // threads of the line warp groups
+constexpr int LN_COMPUTE = 3 * nn;  // line threads
+constexpr int LN_THREADS = LN_EPI + LN_GROUP;
+constexpr int LN_REG_LAUNCH = 65536 / LN_THREADS, LN_REG_LINE = 168, LN_REG_EPI = 88;
+static_assert(LN_EPI * LN_REG_EPI + LN_GROUP * LN_REG_LINE <= LN_THREADS * LN_REG_LAUNCH,
+              "the register split must fit the registers the block is launched with");
 constexpr unsigned LN_CBUF = TB_UF + TB_JA + TB_FV;  // per-element TMA slices of the line phase
 constexpr unsigned LN_ACC = 15u * nnn * 4u;          // [3 d][5][nnn] per-direction sums
 constexpr unsigned LN_SMEM = 2u * LN_CBUF + TB_P + 2u * LN_ACC + WS_UG + 64u;
 static_assert(!LN_OK || LN_SMEM <= 232448 - 256, "line kernel exceeds the shared memory of one CTA");
 static_assert(!LN_OK || (LN_CBUF % 16 == 0 && LN_ACC % 16 == 0), "shared-memory regions must stay 16-byte aligned");
-static_assert(!LN_OK || nnn % LN_EPI == 0, "the epilogue threads take whole nodes");
+static_assert(!LN_OK || (nnn % LN_EPI == 0 && nnn % LN_GROUP == 0 && LN_COMPUTE <= LN_GROUP),
+              "the epilogue and staging threads take whole nodes");
 
 // bijective swizzle of node (i, j, k) = i + 8 j + 64 k for N = 7 (identity otherwise): the five
 // low bits (the bank) are (i ^ j, (j ^ k) mod 4), which differ across the 32 lanes of an x, y or z
@@ -1618,6 +1642,13 @@ __device__ __forceinline__ void line_pairs(LineRegs &R, float gam, float pref) {
   }
 }
 
+__device__ __forceinline__ void regs_inc_line() {
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(LN_REG_LINE));
+}
+__device__ __forceinline__ void regs_dec_epi() {
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(LN_REG_EPI));
+}
+
 template <int VF>
 __global__ void __launch_bounds__(LN_THREADS, 1) k_volume_f32_line(const DgDevice d, const double *U, double *out,
                                                                     double *g, int mode, int first, double dt,
@@ -1639,8 +1670,8 @@ __global__ void __launch_bounds__(LN_THREADS, 1) k_volume_f32_line(const DgDevic
     if (tid == 0) {
       mbar_init(smem_addr(&bar[0]));
       mbar_init(smem_addr(&bar[1]));
-      mbar_init_n(smem_addr(&bar[2]), LN_COMPUTE);
-      mbar_init_n(smem_addr(&bar[3]), LN_COMPUTE);
+      mbar_init_n(smem_addr(&bar[2]), LN_GROUP);
+      mbar_init_n(smem_addr(&bar[3]), LN_GROUP);
       mbar_init_n(smem_addr(&bar[4]), LN_EPI);
       mbar_init_n(smem_addr(&bar[5]), LN_EPI);
       mbar_init(smem_addr(&bar[6]));
@@ -1659,13 +1690,16 @@ __global__ void __launch_bounds__(LN_THREADS, 1) k_volume_f32_line(const DgDevic
       bulk_g2s(smem_addr(b + TB_UF), d.Jaf + e * 9 * nnn, TB_JA, mb);
       if (ns) bulk_g2s(smem_addr(b + TB_UF + TB_JA), d.Fv_f + e * 12 * nnn, TB_FV, mb);
     };
-    if (tid < LN_COMPUTE) {
-      if (tid == 0) {
+    if (tid >= LN_EPI) {
+      regs_inc_line();
+      const int ct = tid - LN_EPI;  // thread of the line warp groups
+      const bool line = ct < LN_COMPUTE;
+      if (ct == 0) {
         issue(0);
         issue(1);
       }
       // this thread's line: direction dd (warp-uniform), position (la, lb) on the faces 2dd, 2dd+1
-      const int dd = tid / nn, L = tid % nn, la = L % n, lb = L / n;
+      const int dd = line ? ct / nn : 0, L = ct % nn, la = L % n, lb = L / n;
       const int st = dd == 0 ? 1 : dd == 1 ? n : nn;
       const int base = dd == 0 ? n * la + nn * lb : dd == 1 ? la + nn * lb : la + n * lb;
       const float gam = d.gamma_f, pref = d.p_ref_f;
@@ -1673,7 +1707,7 @@ __global__ void __launch_bounds__(LN_THREADS, 1) k_volume_f32_line(const DgDevic
       // face records of the line's two faces, loaded one element ahead (a warp issues in order: an
       // address computed from a just-loaded record would stall it for a full memory latency)
       int4 rec_next[2] = {make_int4(0, 0, 0, 0), make_int4(0, 0, 0, 0)};
-      if (ns && blockIdx.x < d.nE) {
+      if (ns && line && blockIdx.x < d.nE) {
         rec_next[0] = *reinterpret_cast<const int4 *>(d.ef + ((size_t)blockIdx.x * 6 + 2 * dd) * 4);
         rec_next[1] = *reinterpret_cast<const int4 *>(d.ef + ((size_t)blockIdx.x * 6 + 2 * dd + 1) * 4);
       }
@@ -1683,7 +1717,7 @@ __global__ void __launch_bounds__(LN_THREADS, 1) k_volume_f32_line(const DgDevic
         if (e >= d.nE) break;
         const int b = k & 1;
         const int4 rec[2] = {rec_next[0], rec_next[1]};
-        if (ns && e + gridDim.x < d.nE) {
+        if (ns && line && e + gridDim.x < d.nE) {
           rec_next[0] = *reinterpret_cast<const int4 *>(d.ef + ((size_t)(e + gridDim.x) * 6 + 2 * dd) * 4);
           rec_next[1] = *reinterpret_cast<const int4 *>(d.ef + ((size_t)(e + gridDim.x) * 6 + 2 * dd + 1) * 4);
         }
@@ -1693,12 +1727,13 @@ __global__ void __launch_bounds__(LN_THREADS, 1) k_volume_f32_line(const DgDevic
         const float *Jb = reinterpret_cast<const float *>(buf + TB_UF);
         const float *Fb = reinterpret_cast<const float *>(buf + TB_UF + TB_JA);
         if (!s_abort)
-          for (int t = tid; t < nnn; t += LN_COMPUTE) {
+          for (int t = ct; t < nnn; t += LN_GROUP) {
             const float Uv[5] = {Uf[t], Uf[nnn + t], Uf[2 * nnn + t], Uf[3 * nnn + t], Uf[4 * nnn + t]};
             f32_stage<VF>(d, Uv, P + ln_sw(t));
           }
-        named_sync(1, LN_COMPUTE);
+        named_sync(1, LN_GROUP);
         if (s_abort) break;
+        if (line) {
         // end-node data from global memory, loaded before the pair sums so that its latency overlaps them
         float fs[2][5], fnb[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
         int wall[2] = {0, 0};
@@ -1779,12 +1814,13 @@ __global__ void __launch_bounds__(LN_THREADS, 1) k_volume_f32_line(const DgDevic
 #pragma unroll
           for (int v = 0; v < 5; ++v) Ab[v * nnn + sw] = acc[i][v];
         }
+        }  // line
         mbar_arrive(smem_addr(&bar[2 + b]));
-        named_sync(1, LN_COMPUTE);  // buffer b and P are free again
+        named_sync(1, LN_GROUP);  // buffer b and P are free again
         if (s_abort) break;
-        if (tid == 0) issue(k + 2);
+        if (ct == 0) issue(k + 2);
       }
-      if (s_abort && tid == 0) {  // report; wait (bounded) for the next element's copy still in flight
+      if (s_abort && ct == 0) {  // report; wait (bounded) for the next element's copy still in flight
         flag_set(d.flag, 4);
         if ((long long)blockIdx.x + (long long)(k + 1) * gridDim.x < d.nE)
           mbar_wait(smem_addr(&bar[(k + 1) & 1]), (unsigned)(((k + 1) >> 1) & 1));
@@ -1792,7 +1828,8 @@ __global__ void __launch_bounds__(LN_THREADS, 1) k_volume_f32_line(const DgDevic
     } else {
       // epilogue warps: sum the three directions, scale, -1/J and the FP64 LSERK stage; the FP64
       // state, register and 1/J arrive by TMA one element ahead (issued once the group is done)
-      const int et = tid - LN_COMPUTE;
+      regs_dec_epi();
+      const int et = tid;
       const bool needU = mode == 1, needG = mode == 1 && !first;
       const unsigned ug_bytes = TB_IJ + (needU ? TB_U : 0u) + (needG ? TB_G : 0u);
       auto issue_ug = [&](int k) {
@@ -1813,25 +1850,34 @@ __global__ void __launch_bounds__(LN_THREADS, 1) k_volume_f32_line(const DgDevic
         const int b = k & 1;
         if (!mbar_wait(smem_addr(&bar[2 + b]), (unsigned)((k >> 1) & 1))) s_abort_e = 1;
         if (!mbar_wait(smem_addr(&bar[6]), (unsigned)(k & 1))) s_abort_e = 1;
+        // the thread's nodes' sums, U, g and 1/J into registers first; then the sums buffer and the
+        // U, g, 1/J buffer are released (the next element's copy overlaps this element's FP64 stage)
+        constexpr int R = nnn / LN_EPI;
+        float sv[R][5];
+        double Uv[R][5], gv0[R][5], iJ[R];
         if (!s_abort_e) {
           const float *A0 = ACC + (b * 3) * 5 * nnn, *A1 = A0 + 5 * nnn, *A2 = A1 + 5 * nnn;
           const double *Ue = reinterpret_cast<const double *>(UG), *ge = reinterpret_cast<const double *>(UG + TB_U),
                        *iJe = reinterpret_cast<const double *>(UG + TB_U + TB_G);
-          // all of the thread's nodes at once (unrolled): their conversion and FP64 chains overlap
 #pragma unroll
-          for (int r = 0; r < nnn / LN_EPI; ++r) {
+          for (int r = 0; r < R; ++r) {
             const int node = et + r * LN_EPI, sw = ln_sw(node);
-            float sv[5];
 #pragma unroll
-            for (int v = 0; v < 5; ++v)
-              sv[v] = (v == 0 ? SC0 : SC1) * ((A0[v * nnn + sw] + A1[v * nnn + sw]) + A2[v * nnn + sw]);
-            f32_finish(d, Ue, ge, iJe, out, g, (int)e, node, sv, mode, first, dt, A, B);
+            for (int v = 0; v < 5; ++v) {
+              sv[r][v] = (v == 0 ? SC0 : SC1) * ((A0[v * nnn + sw] + A1[v * nnn + sw]) + A2[v * nnn + sw]);
+              Uv[r][v] = needU ? Ue[node + v * nnn] : 0.0;
+              gv0[r][v] = needG ? ge[node + v * nnn] : 0.0;
+            }
+            iJ[r] = iJe[node];
           }
         }
         mbar_arrive(smem_addr(&bar[4 + b]));
         named_sync(2, LN_EPI);  // the group is done with the U, g, 1/J buffer
         if (s_abort_e) break;
         if (et == 0) issue_ug(k + 1);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          f32_finish_reg(d, Uv[r], gv0[r], iJ[r], out, g, (int)e, et + r * LN_EPI, sv[r], mode, first, dt, A, B);
       }
       if (s_abort_e && et == 0) {  // report; wait (bounded) for this element's copy, the one in flight
         flag_set(d.flag, 4);
@@ -2099,16 +2145,24 @@ template <int VF>
 void launch_volume_f32(const DgDevice &d, const double *U, double *out, double *g, int mode, int first, double dt,
                        double A, double B, cudaStream_t s) {
   const bool aligned = !(((uintptr_t)U | (uintptr_t)out | (uintptr_t)g) & 15u);
-  if (LN_OK && d.use_tma == 3 && aligned) {  // pair-symmetric line kernel, warp-specialised
-    static int grid_ln = 0;
-    if (!grid_ln) {
+  // pair-symmetric line kernel, warp-specialised. Its warp groups trade registers (setmaxnreg), which
+  // is only safe if the block is launched with exactly the registers the split assumes; any other
+  // compiled count takes the warp-specialised node kernel instead.
+  static int grid_ln = 0;  // > 0: usable, < 0: not usable
+  if (LN_OK && d.use_tma == 3 && aligned && grid_ln == 0) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, k_volume_f32_line<VF>) == cudaSuccess && fa.numRegs == LN_REG_LAUNCH) {
       cudaFuncSetAttribute(k_volume_f32_line<VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM);
       int dev = 0, sms = 0, per_sm = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_volume_f32_line<VF>, LN_THREADS, LN_SMEM);
-      grid_ln = sms * (per_sm > 0 ? per_sm : 1);
+      grid_ln = per_sm == 1 ? sms : -1;  // one block per SM: the register split needs the whole file
+    } else {
+      grid_ln = -1;
     }
+  }
+  if (LN_OK && d.use_tma == 3 && aligned && grid_ln > 0) {
     const int blocks = d.nE < grid_ln ? d.nE : grid_ln;
     k_volume_f32_line<VF><<<blocks, LN_THREADS, LN_SMEM, s>>>(d, U, out, g, mode, first, dt, A, B);
     return;
