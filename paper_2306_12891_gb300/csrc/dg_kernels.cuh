@@ -542,6 +542,84 @@ __global__ void __launch_bounds__(256) k_face(const DgDevice d, const double *__
 // resident 256-thread CTAs per SM the register budget must allow: FP32 five (48 registers), FP64 three
 template <typename R> __host__ __device__ constexpr int lift_min_blocks() { return std::is_same<R, float>::value ? 5 : 3; }
 
+// (u, v, w, T) of one node from its state values (lifted quantities of BR1)
+template <typename R>
+__device__ __forceinline__ void lift_prim(const R Uv[5], R gm1, R iR, R pref, R Wn[4]) {
+  const R r = Uv[0], ir = R(1) / r;
+  const R u = Uv[1] * ir, v = Uv[2] * ir, w = Uv[3] * ir;
+  R p = gm1 * (Uv[4] - R(0.5) * r * (u * u + v * v + w * w));
+  if (kShift<R>) p += pref;
+  Wn[0] = u;
+  Wn[1] = v;
+  Wn[2] = w;
+  Wn[3] = p * ir * iR;
+}
+
+// one node's BR1 gradients and contravariant viscous flux: W = the element's lifted quantities
+// [4][nnn] (shared memory), Jae its metric terms [3 d][3 c][nnn], Wse its BR1 face jumps [6][4][nn],
+// iJ this node's 1/J; writes the element's Fv [3 d][4][nnn] at `node` (out = the element's Fv)
+template <typename R>
+__device__ __forceinline__ void lift_node(const DgDevice &d, int node, const R *__restrict__ W,
+                                          const R (*__restrict__ sD)[n + 1], const R *__restrict__ Jae,
+                                          const R *__restrict__ Wse, R iJ, R mu, R kappa, R *__restrict__ out) {
+  const int ijk[3] = {node % n, (node / n) % n, node / nn};
+  R Ja[3][3];
+#pragma unroll
+  for (int dd = 0; dd < 3; ++dd)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Ja[dd][c] = Jae[(dd * 3 + c) * nnn + node];
+  R g[4][3];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) g[q][0] = g[q][1] = g[q][2] = R(0);
+#pragma unroll
+  for (int dd = 0; dd < 3; ++dd) {
+    const int id = ijk[dd];
+    const int st = dd == 0 ? 1 : dd == 1 ? n : nn;
+    const int base = node - id * st;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      R s = R(0);
+#pragma unroll
+      for (int m = 0; m < n; ++m) s += sD[id][m] * W[q * nnn + base + m * st];
+      g[q][0] += Ja[dd][0] * s;
+      g[q][1] += Ja[dd][1] * s;
+      g[q][2] += Ja[dd][2] * s;
+    }
+    // surface terms on the faces of direction dd through this node
+    if (id == 0 || id == N) {
+      const int f = 2 * dd + (id == N ? 1 : 0);
+      const R sc = (id == N ? R(1) : R(-1)) * Tab<R>::invw(id);
+      const int pp = dd == 0 ? ijk[1] : ijk[0];
+      const int qq = dd == 2 ? ijk[1] : ijk[2];
+      const R *js = Wse + f * 4 * nn + pp + n * qq;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const R jq = sc * js[q * nn];
+        g[q][0] += Ja[dd][0] * jq;
+        g[q][1] += Ja[dd][1] * jq;
+        g[q][2] += Ja[dd][2] * jq;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) { g[q][0] *= iJ; g[q][1] *= iJ; g[q][2] *= iJ; }
+  // Navier-Stokes-Fourier flux in Cartesian direction c: (tau_xc, tau_yc, tau_zc, u.tau_c + kappa dT/dx_c)
+  const R u = W[node], v = W[nnn + node], w = W[2 * nnn + node];
+  const R div = g[0][0] + g[1][1] + g[2][2];
+  const R t23 = R(2.0 / 3.0) * mu * div;
+  const R txx = R(2) * mu * g[0][0] - t23, tyy = R(2) * mu * g[1][1] - t23, tzz = R(2) * mu * g[2][2] - t23;
+  const R txy = mu * (g[0][1] + g[1][0]), txz = mu * (g[0][2] + g[2][0]), tyz = mu * (g[1][2] + g[2][1]);
+  R Fc[3][4];
+  Fc[0][0] = txx; Fc[0][1] = txy; Fc[0][2] = txz; Fc[0][3] = u * txx + v * txy + w * txz + kappa * g[3][0];
+  Fc[1][0] = txy; Fc[1][1] = tyy; Fc[1][2] = tyz; Fc[1][3] = u * txy + v * tyy + w * tyz + kappa * g[3][1];
+  Fc[2][0] = txz; Fc[2][1] = tyz; Fc[2][2] = tzz; Fc[2][3] = u * txz + v * tyz + w * tzz + kappa * g[3][2];
+#pragma unroll
+  for (int dd = 0; dd < 3; ++dd)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      out[(dd * 4 + q) * nnn + node] = Ja[dd][0] * Fc[0][q] + Ja[dd][1] * Fc[1][q] + Ja[dd][2] * Fc[2][q];
+}
+
 template <typename R>
 __global__ void __launch_bounds__(LIFT_THREADS, lift_min_blocks<R>()) k_lift(const DgDevice d, const double *__restrict__ U) {
   __shared__ R W[LIFT_EPB][4][nnn];
@@ -550,20 +628,14 @@ __global__ void __launch_bounds__(LIFT_THREADS, lift_min_blocks<R>()) k_lift(con
   const int e0 = blockIdx.x * LIFT_EPB;
   const R gm1 = Cst<R>::gm1(d), iR = Cst<R>::iR(d);
   const R pref = Cst<R>::pref(d);
-  const R *Jab = Buf<R>::Ja(d);
   for (int t = threadIdx.x; t < LIFT_EPB * nnn; t += blockDim.x) {
     const int le = t / nnn, node = t % nnn, e = e0 + le;
     if (e >= d.nE) continue;
-    R Uv[5];
+    R Uv[5], Wn[4];
     load_state<R>(d, U, e, node, Uv);
-    const R r = Uv[0], ir = R(1) / r;
-    const R u = Uv[1] * ir, v = Uv[2] * ir, w = Uv[3] * ir;
-    R p = gm1 * (Uv[4] - R(0.5) * r * (u * u + v * v + w * w));
-    if (kShift<R>) p += pref;
-    W[le][0][node] = u;
-    W[le][1][node] = v;
-    W[le][2][node] = w;
-    W[le][3][node] = p * ir * iR;
+    lift_prim<R>(Uv, gm1, iR, pref, Wn);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) W[le][q][node] = Wn[q];
   }
   __syncthreads();
   const R mu = Cst<R>::mu(d), kappa = Cst<R>::kappa(d);
@@ -574,64 +646,9 @@ __global__ void __launch_bounds__(LIFT_THREADS, lift_min_blocks<R>()) k_lift(con
     if (t >= LIFT_EPB * nnn) continue;
     const int le = t / nnn, node = t % nnn, e = e0 + le;
     if (e >= d.nE) continue;
-    const int ijk[3] = {node % n, (node / n) % n, node / nn};
-    R Ja[3][3];
-#pragma unroll
-    for (int dd = 0; dd < 3; ++dd)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) Ja[dd][c] = Jab[(((size_t)e * 3 + dd) * 3 + c) * nnn + node];
-    R g[4][3];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) g[q][0] = g[q][1] = g[q][2] = R(0);
-#pragma unroll
-    for (int dd = 0; dd < 3; ++dd) {
-      const int id = ijk[dd];
-      const int st = dd == 0 ? 1 : dd == 1 ? n : nn;
-      const int base = node - id * st;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        R s = R(0);
-#pragma unroll
-        for (int m = 0; m < n; ++m) s += sD[id][m] * W[le][q][base + m * st];
-        g[q][0] += Ja[dd][0] * s;
-        g[q][1] += Ja[dd][1] * s;
-        g[q][2] += Ja[dd][2] * s;
-      }
-      // surface terms on the faces of direction dd through this node
-      if (id == 0 || id == N) {
-        const int f = 2 * dd + (id == N ? 1 : 0);
-        const R sc = (id == N ? R(1) : R(-1)) * Tab<R>::invw(id);
-        const int pp = dd == 0 ? ijk[1] : ijk[0];
-        const int qq = dd == 2 ? ijk[1] : ijk[2];
-        const R *js = Buf<R>::Wsurf(d) + ((size_t)e * 6 + f) * 4 * nn + pp + n * qq;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const R jq = sc * js[q * nn];
-          g[q][0] += Ja[dd][0] * jq;
-          g[q][1] += Ja[dd][1] * jq;
-          g[q][2] += Ja[dd][2] * jq;
-        }
-      }
-    }
     const R iJ = kShift<R> ? (R)d.invJf[(size_t)e * nnn + node] : (R)d.invJ[(size_t)e * nnn + node];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) { g[q][0] *= iJ; g[q][1] *= iJ; g[q][2] *= iJ; }
-    // Navier-Stokes-Fourier flux in Cartesian direction c: (tau_xc, tau_yc, tau_zc, u.tau_c + kappa dT/dx_c)
-    const R u = W[le][0][node], v = W[le][1][node], w = W[le][2][node];
-    const R div = g[0][0] + g[1][1] + g[2][2];
-    const R t23 = R(2.0 / 3.0) * mu * div;
-    const R txx = R(2) * mu * g[0][0] - t23, tyy = R(2) * mu * g[1][1] - t23, tzz = R(2) * mu * g[2][2] - t23;
-    const R txy = mu * (g[0][1] + g[1][0]), txz = mu * (g[0][2] + g[2][0]), tyz = mu * (g[1][2] + g[2][1]);
-    R Fc[3][4];
-    Fc[0][0] = txx; Fc[0][1] = txy; Fc[0][2] = txz; Fc[0][3] = u * txx + v * txy + w * txz + kappa * g[3][0];
-    Fc[1][0] = txy; Fc[1][1] = tyy; Fc[1][2] = tyz; Fc[1][3] = u * txy + v * tyy + w * tyz + kappa * g[3][1];
-    Fc[2][0] = txz; Fc[2][1] = tyz; Fc[2][2] = tzz; Fc[2][3] = u * txz + v * tyz + w * tzz + kappa * g[3][2];
-    R *out = Buf<R>::Fv(d) + (size_t)e * 12 * nnn + node;
-#pragma unroll
-    for (int dd = 0; dd < 3; ++dd)
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        out[(dd * 4 + q) * nnn] = Ja[dd][0] * Fc[0][q] + Ja[dd][1] * Fc[1][q] + Ja[dd][2] * Fc[2][q];
+    lift_node<R>(d, node, &W[le][0][0], sD, Buf<R>::Ja(d) + (size_t)e * 9 * nnn,
+                 Buf<R>::Wsurf(d) + (size_t)e * 6 * 4 * nn, iJ, mu, kappa, Buf<R>::Fv(d) + (size_t)e * 12 * nnn);
   }
 }
 
@@ -1888,6 +1905,82 @@ __global__ void __launch_bounds__(LN_THREADS, 1) k_volume_f32_line(const DgDevic
 }
 
 // ---------------------------------------------------------------------------------------------
+// FP32-bulk BR1 lifting as a persistent kernel fed by TMA (N = 3, 5, 7): one thread per node, two
+// CTAs per SM; each element's FP32 state, metric terms, 1/J and BR1 face jumps arrive by
+// cp.async.bulk one element ahead into a double buffer, so the loads of the next element overlap
+// this element's arithmetic. The per-node arithmetic is lift_prim / lift_node, as in k_lift.
+// ---------------------------------------------------------------------------------------------
+constexpr int LT_THREADS = TMA_THREADS;
+constexpr unsigned LT_IJ = nnn * 4u, LT_WS = 24u * nn * 4u;
+constexpr unsigned LT_BUF = TB_UF + TB_JA + LT_IJ + LT_WS;
+constexpr unsigned LT_SMEM = 2u * LT_BUF + 4u * nnn * 4u + 16u;
+static_assert(!TMA_OK || (LT_IJ % 16 == 0 && LT_WS % 16 == 0 && LT_BUF % 16 == 0),
+              "TMA slices must be multiples of 16 bytes");
+
+__global__ void __launch_bounds__(LT_THREADS, 2) k_lift_f32_tma(const DgDevice d) {
+  extern __shared__ __align__(128) unsigned char sm_tma[];
+  float *W = reinterpret_cast<float *>(sm_tma + 2 * LT_BUF);  // [4][nnn]
+  unsigned long long *bar = reinterpret_cast<unsigned long long *>(sm_tma + 2 * LT_BUF + 4 * nnn * 4);
+  __shared__ float sD[n][n + 1];
+  __shared__ int s_ok;
+  const int tid = threadIdx.x;
+  for (int t = tid; t < nn; t += blockDim.x) sD[t / n][t % n] = f_D[t];
+  if (tid == 0) {
+    mbar_init(smem_addr(&bar[0]));
+    mbar_init(smem_addr(&bar[1]));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int k) {
+    const long long e = (long long)blockIdx.x + (long long)k * gridDim.x;
+    if (e >= d.nE) return;
+    unsigned char *b = sm_tma + (k & 1) * LT_BUF;
+    const unsigned mb = smem_addr(&bar[k & 1]);
+    mbar_expect_tx(mb, LT_BUF);
+    bulk_g2s(smem_addr(b), d.Uf + e * 5 * nnn, TB_UF, mb);
+    bulk_g2s(smem_addr(b + TB_UF), d.Jaf + e * 9 * nnn, TB_JA, mb);
+    bulk_g2s(smem_addr(b + TB_UF + TB_JA), d.invJf + e * nnn, LT_IJ, mb);
+    bulk_g2s(smem_addr(b + TB_UF + TB_JA + LT_IJ), d.Wsurf_f + e * 24 * nn, LT_WS, mb);
+  };
+  if (tid == 0) {
+    issue(0);
+    issue(1);
+  }
+  const float gm1 = d.gm1_f, iR = d.iR_f, pref = d.p_ref_f, mu = d.mu_f, kappa = d.kappa_f;
+  for (int k = 0;; ++k) {
+    const long long e = (long long)blockIdx.x + (long long)k * gridDim.x;
+    if (e >= d.nE) break;
+    const unsigned mb = smem_addr(&bar[k & 1]), parity = (unsigned)((k >> 1) & 1);
+    if (tid == 0) s_ok = mbar_wait(mb, parity) ? 1 : 0;
+    __syncthreads();
+    if (!s_ok) {  // a copy never completed: report, wait (bounded) for the other buffer's copy, stop
+      if (tid == 0) {
+        flag_set(d.flag, 4);
+        if (e + gridDim.x < d.nE) mbar_wait(smem_addr(&bar[(k + 1) & 1]), (unsigned)(((k + 1) >> 1) & 1));
+      }
+      return;
+    }
+    mbar_wait(mb, parity);  // completed: returns at once and orders this thread's reads after the copy
+    const unsigned char *b = sm_tma + (k & 1) * LT_BUF;
+    const float *Uf = reinterpret_cast<const float *>(b);
+    const float *Jb = reinterpret_cast<const float *>(b + TB_UF);
+    const float *Ib = reinterpret_cast<const float *>(b + TB_UF + TB_JA);
+    const float *Sb = reinterpret_cast<const float *>(b + TB_UF + TB_JA + LT_IJ);
+    if (tid < nnn) {
+      const float Uv[5] = {Uf[tid], Uf[nnn + tid], Uf[2 * nnn + tid], Uf[3 * nnn + tid], Uf[4 * nnn + tid]};
+      float Wn[4];
+      lift_prim<float>(Uv, gm1, iR, pref, Wn);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) W[q * nnn + tid] = Wn[q];
+    }
+    __syncthreads();
+    if (tid < nnn) lift_node<float>(d, tid, W, sD, Jb, Sb, Ib[tid], mu, kappa, d.Fv_f + (size_t)e * 12 * nnn);
+    __syncthreads();  // buffer k & 1 and W are free again
+    if (tid == 0) issue(k + 2);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // modified Persson indicator (Sec. 4.1, Eq. (7)) and the neighbour extension (FP64)
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_indicator(const DgDevice d, const double *__restrict__ U) {
@@ -2122,6 +2215,20 @@ void launch_face(const DgDevice &d, const double *U, cudaStream_t s) {
 }
 
 void launch_lift(const DgDevice &d, const double *U, cudaStream_t s) {
+  if (TMA_OK && d.precision == 1 && d.use_tma) {  // FP32-bulk: the TMA-fed persistent form
+    static int grid_lt = 0;
+    if (!grid_lt) {
+      cudaFuncSetAttribute(k_lift_f32_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LT_SMEM);
+      int dev = 0, sms = 0, per_sm = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lift_f32_tma, LT_THREADS, LT_SMEM);
+      grid_lt = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const int blocks = d.nE < grid_lt ? d.nE : grid_lt;
+    k_lift_f32_tma<<<blocks, LT_THREADS, LT_SMEM, s>>>(d);
+    return;
+  }
   const unsigned grid = (d.nE + LIFT_EPB - 1) / LIFT_EPB;
   if (d.precision == 1) k_lift<float><<<grid, LIFT_THREADS, 0, s>>>(d, U);
   else k_lift<double><<<grid, LIFT_THREADS, 0, s>>>(d, U);
