@@ -310,6 +310,10 @@ __global__ void __launch_bounds__(LIFT_THREADS) k_adj_visc(const DgDevice d, con
   double *Ls = Ws + LIFT_EPB * 4 * nnn;              // [EPB][4][nnn]
   double *Hs = Ls + LIFT_EPB * 4 * nnn;              // [EPB][12][nnn]
   double *Os = Hs + LIFT_EPB * 12 * nnn;             // [EPB][3][nnn]
+  // D in shared memory, rows padded: the sweeps index it by the thread's own node, which would
+  // serialise a constant-memory load
+  __shared__ double sD[n][n + 1];
+  for (int t = threadIdx.x; t < nn; t += blockDim.x) sD[t / n][t % n] = c_D[t];
   const int e0 = blockIdx.x * LIFT_EPB;
   const double gm1 = d.gamma - 1.0, iR = 1.0 / d.R, mu = d.mu, kappa = d.kappa;
   for (int t = threadIdx.x; t < LIFT_EPB * nnn; t += blockDim.x) {
@@ -357,8 +361,8 @@ __global__ void __launch_bounds__(LIFT_THREADS) k_adj_visc(const DgDevice d, con
         double s = 0.0, z = 0.0;
 #pragma unroll
         for (int m = 0; m < n; ++m) {
-          s += c_D[id * n + m] * W[q * nnn + base + m * st];
-          if (m != id) z -= c_D[m * n + id] * L[q * nnn + base + m * st];
+          s += sD[id][m] * W[q * nnn + base + m * st];
+          if (m != id) z -= sD[m][id] * L[q * nnn + base + m * st];
         }
         g[q][0] += Ja[dd][0] * s;
         g[q][1] += Ja[dd][1] * s;
@@ -444,7 +448,7 @@ __global__ void __launch_bounds__(LIFT_THREADS) k_adj_visc(const DgDevice d, con
       for (int q = 0; q < 4; ++q) {
         double s = 0.0;
 #pragma unroll
-        for (int m = 0; m < n; ++m) s += c_D[m * n + id] * H[(dd * 4 + q) * nnn + base + m * st];
+        for (int m = 0; m < n; ++m) s += sD[m][id] * H[(dd * 4 + q) * nnn + base + m * st];
         cw[q] += s;
       }
       if (id == 0 || id == N) {
