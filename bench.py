@@ -40,6 +40,10 @@ P0_TGV = 1.0 / (1.4 * 0.1 ** 2)  # background pressure of the Ma 0.1 Taylor-Gree
 # scaled to a launch by the element count (the kernel's traffic is per element). None once the kernel
 # has changed since that capture.
 VOLUME_DRAM_BYTES_PER_ELEMENT = 661.0e6 / 16 ** 3
+# DRAM bytes (read + write) of one FP32-bulk volume launch (pair-symmetric line kernel) per element,
+# from one ncu capture of the 16^3 case (profiles/k_volume_f32_line_tgv_ns_n7_16x16x16.md), scaled
+# by the element count: 351.5 + 157.2 MB for 4096 elements
+VOLUME_F32_DRAM_BYTES_PER_ELEMENT = (351.5e6 + 157.2e6) / 16 ** 3
 
 
 def volume_kernel_flops_per_element(N: int, navier_stokes: bool) -> float:
@@ -598,6 +602,7 @@ def run_gpu(args):
             gbs = b32 / (v32_ms / v32_n * 1e-3) / 1e9
             fp32["roofline"] = {"bound": "hbm", "kernel": "volume (FP32-bulk)", "achieved": gbs, "peak": HBM_GBS,
                                 "unit": "GB/s", "frac": gbs / HBM_GBS, "bytes_per_launch": b32,
+                                "traffic": VOLUME_F32_DRAM_BYTES_PER_ELEMENT * w.n_elems if w.N == 7 else None,
                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
         del s32
 
@@ -610,7 +615,8 @@ def run_gpu(args):
         bytes_launch = volume_kernel_bytes_per_element(w.N, True, 4) * w.n_elems
         roofline = {"bound": "hbm", "kernel": "volume (FP32-bulk)", "achieved": bytes_launch / vol_s / 1e9,
                     "peak": HBM_GBS, "unit": "GB/s", "frac": bytes_launch / vol_s / 1e9 / HBM_GBS,
-                    "traffic": None, "bytes_per_launch": bytes_launch,
+                    "traffic": VOLUME_F32_DRAM_BYTES_PER_ELEMENT * w.n_elems if w.N == 7 else None,
+                    "bytes_per_launch": bytes_launch,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
     else:
         flops_launch = volume_kernel_flops_per_element(w.N, True) * w.n_elems
