@@ -36,13 +36,13 @@ UNIT = "DOF-stage/s"
 STAGES = 5
 P0_TGV = 1.0 / (1.4 * 0.1 ** 2)  # background pressure of the Ma 0.1 Taylor-Green vortex
 # DRAM bytes per element of one volume-kernel launch (dram__bytes_read.sum + dram__bytes_write.sum),
-# from an ncu capture of the current kernel on the 16^3 case (profiles/launch_list_tgv_ns_n7_32x32x32.md),
-# scaled to a launch by the element count (the kernel's traffic is per element). None once the kernel
-# has changed since that capture.
+# from an ncu capture of the current kernel on the 16^3 case (a first LSERK stage: 517.87 MB read,
+# 143.12 MB written), scaled to a launch by the element count (the kernel's traffic is per element).
+# None once the kernel has changed since that capture.
 VOLUME_DRAM_BYTES_PER_ELEMENT = 661.0e6 / 16 ** 3
 # DRAM bytes (read + write) of one FP32-bulk volume launch (pair-symmetric line kernel) per element,
-# from one ncu capture of the 16^3 case (profiles/k_volume_f32_line_tgv_ns_n7_16x16x16.md), scaled
-# by the element count: 351.5 + 157.2 MB for 4096 elements
+# from one ncu capture of the 16^3 case (351.5 MB read, 157.2 MB written for 4096 elements), scaled
+# by the element count
 VOLUME_F32_DRAM_BYTES_PER_ELEMENT = (351.5e6 + 157.2e6) / 16 ** 3
 
 
