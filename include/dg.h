@@ -217,8 +217,9 @@ dg_status dg_get_metrics(dg_ctx *ctx, double *Ja, double *J);
  * two-point flux once for both of its nodes (pair symmetry) while separate warps apply the FP64
  * epilogue to the previous element; inputs arrive by TMA bulk copies one element ahead.
  * 2: the same pipeline with one thread per node; 1: mode 2 without warp specialisation; 0: the
- * plain node-per-thread kernel. Modes 0-2 give identical bits; mode 3 sums in another order, so it
- * agrees with them to FP32 rounding. DG_ERR_ARG for other values. */
+ * plain node-per-thread kernel. Modes 1-3 also run the FP32 lifting as a TMA-fed persistent kernel
+ * (same arithmetic, same bits as mode 0's). Modes 0-2 give identical bits; mode 3 sums in another
+ * order, so it agrees with them to FP32 rounding. No effect in FP64. DG_ERR_ARG for other values. */
 dg_status dg_use_tma(dg_ctx *ctx, int mode);
 
 /* 1 (default): multi-step calls replay a CUDA graph of one step; 0: every kernel is launched. Both
