@@ -515,6 +515,7 @@ def run_gpu(args):
     p_ref = P0_TGV if w.initial == "tgv" else 0.0
     prec = dict(precision="fp32_bulk", p_ref=p_ref) if fp32_main else {}
     solver = dg.DG(w.N, xyz, faces, stream=stream, **prec, **w.physics())
+    solver.use_tma(args.tma_mode)
     U = torch.from_numpy(U0).cuda()
     dt = solver.max_dt(U, w.cfl)
     peak_fp64 = dg.probe_fma("fp64", stream)
@@ -569,6 +570,7 @@ def run_gpu(args):
         n_done = args.warmup + args.steps
         del solver
         s32 = dg.DG(w.N, xyz, faces, stream=stream, precision="fp32_bulk", p_ref=p_ref, **w.physics())
+        s32.use_tma(args.tma_mode)
         V = torch.from_numpy(U0).cuda()
         s32.lserk_steps(V, dt, args.warmup)
         torch.cuda.synchronize()
@@ -640,6 +642,7 @@ def run_gpu(args):
                    "N": w.N, "elements": w.n_elems, "dofs": dofs,
                    "physics": "Navier-Stokes, Pirozzoli split form, Roe, BR1, curved mesh, TGV Re 1600 Ma 0.1",
                    "precision": args.precision, "dt": dt, "cfl": w.cfl,
+                   **({"fp32_kernel_form": args.tma_mode} if fp32_main else {}),
                    "l2": f"inputs larger than L2 (state {state_bytes / 1e6:.0f} MB, working set > 5 GB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "pid_s_per_dof_stage": 1.0 / (value / world),
@@ -678,6 +681,9 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk"])
     ap.add_argument("--nel", type=int, default=None, help="elements per direction (default: the workload's 32)")
+    ap.add_argument("--tma-mode", type=int, default=3, choices=[0, 1, 2, 3],
+                    help="FP32-bulk kernel form (dg_use_tma): 3 pair-symmetric line kernel (default), "
+                         "2 warp-specialised node kernel, 1 TMA node kernel, 0 plain kernels")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
