@@ -188,3 +188,18 @@ def test_rhs_invariant_under_element_rotation(oracle_mod, eq, sc):
     bad[i, 4] = 0
     R3 = oracle_mod.Oracle(N, xr, bad, **kw).rhs(field(xr))
     assert np.abs(R3 - R2).max() > 1e-3 * np.abs(R1).max()
+
+
+def test_paper_freestream_workload_is_a_steady_state(oracle_mod):
+    """The paper's performance case (N = 7, periodic Cartesian box, Navier-Stokes, Pirozzoli + Roe +
+    BR1, free stream), reduced to 2^3 elements: a uniform flow is an exact steady state of the
+    discretisation, so the right-hand side vanishes to rounding (relative to the flux scale)."""
+    w = W.WORKLOADS["freestream_ns_n7_32x32x32"].with_(nel=(2, 2, 2))
+    xyz, faces = w.mesh()
+    U = w.initial_state(xyz)
+    assert np.ptp(U[:, 0]) == 0.0 and np.ptp(U[:, 4]) == 0.0  # uniform density and energy
+    o = oracle_mod.Oracle(w.N, xyz, faces, **w.physics())
+    Ut = o.rhs(U)
+    scale = flux_scale(U, o.Ja, o.J, oracle_mod.dmatrix(w.N))
+    err = np.abs(Ut).reshape(Ut.shape[0], 5, -1).max(axis=(0, 2))
+    assert (err <= 1e-13 * scale.max()).all(), (err, scale)
