@@ -198,6 +198,12 @@ dg_status dg_lserk_steps_record(dg_ctx *ctx, double *U, double dt, double t, int
  * has been recorded over. */
 dg_status dg_lserk_steps_vjp_recorded(dg_ctx *ctx, long long tape, double *Ubar);
 
+/* *tape = the id of the recording that dg_lserk_steps_vjp_recorded accepts now, or 0 when there is
+ * none (never recorded, or a recording that failed part way). Host-only query; no GPU work. A caller
+ * that may have recorded over its tape checks this before the reverse sweep instead of treating an
+ * error of the sweep as a stale tape. */
+dg_status dg_tape_current(const dg_ctx *ctx, long long *tape);
+
 /* grad = d/dU of the kinetic-energy integral sum J w rho|u|^2/2 (out[6] of dg_invariants). */
 dg_status dg_kinetic_energy_grad(dg_ctx *ctx, const double *U, double *grad);
 

@@ -44,9 +44,11 @@ class _Steps(torch.autograd.Function):
         (U0,) = ctx.saved_tensors
         Ubar = grad_out.detach().contiguous().clone()
         if ctx.n_steps > 0:
-            try:
+            # a later forward may have recorded over this run's tape: then recompute from U0. Any
+            # error of the reverse sweep itself propagates (Ubar is partly reversed by then).
+            if ctx.dg.tape_current() == ctx.tape:
                 ctx.dg.lserk_steps_vjp_recorded(ctx.tape, Ubar)
-            except Exception:  # the tape was recorded over by a later forward: recompute from U0
+            else:
                 ctx.dg.lserk_steps_vjp(U0, Ubar, ctx.dt, ctx.n_steps, ctx.interval)
         return Ubar, None, None, None, None
 

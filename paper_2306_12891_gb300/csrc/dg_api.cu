@@ -711,6 +711,12 @@ dg_status dg_lserk_steps_vjp_recorded(dg_ctx *c, long long tape, double *Ubar) {
   return reverse_from_checkpoints(c, cps, c->tape_interval, n_steps, Ubar, dt, 5);
 }
 
+dg_status dg_tape_current(const dg_ctx *c, long long *tape) {
+  if (!c || !tape) return DG_ERR_ARG;
+  *tape = c->tape_id;
+  return DG_OK;
+}
+
 dg_status dg_adjoint_memory_limit(dg_ctx *c, double bytes) {
   if (!c || !(bytes >= 0.0)) return fail(c, DG_ERR_ARG, "dg_adjoint_memory_limit: bad argument");
   c->adj_limit = (size_t)bytes;

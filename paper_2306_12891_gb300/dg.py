@@ -94,6 +94,7 @@ def lib() -> ctypes.CDLL:
             "dg_use_graphs": (i, [vp, i]),
             "dg_lserk_steps_record": (i, [vp, vp, d, d, i, i, ctypes.POINTER(ctypes.c_longlong)]),
             "dg_lserk_steps_vjp_recorded": (i, [vp, ctypes.c_longlong, vp]),
+            "dg_tape_current": (i, [vp, ctypes.POINTER(ctypes.c_longlong)]),
             "dg_use_tma": (i, [vp, i]),
         }
         for name, (res, args) in sig.items():
@@ -281,6 +282,12 @@ class DG:
         self._check(lib().dg_lserk_steps_vjp_recorded(self._ctx, int(tape), self._state(Ubar, "Ubar")),
                     "dg_lserk_steps_vjp_recorded")
         return Ubar
+
+    def tape_current(self) -> int:
+        """Id of the recording that lserk_steps_vjp_recorded accepts now (0: none)."""
+        tape = ctypes.c_longlong(0)
+        self._check(lib().dg_tape_current(self._ctx, ctypes.byref(tape)), "dg_tape_current")
+        return tape.value
 
     def kinetic_energy_grad(self, U, grad=None):
         if grad is None:

@@ -224,7 +224,9 @@ def test_recorded_run_reverses_to_the_same_bits(env):
         assert torch.equal(Ub, want)
     gpu.adjoint_memory_limit(0.0)
     t1 = gpu.lserk_steps_record(U0.clone(), dt, 2, 2)
-    gpu.lserk_steps_record(U0.clone(), dt, 2, 2)
+    assert gpu.tape_current() == t1
+    t2 = gpu.lserk_steps_record(U0.clone(), dt, 2, 2)
+    assert gpu.tape_current() == t2 != t1
     with pytest.raises(dg.DGError) as ei:
         gpu.lserk_steps_vjp_recorded(t1, seed.clone())
     assert ei.value.status == -1
@@ -408,6 +410,14 @@ def test_autograd_functions(env):
     assert torch.equal(X.grad, g)
     UK = gpu.lserk_steps(U0.clone(), dt, 5)
     assert abs(ke.item() - gpu.invariants(UK, UK)[6]) == 0.0
+    # two recorded forwards before either backward: the first one's tape is gone, so its backward
+    # recomputes from U0 (the same bits); the second reverses its own tape
+    X1, X2 = U0.clone().requires_grad_(True), U0.clone().requires_grad_(True)
+    ke1 = AG.kinetic_energy(gpu, AG.lserk_steps(gpu, X1, dt, 5, 2))
+    ke2 = AG.kinetic_energy(gpu, AG.lserk_steps(gpu, X2, dt, 5, 2))
+    ke1.backward()
+    ke2.backward()
+    assert torch.equal(X1.grad, g) and torch.equal(X2.grad, g)
 
 
 def test_kinetic_energy_gradient_closed_form(env):
