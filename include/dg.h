@@ -128,9 +128,10 @@ dg_status dg_indicator(dg_ctx *ctx, const double *U, double *alpha);
 dg_status dg_invariants(dg_ctx *ctx, const double *U, const double *Ut, double out[8]);
 
 /* The same eight integrals as dg_invariants, for callers that cannot allocate device memory where
- * they need them: a stream being captured into a CUDA graph (cudaMalloc is not allowed during
- * capture), a host callback, or a host framework whose memory pool holds nearly all of the device
- * memory. (The paper has no counterpart; this is a service of the library.)
+ * they need them: a host framework whose caching allocator already holds nearly all of the device
+ * memory (a cudaMalloc there fails, or forces the pool to give memory back), or real-time and
+ * embedded callers whose rules forbid any allocation after start-up. (The paper has no
+ * counterpart; this is a service of the library.)
  *  - Needs no context and allocates nothing: every input and output belongs to the caller.
  *    U, Ut: device [n_elems][5][N+1]^3; J: device Jacobian [n_elems][N+1]^3 (e.g. from
  *    dg_get_metrics); out8: device double[8], written asynchronously on `cuda_stream`

@@ -10,6 +10,9 @@ runs every state-dependent statement in complex arithmetic: ``jvp`` and ``lserk_
 Im L(U + i h V) / h, the exact directional derivative of the oracle's own arithmetic (complex
 step; no subtractive cancellation), which is the reference for the discrete adjoint.
 
+A third build, compiled with FMA contraction (``Oracle(..., contracted=True)``), is a second
+correct FP64 evaluation with other rounding; the tests use it only to calibrate their parity bound.
+
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
 may import this package. The CUDA path never does, and this package never imports the
 CUDA path: the two share no code.
@@ -18,6 +21,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 
 import numpy as np
@@ -27,6 +31,7 @@ SRC = os.path.join(HERE, "dgsem_oracle.c")
 HDR = os.path.join(HERE, "dgsem_oracle.h")
 LIB_PATH = os.path.join(HERE, "_build", "liboracle.so")
 LIB_CS_PATH = os.path.join(HERE, "_build", "liboracle_cs.so")
+LIB_FMA_PATH = os.path.join(HERE, "_build", "liboracle_fma.so")
 CS_STEP = 1e-30  # complex-step size: h^2 is far below one ulp of any value the oracle forms
 
 EQUATIONS = {"euler": 0, "ns": 1, "navier_stokes": 1}
@@ -67,10 +72,28 @@ _DP = ctypes.POINTER(ctypes.c_double)
 RHS_FN = ctypes.CFUNCTYPE(None, _DP, _DP, ctypes.c_double, ctypes.c_void_p)
 
 
-def lib(complex_step: bool = False):
-    if complex_step not in _libs:
+def build_contracted(force: bool = False) -> str:
+    """The same source compiled with FMA contraction (-ffp-contract=fast, -O3): a second correct FP64
+    evaluation with other rounding, used only to calibrate the parity bound of the tests. Built on
+    request, never by build()."""
+    os.makedirs(os.path.dirname(LIB_FMA_PATH), exist_ok=True)
+    newest = max(os.path.getmtime(SRC), os.path.getmtime(HDR))
+    if force or not os.path.exists(LIB_FMA_PATH) or os.path.getmtime(LIB_FMA_PATH) < newest:
+        tmp = LIB_FMA_PATH + f".tmp{os.getpid()}"
+        isa = ["-mfma"] if platform.machine() in ("x86_64", "AMD64") else []  # FMA is baseline on aarch64
+        subprocess.check_call(["gcc", "-O3", "-std=c11", "-fPIC", "-shared", "-ffp-contract=fast", *isa,
+                               "-fno-fast-math", "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, LIB_FMA_PATH)
+    return LIB_FMA_PATH
+
+
+def lib(complex_step: bool = False, contracted: bool = False):
+    key = "fma" if contracted else complex_step
+    if key not in _libs:
         build()
-        L = ctypes.CDLL(LIB_CS_PATH if complex_step else LIB_PATH)
+        if contracted:
+            build_contracted()
+        L = ctypes.CDLL(LIB_FMA_PATH if contracted else (LIB_CS_PATH if complex_step else LIB_PATH))
         vp = ctypes.c_void_p
         L.orc_create.restype = vp
         L.orc_create.argtypes = [ctypes.POINTER(_Problem), ctypes.POINTER(ctypes.c_int)]
@@ -106,8 +129,8 @@ def lib(complex_step: bool = False):
             L.orc_van_driest.argtypes = [ctypes.c_double] * 5
             L.orc_wall_utau.restype = ctypes.c_double
             L.orc_wall_utau.argtypes = [ctypes.c_double] * 7 + [ctypes.c_int]
-        _libs[complex_step] = L
-    return _libs[complex_step]
+        _libs[key] = L
+    return _libs[key]
 
 
 def _p(a: np.ndarray):
@@ -233,9 +256,9 @@ class Oracle:
     def __init__(self, N, xyz, faces, equations="euler", vflux="kg", sflux="llf", gamma=1.4, R=1.0,
                  mu=0.0, Pr=0.72, shock_capturing=False, alpha_min=0.01, alpha_max=0.7,
                  sharpness=DEFAULT_SHARPNESS, alpha_fixed=-1.0, wm_index=1, wm_uinf=1.0, wm_mainf=0.0,
-                 wm_van_driest=False, complex_step=False):
+                 wm_van_driest=False, complex_step=False, contracted=False):
         self.cs = bool(complex_step)
-        self._L = lib(self.cs)
+        self._L = lib(self.cs, contracted=bool(contracted) and not self.cs)
         self._dtype = np.complex128 if self.cs else np.float64
         self.N = int(N)
         self.n = self.N + 1

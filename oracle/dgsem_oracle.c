@@ -736,6 +736,18 @@ static orc_real minmod(orc_real a, orc_real b) {
   return (fabs(RE(a)) < fabs(RE(b))) ? a : b;
 }
 
+/* Test hook, 0 in every use but one: the reconstruction pins set it to plant a deliberate mistake
+ * and check that they then fail. 1: no slopes anywhere (first order everywhere); 2: one-sided slopes
+ * in the outer subcells too; 3: states evaluated at the midpoints between nodes instead of at the
+ * subcell interfaces; 4: the larger slope where minmod takes the smaller (maxmod); 5: interface
+ * metrics averaged from the two neighbouring nodes instead of telescoped from Ja_0. */
+int orc_fv_plant = 0;
+
+static orc_real maxmod(orc_real a, orc_real b) {
+  if (RE(a) * RE(b) <= 0.0) return 0.0;
+  return (fabs(RE(a)) < fabs(RE(b))) ? b : a;
+}
+
 static void cons_from_prim(const orc_real q[5], double gamma, orc_real U[5]) {
   U[0] = q[0];
   U[1] = q[0] * q[1]; U[2] = q[0] * q[2]; U[3] = q[0] * q[3];
@@ -749,6 +761,9 @@ static void fv_element(const orc_state *s, const orc_real *U, int e, orc_real *a
   double xh[NMAX + 2]; /* subcell interfaces xi_{i+1/2}, i = -1..N */
   xh[0] = -1.0;
   for (int i = 0; i <= N; ++i) xh[i + 1] = xh[i] + s->w[i];
+  double xr[NMAX + 2]; /* where the reconstructed states are evaluated: the interfaces */
+  for (int i = 0; i <= n; ++i)
+    xr[i] = (orc_fv_plant == 3 && i > 0 && i < n) ? 0.5 * (s->xi[i - 1] + s->xi[i]) : xh[i];
   for (size_t i = 0; i < (size_t)NVAR * nnn; ++i) accFV[i] = 0.0;
   for (int d = 0; d < 3; ++d) {
     int fm = 2 * d, fp = 2 * d + 1;
@@ -774,14 +789,19 @@ static void fv_element(const orc_state *s, const orc_real *U, int e, orc_real *a
         orc_real qL[NMAX + 1][5], qR[NMAX + 1][5];
         for (int i = 0; i < n; ++i) {
           orc_real sig[5] = {0, 0, 0, 0, 0};
-          if (i > 0 && i < N) {
-            for (int v = 0; v < 5; ++v)
-              sig[v] = minmod((q[i][v] - q[i - 1][v]) / (s->xi[i] - s->xi[i - 1]),
-                              (q[i + 1][v] - q[i][v]) / (s->xi[i + 1] - s->xi[i]));
+          if (i > 0 && i < N && orc_fv_plant != 1) {
+            for (int v = 0; v < 5; ++v) {
+              orc_real a = (q[i][v] - q[i - 1][v]) / (s->xi[i] - s->xi[i - 1]);
+              orc_real b = (q[i + 1][v] - q[i][v]) / (s->xi[i + 1] - s->xi[i]);
+              sig[v] = orc_fv_plant == 4 ? maxmod(a, b) : minmod(a, b);
+            }
+          } else if (orc_fv_plant == 2) {
+            int i0 = i == 0 ? 0 : N - 1;
+            for (int v = 0; v < 5; ++v) sig[v] = (q[i0 + 1][v] - q[i0][v]) / (s->xi[i0 + 1] - s->xi[i0]);
           }
           for (int v = 0; v < 5; ++v) {
-            qL[i][v] = q[i][v] + sig[v] * (xh[i] - s->xi[i]);
-            qR[i][v] = q[i][v] + sig[v] * (xh[i + 1] - s->xi[i]);
+            qL[i][v] = q[i][v] + sig[v] * (xr[i] - s->xi[i]);
+            qR[i][v] = q[i][v] + sig[v] * (xr[i + 1] - s->xi[i]);
           }
           if (RE(qL[i][0]) <= 0.0 || RE(qL[i][4]) <= 0.0 || RE(qR[i][0]) <= 0.0 || RE(qR[i][4]) <= 0.0)
             for (int v = 0; v < 5; ++v) { qL[i][v] = q[i][v]; qR[i][v] = q[i][v]; }
@@ -795,6 +815,7 @@ static void fv_element(const orc_state *s, const orc_real *U, int e, orc_real *a
             double dj = 0.0;
             for (int m = 0; m < n; ++m) dj += s->D[i * n + m] * Jl[m][c];
             ah[i + 1][c] = ah[i][c] + s->w[i] * dj;
+            if (orc_fv_plant == 5 && i < N) ah[i + 1][c] = 0.5 * (Jl[i][c] + Jl[i + 1][c]);
           }
         /* fluxes at the N+2 subcell interfaces, in +xi_d direction */
         orc_real fh[NMAX + 2][5];

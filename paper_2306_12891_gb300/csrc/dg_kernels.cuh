@@ -32,6 +32,7 @@
 
 #include "dg_convert.cuh"
 #include "dg_internal.h"
+#include "dg_invariants_node.cuh"
 #include "dg_wall.cuh"
 
 #ifndef DG_N
@@ -1137,18 +1138,7 @@ __global__ void __launch_bounds__(256) k_invariants(const DgDevice d, const doub
     double Uv[5], Tv[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) { Uv[v] = U[b + v * nnn]; Tv[v] = Ut[b + v * nnn]; }
-    const double r = Uv[0], ir = 1.0 / r;
-    const double u = Uv[1] * ir, v = Uv[2] * ir, w = Uv[3] * ir;
-    const double q2 = u * u + v * v + w * w;
-    const double p = (gam - 1.0) * (Uv[4] - 0.5 * r * q2);
-    const double s = log(p) - gam * log(r);
-    const double ip = 1.0 / p;
-    const double ev[5] = {(gam - s) / (gam - 1.0) - 0.5 * r * q2 * ip, r * u * ip, r * v * ip, r * w * ip, -r * ip};
-#pragma unroll
-    for (int m = 0; m < 5; ++m) acc[m] += wq * Tv[m];
-    acc[5] += wq * (ev[0] * Tv[0] + ev[1] * Tv[1] + ev[2] * Tv[2] + ev[3] * Tv[3] + ev[4] * Tv[4]);
-    acc[6] += wq * 0.5 * r * q2;
-    acc[7] += wq * (u * Tv[1] + v * Tv[2] + w * Tv[3] - 0.5 * q2 * Tv[0]);
+    invariants_node(gam, wq, Uv, Tv, acc);
   }
 #pragma unroll
   for (int m = 0; m < 8; ++m) red[m][threadIdx.x] = acc[m];

@@ -1,9 +1,9 @@
 // dg_noalloc.cu -- integral diagnostics without any memory allocation (dg_invariants_noalloc).
 //
-// Some callers cannot allocate device memory at the point where they want the diagnostics: a
-// stream that is being captured into a CUDA graph (cudaMalloc is not allowed during capture), a
-// host callback, or a host framework whose memory pool already holds nearly all of the device
-// memory. This variant of the invariants reduction therefore keeps its per-chunk partial sums in
+// Some callers cannot allocate device memory at the point where they want the diagnostics: a host
+// framework whose caching allocator already holds nearly all of the device memory (a cudaMalloc
+// there fails, or forces the pool to give memory back), or real-time and embedded callers whose
+// rules forbid any allocation after start-up. This variant of the invariants reduction therefore keeps its per-chunk partial sums in
 // a fixed, file-scope device array instead of context memory, and takes every input and output
 // from the caller.
 //
@@ -19,6 +19,7 @@
 
 #include "../../include/dg.h"
 #include "dg_internal.h"
+#include "dg_invariants_node.cuh"
 
 #define DG_NOALLOC_CHUNK 16384LL   // nodes per chunk (one CTA)
 #define DG_NOALLOC_MAX_CHUNKS 2048  // rows of the scratch array
@@ -60,18 +61,7 @@ __global__ void __launch_bounds__(kThreads) k_invariants_chunks(int n, long long
     double Uv[5], Tv[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) { Uv[v] = U[b + (size_t)v * nnn]; Tv[v] = Ut[b + (size_t)v * nnn]; }
-    const double r = Uv[0], ir = 1.0 / r;
-    const double u = Uv[1] * ir, v = Uv[2] * ir, w = Uv[3] * ir;
-    const double q2 = u * u + v * v + w * w;
-    const double p = (gam - 1.0) * (Uv[4] - 0.5 * r * q2);
-    const double s = log(p) - gam * log(r);
-    const double ip = 1.0 / p;
-    const double ev[5] = {(gam - s) / (gam - 1.0) - 0.5 * r * q2 * ip, r * u * ip, r * v * ip, r * w * ip, -r * ip};
-#pragma unroll
-    for (int m = 0; m < 5; ++m) acc[m] += wq * Tv[m];
-    acc[5] += wq * (ev[0] * Tv[0] + ev[1] * Tv[1] + ev[2] * Tv[2] + ev[3] * Tv[3] + ev[4] * Tv[4]);
-    acc[6] += wq * 0.5 * r * q2;
-    acc[7] += wq * (u * Tv[1] + v * Tv[2] + w * Tv[3] - 0.5 * q2 * Tv[0]);
+    invariants_node(gam, wq, Uv, Tv, acc);
   }
 #pragma unroll
   for (int m = 0; m < 8; ++m) red[m][threadIdx.x] = acc[m];
@@ -102,6 +92,8 @@ extern "C" dg_status dg_invariants_noalloc(int N, int n_elems, double gamma, con
   const long long n = N + 1;
   const long long total = (long long)n_elems * n * n * n;
   if (total > kChunk * kMaxChunks) return DG_ERR_UNSUPPORTED;  // beyond the fixed scratch array
+  // an error left pending by earlier, unrelated work is its owner's to read: refuse without clearing it
+  if (cudaPeekAtLastError() != cudaSuccess) return DG_ERR_CUDA;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return DG_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return DG_ERR_UNSUPPORTED;
@@ -125,7 +117,9 @@ extern "C" dg_status dg_invariants_noalloc(int N, int n_elems, double gamma, con
   for (int i = 0; i <= DG_NMAX; ++i) wts.w[i] = i <= N ? t.w[i] : 0.0;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const int rows = (int)((total + kChunk - 1) / kChunk);
+  // no error was pending above, so an error read here is one of these launches
   k_invariants_chunks<<<rows, kThreads, 0, st>>>((int)n, total, gamma, wts, U, Ut, J, scratch);
+  if (cudaGetLastError() != cudaSuccess) return DG_ERR_CUDA;
   k_invariants_rows<<<1, 32, 0, st>>>(scratch, rows, out8);
   if (cudaGetLastError() != cudaSuccess) return DG_ERR_CUDA;
   return DG_OK;

@@ -11,13 +11,19 @@ must agree to TOL32 = 64 * 2^-24 (~3.8e-6) -- FP32 rounding of the O(3(N+1)) flu
 import numpy as np
 import pytest
 
-from helpers import flux_scale, normwise, parity
+from helpers import flux_scale as _flux_scale, normwise, parity
 from paper_2306_12891_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 EPS32 = 2.0 ** -24
 TOL32 = 64 * EPS32
 P0_TGV = 1.0 / (1.4 * 0.1 ** 2)  # Taylor-Green background pressure at Ma 0.1
+
+
+def flux_scale(U, Ja, J, D):
+    """The flux scale with the FP32 state-rounding term c |Ja| |U| of the Riemann dissipation: in this
+    form the dissipation differences states rounded to FP32 (tests/helpers.py)."""
+    return _flux_scale(U, Ja, J, D, state_dissipation=True)
 
 
 @pytest.fixture(scope="module")

@@ -203,3 +203,74 @@ def test_paper_freestream_workload_is_a_steady_state(oracle_mod):
     scale = flux_scale(U, o.Ja, o.J, oracle_mod.dmatrix(w.N))
     err = np.abs(Ut).reshape(Ut.shape[0], 5, -1).max(axis=(0, 2))
     assert (err <= 1e-13 * scale.max()).all(), (err, scale)
+
+
+# ------------------------------------------------------------------ split forms as product-rule derivatives
+#
+# Flux differencing with a two-point flux that is a product of arithmetic means equals a product-rule
+# split of the derivative (Fisher & Carpenter 2013; Gassner, Winters & Kopriva 2016, for SBP
+# operators with D 1 = 0):
+#   sum_m 2 D_im {a}{b}     = (a D b + b D a + D(ab))_i / 2
+#   sum_m 2 D_im {a}{b}{c}  = (ab Dc + ac Db + bc Da + a D(bc) + b D(ac) + c D(ab) + D(abc))_i / 4
+#   sum_m 2 D_im {p}        = (D p)_i
+# So on a Cartesian mesh, for a continuous state (no surface terms), the Euler right-hand side of each
+# volume flux is a known combination of plain D-derivatives of products: Pirozzoli's energy flux
+# {rho}{u}{h} is the cubic split of rho u h, Kennedy-Gruber's {rho}{u}{e} + {p}{u} the cubic split of
+# rho u e plus the quadratic split of p u, the central flux the plain derivative of F. An energy
+# average formed another way ({rho h} for {rho}{h}, say) changes the result, and KG's and
+# Pirozzoli's expectations tell the two apart, so each pins the other's energy flux too.
+
+def _split_rhs(kind, U, D, h, gamma=1.4):
+    """-sum_d (2/h_d) split_d for a Cartesian element of sides h; U [nE][5][k][j][i]."""
+    rho = U[:, 0]
+    u = [U[:, 1 + c] / rho for c in range(3)]
+    p = (gamma - 1.0) * (U[:, 4] - 0.5 * rho * (u[0] ** 2 + u[1] ** 2 + u[2] ** 2))
+    e, hh = U[:, 4] / rho, (U[:, 4] + p) / rho
+    out = np.zeros(U.shape)
+    for d in range(3):
+        ax = 3 - d  # node index i + n(j + n k), array [e][k][j][i]: direction 0 is the last axis
+
+        def Dd(f):
+            return np.moveaxis(np.tensordot(D, np.moveaxis(f, ax, 0), axes=(1, 0)), 0, ax)
+
+        def q2(a, b):
+            return 0.5 * (a * Dd(b) + b * Dd(a) + Dd(a * b))
+
+        def q3(a, b, c):
+            return 0.25 * (a * b * Dd(c) + a * c * Dd(b) + b * c * Dd(a) + a * Dd(b * c) + b * Dd(a * c)
+                           + c * Dd(a * b) + Dd(a * b * c))
+
+        ud = u[d]
+        if kind == "central":
+            F = [rho * ud] + [rho * u[c] * ud + (p if c == d else 0.0) for c in range(3)] + [(U[:, 4] + p) * ud]
+            vol = [Dd(f) for f in F]
+        else:
+            vol = [q2(rho, ud)] + [q3(rho, ud, u[c]) + (Dd(p) if c == d else 0.0) for c in range(3)]
+            vol.append(q3(rho, ud, hh) if kind == "pirozzoli" else q3(rho, ud, e) + q2(p, ud))
+        for v in range(5):
+            out[:, v] -= (2.0 / h[d]) * vol[v]
+    return out
+
+
+@pytest.mark.parametrize("kind", ["pirozzoli", "kg", "central"])
+def test_split_form_volume_flux_equals_product_rule_split(oracle_mod, kind):
+    N = 5
+    lo, hi, nel = (0.0, 0.0, 0.0), (2 * np.pi, 2 * np.pi, 2 * np.pi), (2, 3, 2)
+    xyz, faces = W.box_mesh(N, nel, lo=lo, hi=hi)
+    x, y, z = xyz[:, 0], xyz[:, 1], xyz[:, 2]
+    # high wavenumbers on a coarse mesh: the splits are equivalent at any resolution, and under-resolved
+    # data make the discretisation difference between the two energy averages large
+    rho = 1.0 + 0.3 * np.sin(5 * x + 4 * y) * np.cos(3 * z)
+    U = W.cons_from_prim(rho, 0.4 + 0.3 * np.cos(4 * y) * np.sin(5 * z), 0.2 * np.sin(3 * x + 4 * z),
+                         -0.3 * np.cos(5 * x) * np.sin(4 * y), 1.0 + 0.2 * np.cos(4 * x - 3 * z) * np.sin(5 * y))
+    D = oracle_mod.dmatrix(N)
+    h = [(hi[d] - lo[d]) / nel[d] for d in range(3)]
+    got = oracle_mod.Oracle(N, xyz, faces, vflux=kind, sflux="llf").rhs(U)
+    want = _split_rhs(kind, U, D, h)
+    mag = np.abs(want).max()
+    print(f"SPLIT {kind}: max|oracle - split| / max|split| = {np.abs(got - want).max() / mag:.2e}")
+    assert np.abs(got - want).max() <= 1e-11 * mag, np.abs(got - want).max() / mag
+    if kind != "central":  # the other energy average is far off: the pin sees the energy flux
+        other = _split_rhs("kg" if kind == "pirozzoli" else "pirozzoli", U, D, h)
+        assert np.abs(got[:, 4] - other[:, 4]).max() > 1e-2 * np.abs(want[:, 4]).max()
+        np.testing.assert_allclose(got[:, :4], other[:, :4], rtol=0, atol=1e-12 * mag)

@@ -91,6 +91,11 @@ def test_fv_freestream_and_conservation(oracle_mod, sf):
     Ut, alpha = o.rhs(U, return_alpha=True)
     assert (alpha == 1.0).all()
     assert np.abs(Ut).max() < 1e-12
+    try:  # interface metrics averaged from the nodes instead of telescoped from Ja_0: no freestream
+        _plant(oracle_mod, 5)
+        assert np.abs(o.rhs(U)).max() > 1e-6
+    finally:
+        _plant(oracle_mod, 0)
     U = W.random_smooth_state(xyz, seed=5, amp=0.1)
     U = U * (1.0 + 0.01 * np.random.default_rng(6).uniform(-1, 1, U.shape))
     Ut = o.rhs(U)
@@ -157,3 +162,96 @@ def test_blend_acts_on_the_advective_part_only(oracle_mod):
     eu = oracle_mod.Oracle(N, xyz, faces, equations="euler", **kw).rhs(U)
     np.testing.assert_allclose(ns_sc - eu_sc, ns - eu, rtol=0, atol=1e-12 * np.abs(ns).max())
     assert np.abs(eu_sc - eu).max() > 1e-4  # FV differs from DG on these data
+
+
+# ------------------------------------------------------------------ the subcell reconstruction itself
+#
+# Sec. 4.1: the FV subcells are second order inside the element and first order in the two outer
+# subcells; Hennemann et al.: minmod slopes of the primitive variables, states evaluated at the
+# subcell interfaces (the cumulative LGL weights). The pins use a contact -- u = (U, 0, 0), p
+# constant, rho piecewise linear in x -- on a Cartesian element, where a second-order reconstruction
+# is exact: where both interfaces of a subcell see one line from both sides, the Riemann flux is the
+# exact flux of that line and the subcell's rho_t is exactly -U b (b = the line's slope), so which
+# subcells are exact tells what was reconstructed where.
+
+U_ADV = 0.6
+
+
+def _plant(oracle_mod, k):
+    import ctypes
+
+    ctypes.c_int.in_dll(oracle_mod.lib(), "orc_fv_plant").value = k
+
+
+def _contact(N, rho_of_x):
+    """Two Cartesian elements on [0,2]x[0,1]x[0,1]; returns (xyz, faces, U, x nodes of element 0)."""
+    xyz, faces = W.box_mesh(N, (2, 1, 1), lo=(0, 0, 0), hi=(2, 1, 1))
+    x = xyz[:, 0]
+    zero = np.zeros_like(x)
+    U = W.cons_from_prim(rho_of_x(x), U_ADV + zero, zero, zero, 1.0 + zero)
+    return xyz, faces, U, xyz[0, 0, 0, 0, :]
+
+
+def _subcell_rates(oracle_mod, N, xyz, faces, U):
+    """rho_t of element 0 per subcell along x (after checking it is the same on every y-z line)."""
+    o = oracle_mod.Oracle(N, xyz, faces, vflux="pirozzoli", sflux="llf", **FV_ONLY)
+    r = o.rhs(U)[0, 0]  # [k][j][i]
+    assert np.abs(r - r[:1, :1, :]).max() <= 1e-13 * np.abs(r).max()
+    return r[0, 0, :]
+
+
+def _exact_set(rates, slopes):
+    """Subcells whose rho_t equals -U b for the slope b of the line they sit on."""
+    return {i for i in range(len(rates)) if abs(rates[i] + U_ADV * slopes[i]) <= 1e-10 * abs(U_ADV * slopes[i])}
+
+
+@pytest.mark.parametrize("N", [5, 7])
+def test_fv_reconstruction_exact_for_linear_data_in_interior_subcells(oracle_mod, N):
+    b = 0.2
+    xyz, faces, U, _ = _contact(N, lambda x: 1.5 + b * x)
+    rates = _subcell_rates(oracle_mod, N, xyz, faces, U)
+    exact = _exact_set(rates, [b] * (N + 1))
+    assert exact == set(range(2, N - 1)), exact  # second order inside
+    for i in (1, N - 1):  # next to a first-order outer subcell: the interface jump adds dissipation
+        assert abs(rates[i] + U_ADV * b) > 1e-3 * U_ADV * b
+    try:
+        for plant in (1, 2, 3):  # no slopes; slopes in the outer subcells; states off the interfaces
+            _plant(oracle_mod, plant)
+            got = _exact_set(_subcell_rates(oracle_mod, N, xyz, faces, U), [b] * (N + 1))
+            assert got != set(range(2, N - 1)), (plant, got)
+    finally:
+        _plant(oracle_mod, 0)
+
+
+@pytest.mark.parametrize("b1,b2", [(0.1, 0.3), (0.3, 0.1), (0.2, -0.3)])
+def test_fv_minmod_takes_the_smaller_slope_at_a_kink(oracle_mod, b1, b2):
+    """rho has a kink at node k = 3 of element 0 (N = 7): slopes b1 left of it, b2 right of it.
+    Minmod gives node k the smaller slope of the same sign, or none at an extremum. The exact
+    subcells are then those whose two interfaces each see one line from both sides (subcells 1 and
+    6 border the first-order outer subcells and are never exact):
+      |b1| < |b2|: node k carries the left line, interface k+1/2 jumps -> {2, 5} exact;
+      |b1| > |b2|: node k carries the right line, interface k-1/2 jumps -> {4, 5} exact;
+      opposite signs: node k is flat, both interfaces jump -> {5} exact;
+    and the larger slope (maxmod) gives {4, 5} instead of {2, 5} when |b1| < |b2|."""
+    N, k = 7, 3
+    xk = None
+
+    def rho(x):
+        return 1.5 + np.where(x < xk, b1 * (x - xk), b2 * (x - xk))
+
+    _, _, _, xs = _contact(N, lambda x: x)
+    xk = xs[k]
+    xyz, faces, U, _ = _contact(N, rho)
+    slopes = [b1 if i < k else b2 for i in range(N + 1)]
+    rates = _subcell_rates(oracle_mod, N, xyz, faces, U)
+    exact = _exact_set(rates, slopes)
+    want = {2, 5} if abs(b1) < abs(b2) and b1 * b2 > 0 else ({4, 5} if b1 * b2 > 0 else {5})
+    assert exact == want, exact
+    assert abs(rates[k] + U_ADV * slopes[k]) > 1e-3 * abs(U_ADV * slopes[k])
+    if abs(b1) < abs(b2) and b1 * b2 > 0:
+        try:
+            _plant(oracle_mod, 4)
+            got = _exact_set(_subcell_rates(oracle_mod, N, xyz, faces, U), slopes)
+            assert got == {4, 5}, got
+        finally:
+            _plant(oracle_mod, 0)

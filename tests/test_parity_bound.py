@@ -1,0 +1,69 @@
+"""Calibration of the FP64 parity bound that the GPU tests assert (tests/helpers.py): the GPU's
+right-hand side may differ from the oracle's by at most ULP_FACTOR times the oracle's own spread
+under seeded one-ulp perturbations of the state.
+
+Two facts make that a bound on rounding and nothing else:
+- a second correct FP64 evaluation -- the oracle compiled with FMA contraction, which rounds the
+  metrics, the fluxes and every sum differently -- lies within one spread of the oracle;
+- a small planted mistake (gamma wrong in its ninth digit) exceeds the bound several times over.
+  On the N = 7 Taylor-Green workload (Ma 0.1) it still passes the flux-scale criterion (err <=
+  1e-12 of the largest flux term): there the flux terms are ~1e5 times the right-hand side, which
+  is why the normwise bound, not the flux-scale one, is the test of record.
+"""
+import numpy as np
+import pytest
+
+from helpers import ULP_FACTOR, flux_scale, per_var_max, ulp_spread
+from paper_2306_12891_gb300 import workloads as W
+
+
+def _generic_map(x, y, z):
+    return (x + 0.1 * np.sin(y) * np.cos(z), y + 0.1 * np.sin(z) * np.sin(x) + 0.05 * np.sin(2 * x),
+            z + 0.1 * np.sin(x) * np.cos(y))
+
+
+def _cases():
+    out = []
+    w = W.WORKLOADS["tgv_ns_n7_32x32x32_curved"].with_(nel=(4, 4, 4))
+    out.append(("tgv_ns_n7_4x4x4_curved", w.N, w, None, w.physics()))
+    w = W.WORKLOADS["tgv_euler_n3_4x4x4"]
+    out.append(("tgv_euler_n3_4x4x4", w.N, w, None, w.physics()))
+    out.append(("random_ns_n5_curved", 5, None, 5, dict(equations="ns", vflux="pirozzoli", sflux="roe", mu=0.02)))
+    out.append(("random_euler_n5_fv_blend", 5, None, 6, dict(equations="euler", vflux="pirozzoli", sflux="llf",
+                                                               shock_capturing=True, alpha_fixed=0.5)))
+    return out
+
+
+CASES = _cases()
+
+
+def _mesh_state(N, w, seed):
+    if w is not None:
+        xyz, faces = w.mesh()
+        return xyz, faces, w.initial_state(xyz)
+    xyz, faces = W.box_mesh(N, (3, 2, 3), mapping=_generic_map)
+    U = W.random_smooth_state(xyz, seed=seed, amp=0.1)
+    return xyz, faces, U * (1.0 + 0.01 * np.random.default_rng(seed + 1).uniform(-1, 1, U.shape))
+
+
+@pytest.mark.parametrize("tag,N,w,seed,phys", CASES, ids=[c[0] for c in CASES])
+def test_parity_bound_is_a_rounding_bound(oracle_mod, tag, N, w, seed, phys):
+    xyz, faces, U0 = _mesh_state(N, w, seed)
+    ref = oracle_mod.Oracle(N, xyz, faces, **phys)
+    spread, base = ulp_spread(ref.rhs, U0)
+    bound = ULP_FACTOR * spread
+    mag = per_var_max(base)
+    scale = flux_scale(U0, ref.Ja, ref.J, oracle_mod.dmatrix(N))
+    # a second correct FP64 evaluation: inside one spread (so ULP_FACTOR leaves a margin of 10)
+    other = oracle_mod.Oracle(N, xyz, faces, contracted=True, **phys).rhs(U0)
+    e_fma = per_var_max(other - base)
+    assert (e_fma > 0).any()  # it really rounds differently
+    assert (e_fma <= spread).all(), (tag, e_fma / spread)
+    # a planted mistake: gamma wrong in the ninth digit
+    bad = oracle_mod.Oracle(N, xyz, faces, **{**phys, "gamma": 1.4 * (1.0 + 1e-9)}).rhs(U0)
+    e_bad = per_var_max(bad - base)
+    print(f"BOUND {tag}: bound/|Ut| {bound / mag} fma/spread {e_fma / spread} planted/bound {e_bad / bound} "
+          f"planted flux-scale {e_bad / scale}")
+    assert (e_bad > 3.0 * bound).any(), (tag, e_bad / bound)
+    if tag.startswith("tgv_ns_n7"):  # Ma 0.1: the flux-scale criterion alone would not see it
+        assert (e_bad <= 1e-12 * scale).all(), e_bad / scale

@@ -1,8 +1,9 @@
 """The allocation-free diagnostics entry point, dg_invariants_noalloc.
 
-It is for callers that cannot allocate device memory where they need the integrals (a stream
-under CUDA-graph capture, a host callback, a framework whose pool owns the device memory): its
-partial sums live in a fixed array inside the library instead of context memory. This file is
+It is for callers that cannot allocate device memory where they need the integrals (a host
+framework whose caching allocator holds nearly all of the device memory, or real-time and embedded
+code that forbids allocation after start-up): its partial sums live in a fixed array inside the
+library instead of context memory. This file is
 collected last so that a run stopping at the first failure has already run every other test.
 """
 import ctypes
@@ -54,6 +55,26 @@ def test_noalloc_invariants_match_dg_invariants_twice(env, name, nel):
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_noalloc_several_rows_then_fewer(env):
+    """Several chunk rows with a partial last one (N = 7 on 5x5x5 elements: 64,000 nodes, 4 rows of
+    16,384), then a smaller call on 2x2x3 elements (6,144 nodes, 1 row): the second call must read
+    only the rows it wrote, not the first call's leftovers. Each result against dg_invariants."""
+    dg, torch = env
+    w = W.WORKLOADS["tgv_ns_n7_32x32x32_curved"]
+    out = torch.full((8,), float("nan"), dtype=torch.float64, device="cuda")
+    for nel in [(5, 5, 5), (2, 2, 3)]:
+        ww = w.with_(nel=nel)
+        xyz, faces = ww.mesh()
+        solver = dg.DG(ww.N, xyz, faces, **ww.physics())
+        U = torch.from_numpy(ww.initial_state(xyz)).cuda()
+        _, J = solver.metrics()
+        Ut = solver.rhs(U)
+        ref = solver.invariants(U, Ut)
+        assert _noalloc(dg, torch, ww.N, solver.nE, 1.4, U, Ut, J, out) == 0
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
 
 
 def test_noalloc_rejects_sizes_beyond_its_array(env):
