@@ -96,6 +96,70 @@ def adjoint_volume_flops_per_element(N: int, navier_stokes: bool) -> float:
     return 67.0 * pairs + per_node * n ** 3 + per_face_pt * 6 * n * n
 
 
+def adjoint_visc_flops_per_element(N: int) -> float:
+    """Algorithmic FP64 flops of one adjoint-viscous launch per element (FMA = 2 flops), counted from
+    the statements of the kernel (BR1 lifting, viscous flux and viscous divergence transposed):
+      per node: staging of (u, v, w, T) and l = -lambda/J 21; per direction and lifted variable the
+        forward D sweep (n FMA), the transposed sweep of l (n - 1 FMA) and the metric contraction
+        (3 FMA): 12 (4n + 4); 1/J 12; div and tau 28; Z = Ja^T zeta 60; omega and Y 33; Gamma 26;
+        H = (1/J) Ja Gamma 72; the transposed D sweeps of H 12 (2n + 1); omega added 3
+        -> 72 n + 317 per node;
+      per (node, face) pair on the element surface (6 n^2 per element): the neighbour's lifted
+        quantities 16, the central face value and its cotangent 4 x 13, the face slot 9 -> 77."""
+    n = N + 1
+    return (72.0 * n + 317.0) * n ** 3 + 77.0 * 6 * n * n
+
+
+def fv_subcell_flops_per_element(N: int, riemann_flops: float) -> float:
+    """Algorithmic FP64 flops of the FV subcell operator of one element (the blend's extra work on a
+    troubled element), from the statements of the kernel, per line of n subcells: the reconstructed
+    interface states (minmod slopes of 5 primitives in the n - 2 interior subcells 51, first-order
+    outer subcells 22), and at each of the N interior interfaces the telescoped metric 3 (2n + 2),
+    the unit normal 10, two conservative states 20, the Riemann flux `riemann_flops`, the area factor
+    5 and the subcell update 10 (plus 10 for the last subcell); 3 n^2 lines per element. The blend
+    itself adds 15 per node."""
+    n = N + 1
+    per_line = 51.0 * (n - 2) + 22.0 * 2 + N * (3 * (2 * n + 2) + 10 + 20 + riemann_flops + 5 + 10) + 10
+    return 3 * n * n * per_line + 15.0 * n ** 3
+
+
+LLF_FLOPS = 82.0  # two Euler fluxes 2 x 26, two sound speeds 6, the wave-speed bound 4, the flux 20
+
+
+def fp32_kernel_bytes_per_launch(N: int, n_elems: int) -> dict:
+    """Algorithmic DRAM bytes of one launch of each FP32-bulk kernel of the Navier-Stokes step:
+      volume: volume_kernel_bytes_per_element(N, True, 4) per element;
+      lift: the FP32 shadow state 20, metric terms 36 and 1/J 4 per node in, the BR1 face jumps
+        (6 faces x 4 x n^2 floats per element) in, the contravariant viscous flux 48 per node out;
+      face: per face point (3 n^2 per element) both elements' shadow states 40 and the normal and area
+        16 in, both outward flux slots 40 and BR1 jumps 32 out, the face record 20 per face;
+      other (the shadow refresh k_shadow): U 40 in, the FP32 shadow 20 out per node."""
+    n = N + 1
+    nodes = n ** 3 * n_elems
+    return {"volume": volume_kernel_bytes_per_element(N, True, 4) * n_elems,
+            "lift": nodes * (20 + 36 + 4 + 48) + 6 * 4 * n * n * 4 * n_elems,
+            "face": 3 * n * n * n_elems * (40 + 16 + 40 + 32) + 3 * n_elems * 20,
+            "other": nodes * 60.0}
+
+
+def fp32_step_roofline(N: int, n_elems: int, kt: dict, region_ms: float) -> dict:
+    """Whole-step HBM roofline of the FP32-bulk form: every kernel's algorithmic bytes (times its
+    launches in the timed region) against the timed region, and per kernel against its own time."""
+    per = fp32_kernel_bytes_per_launch(N, n_elems)
+    total, kernels = 0.0, {}
+    for k, (ms, cnt) in kt.items():
+        if not cnt or k not in per:
+            continue
+        b = per[k] * cnt
+        total += b
+        gbs = b / (ms * 1e-3) / 1e9
+        kernels[k] = {"bytes_per_launch": per[k], "ms_per_launch": ms / cnt, "achieved": gbs, "frac": gbs / HBM_GBS}
+    gbs = total / (region_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": HBM_GBS, "unit": "GB/s", "frac": gbs / HBM_GBS,
+            "bytes_per_step": total / max(1, kt.get("volume", (0, 1))[1] // STAGES), "kernels": kernels,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
+
+
 def volume_kernel_bytes_per_element(N: int, navier_stokes: bool, real_bytes: int) -> float:
     """Algorithmic DRAM bytes of one volume-kernel launch per element in an LSERK stage after the
     first: U and the LSERK register g read and written (FP64), the metric terms Ja (real type),
@@ -405,6 +469,9 @@ def run_adjoint(stream, peak_fp64: float, interval: int = 10) -> dict:
     adj_ms, adj_n = kt.get("adj_volume", (0.0, 0))
     flops = adjoint_volume_flops_per_element(w.N, True) * w.n_elems
     achieved = flops / (adj_ms / adj_n * 1e-3) if adj_n else 0.0
+    vis_ms, vis_n = kt.get("adj_visc", (0.0, 0))
+    vflops = adjoint_visc_flops_per_element(w.N) * w.n_elems
+    vachieved = vflops / (vis_ms / vis_n * 1e-3) if vis_n else 0.0
     total = sum(v[0] for v in kt.values())
     return {"workload": ADJOINT_WORKLOAD, "N": w.N, "elements": w.n_elems, "dofs": w.dofs, "steps": K,
             "checkpoint_interval": interval, "objective": "kinetic energy at step K (sum J w rho|u|^2/2)",
@@ -414,6 +481,9 @@ def run_adjoint(stream, peak_fp64: float, interval: int = 10) -> dict:
             "roofline": {"bound": "alu", "kernel": "adj_volume (transposed flux differencing, FP64 pipe)",
                          "achieved": achieved / 1e12, "peak": peak_fp64 / 1e12, "unit": "TFLOP/s",
                          "frac": achieved / peak_fp64, "traffic": None, "flops_per_launch": flops},
+            "visc_roofline": {"bound": "alu", "kernel": "adj_visc (transposed BR1 lifting and viscous flux, FP64 pipe)",
+                              "achieved": vachieved / 1e12, "peak": peak_fp64 / 1e12, "unit": "TFLOP/s",
+                              "frac": vachieved / peak_fp64, "traffic": None, "flops_per_launch": vflops},
             "kernels": {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / max(total, 1e-9), 4)}
                         for k, v in kt.items() if v[1]}}
 
@@ -455,6 +525,83 @@ def run_other_workloads(stream) -> dict:
             row["troubled_fraction"] = float((alpha > 0).double().mean())
         out[key] = row
         del s
+    return out
+
+
+SC_WORKLOAD = "blast_euler_fv_n5_64x64x64"
+
+
+def run_shock_capturing(stream, peak_fp64: float, steps: int = 200, chunk: int = 20, timed: int = 5) -> dict:
+    """The shock-capturing workload where it does FV work (Sec. 4.1-4.2): the blast at 64^3 as named,
+    run for its 200 LSERK(5,4) steps (dt from the CFL condition at the start of every chunk of
+    `chunk` steps, since the blast's wave speeds change), with the troubled fraction (alpha > 0) after
+    each chunk. Kernel timings over `timed` steps at three points: the initial state (the smooth
+    front: no element troubled, the volume kernel's DG path only), the state after the 200 steps
+    (the shock formed: a shell of troubled elements), and that state with alpha = 1 on every element
+    (the FV subcell operator everywhere). The blended volume kernel's roofline comes from the last
+    (every element does the DG and the FV work), and the load balance of skipping FV work per element
+    from the middle one against the line between the other two."""
+    import torch
+
+    from paper_2306_12891_gb300 import dg
+
+    w = WORKLOADS[SC_WORKLOAD]
+    xyz, faces = w.mesh()
+    s = dg.DG(w.N, xyz, faces, stream=stream, **w.physics())
+    U = torch.from_numpy(w.initial_state(xyz)).cuda()
+
+    def timed_steps(solver, V):
+        dt_ = solver.max_dt(V, w.cfl)
+        V2 = V.clone()
+        solver.lserk_steps(V2, dt_, 3)
+        solver.timing_enable(True)
+        solver.timing_get()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        solver.lserk_steps(V2, dt_, timed)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kt = solver.timing_get()
+        solver.timing_enable(False)
+        solver.check()
+        vol_ms, vol_n = kt["volume"]
+        return {"ms_per_step": e0.elapsed_time(e1) / timed, "volume_ms_per_launch": vol_ms / vol_n,
+                "troubled_fraction": float((solver.indicator(V2) > 0).double().mean()),
+                "kernels": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in kt.items() if v[1]}}
+
+    out = {"workload": SC_WORKLOAD, "N": w.N, "elements": w.n_elems, "dofs": w.dofs}
+    out["initial"] = timed_steps(s, U)
+    fractions, t_run = [], 0.0
+    torch.cuda.synchronize()
+    for k in range(steps // chunk):
+        dt = s.max_dt(U, w.cfl)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.lserk_steps(U, dt, chunk)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_run += e0.elapsed_time(e1)
+        s.check()
+        fractions.append(round(float((s.indicator(U) > 0).double().mean()), 5))
+    out["run"] = {"steps": steps, "ms_per_step": t_run / steps, "value": w.dofs * STAGES * steps / (t_run * 1e-3),
+                  "unit": UNIT, "troubled_fraction_every_%d_steps" % chunk: fractions}
+    out["shocked"] = timed_steps(s, U)
+    del s
+    s1 = dg.DG(w.N, xyz, faces, stream=stream, **{**w.physics(), "alpha_fixed": 1.0})
+    out["fv_everywhere"] = timed_steps(s1, U)
+    del s1
+    t0, t1 = out["initial"]["volume_ms_per_launch"], out["fv_everywhere"]["volume_ms_per_launch"]
+    f = out["shocked"]["troubled_fraction"]
+    lin = t0 + f * (t1 - t0)
+    out["load_balance"] = {"troubled_fraction": f, "volume_ms_linear_model": lin,
+                           "volume_ms_measured": out["shocked"]["volume_ms_per_launch"],
+                           "measured_over_model": out["shocked"]["volume_ms_per_launch"] / lin}
+    flops = (volume_kernel_flops_per_element(w.N, False) + fv_subcell_flops_per_element(w.N, LLF_FLOPS)) * w.n_elems
+    achieved = flops / (t1 * 1e-3)
+    out["roofline"] = {"bound": "alu", "kernel": "volume with the DG/FV blend, alpha = 1 on every element (FP64 pipe)",
+                       "achieved": achieved / 1e12, "peak": peak_fp64 / 1e12, "unit": "TFLOP/s",
+                       "frac": achieved / peak_fp64, "traffic": None, "flops_per_launch": flops}
     return out
 
 
@@ -585,6 +732,7 @@ def run_gpu(args):
         ms32 = max_over_ranks(world, f0.elapsed_time(f1))
         kt32 = s32.timing_get()
         s32.timing_enable(False)
+        step32 = fp32_step_roofline(w.N, w.n_elems, kt32, ms32)
         s32.lserk_steps(V, dt, n_done - args.warmup - args.steps)
         s32.check()
         d = (V - U64).abs().amax(dim=(0, 2, 3, 4))
@@ -596,7 +744,7 @@ def run_gpu(args):
                 "steps_compared": n_done,
                 "linf_err_rel_to_state": (d / scale).tolist(),
                 "linf_err_rel_to_change": (d / change).tolist(),
-                "p_ref": p_ref,
+                "p_ref": p_ref, "step_roofline": step32,
                 "kernels": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in kt32.items() if v[1]}}
         v32_ms, v32_n = kt32.get("volume", (0.0, 0))
         if v32_n:  # the FP32 volume kernel against the copy bandwidth (algorithmic bytes per launch)
@@ -646,7 +794,8 @@ def run_gpu(args):
                    "l2": f"inputs larger than L2 (state {state_bytes / 1e6:.0f} MB, working set > 5 GB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "pid_s_per_dof_stage": 1.0 / (value / world),
-        "step_roofline": step_roofline(w.N, value / world, peak_fp64) if not fp32_main else None,
+        "step_roofline": (step_roofline(w.N, value / world, peak_fp64) if not fp32_main
+                          else fp32_step_roofline(w.N, w.n_elems, ktimes, ms)),
         "roofline": roofline,
         "kernels": breakdown,
         "gpu_launches": launches,
@@ -662,6 +811,11 @@ def run_gpu(args):
         line["wall_model"] = run_wall_model(stream)
     if args.others and not args.nel and world == 1:
         line["other_workloads"] = run_other_workloads(stream)
+    if args.shock and not args.nel and world == 1:
+        try:
+            line["shock_capturing"] = run_shock_capturing(stream, peak_fp64)
+        except dg.DGError as ex:  # a non-physical state in the blast run is reported, not fatal to the line
+            line["shock_capturing"] = {"workload": SC_WORKLOAD, "error": str(ex)}
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -678,6 +832,8 @@ def main():
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false", help="skip the adjoint (gradient) block")
     ap.add_argument("--no-wall", dest="wall", action="store_false", help="skip the wall-model cost block")
     ap.add_argument("--no-others", dest="others", action="store_false", help="skip the other workloads' throughput")
+    ap.add_argument("--no-shock", dest="shock", action="store_false",
+                    help="skip the shock-capturing block (the blast's 200 steps with FV work)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk"])
     ap.add_argument("--nel", type=int, default=None, help="elements per direction (default: the workload's 32)")

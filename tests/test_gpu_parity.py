@@ -2,10 +2,10 @@
 same seeded inputs, element by element.
 
 Every FP64 comparison asserts and prints two figures per conservative variable (tests/helpers.py):
-- normwise: max |Ut_GPU - Ut_oracle| may not exceed ten times the oracle's own spread under seeded
-  one-ulp perturbations of the state, i.e. the GPU must agree with the oracle as closely as the
-  problem's conditioning lets any two correct FP64 evaluations agree (the printed "normwise" and
-  "bound" are relative to max |Ut_oracle|);
+- normwise: max |Ut_GPU - Ut_oracle| may not exceed ULP_FACTOR times the oracle's own spread under
+  seeded one-ulp perturbations of its inputs (state values and mesh points), i.e. the GPU must agree
+  with the oracle as closely as the problem's conditioning lets any two correct FP64 evaluations
+  agree (the printed "normwise" and "bound" are relative to max |Ut_oracle|);
 - flux scale: max |Ut_GPU - Ut_oracle| <= 1e-12 scale_v, scale_v = ||2D||_inf max_nodes
   sum_d |F^d_v(U)| / J, the largest flux-difference term the right-hand side sums.
 Time-stepped states use the spread of the oracle's own time-stepped states, and dt * scale_v per
@@ -14,7 +14,7 @@ stage.
 import numpy as np
 import pytest
 
-from helpers import TOL, check_fp64, flux_scale, parity, ulp_spread
+from helpers import TOL, check_fp64, flux_scale, full_size_ulp_spread, parity, ulp_spread
 from paper_2306_12891_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -42,12 +42,13 @@ def pair(env, N, xyz, faces, **phys):
     return dg.DG(N, xyz, faces, **phys), orc.Oracle(N, xyz, faces, **phys)
 
 
-def check_rhs(env, N, xyz, faces, U0, **phys):
+def check_rhs(env, N, xyz, faces, U0, period=2 * np.pi, **phys):
     dg, orc, torch = env
     gpu, ref = pair(env, N, xyz, faces, **phys)
     U = torch.from_numpy(U0).cuda()
     Ut = gpu.rhs(U).cpu().numpy()
-    spread, Ut_ref = ulp_spread(ref.rhs, U0)
+    spread, Ut_ref = ulp_spread(lambda X, V: orc.Oracle(N, X, faces, **phys).rhs(V), xyz, U0, period=period,
+                                base=ref.rhs(U0))
     scale = flux_scale(U0, ref.Ja, ref.J, orc.dmatrix(N))
     err, _ = check_fp64(f"N={N} nE={xyz.shape[0]} {phys}", Ut, Ut_ref, spread, scale)
     gpu.check()
@@ -72,12 +73,13 @@ def test_tgv_euler_n3_rhs_and_ten_steps(env):
     for _ in range(w.steps):
         gpu.lserk_step(U, dt)
 
-    def evolve(V):
+    def evolve(X, V):
+        o = orc.Oracle(w.N, X, faces, **w.physics())
         for _ in range(w.steps):
-            V = ref.lserk_step(V, dt)
+            V = o.lserk_step(V, dt)
         return V
 
-    spread, Uref = ulp_spread(evolve, U0)
+    spread, Uref = ulp_spread(evolve, xyz, U0)
     scale = flux_scale(U0, ref.Ja, ref.J, orc.dmatrix(w.N))
     check_fp64("tgv_euler_n3_4x4x4 ten steps", U.cpu().numpy(), Uref, spread, dt * scale, tol=5 * w.steps * TOL)
     assert np.abs(Uref - U0).max() > 1e-3  # the state moved
@@ -146,7 +148,7 @@ def test_tgv_ns_n7_curved_reduced_rhs_and_step(env):
     dt = ref.max_dt(U0, w.cfl)
     U = torch.from_numpy(U0).cuda()
     gpu.lserk_step(U, dt)
-    spread, U1 = ulp_spread(lambda V: ref.lserk_step(V, dt), U0)
+    spread, U1 = ulp_spread(lambda X, V: orc.Oracle(w.N, X, faces, **w.physics()).lserk_step(V, dt), xyz, U0)
     scale = flux_scale(U0, ref.Ja, ref.J, orc.dmatrix(w.N))
     check_fp64("tgv_ns_n7_4x4x4 one step", U.cpu().numpy(), U1, spread, dt * scale, tol=5 * TOL)
 
@@ -164,7 +166,7 @@ def test_indicator_and_blended_rhs_on_blast(env):
     raw_ref, alpha_ref = ref.indicator(U0)
     assert (alpha_ref > 0).sum() >= 10 and (alpha_ref == 0).sum() >= 10  # both regimes present
     np.testing.assert_allclose(alpha, alpha_ref, rtol=0, atol=1e-12)
-    check_rhs(env, w.N, xyz, faces, U0, **w.physics())
+    check_rhs(env, w.N, xyz, faces, U0, period=1.0, **w.physics())
 
 
 @pytest.mark.parametrize("alpha", [1.0, 0.37])
@@ -233,7 +235,7 @@ def test_full_size_rhs_sampled(env, name, extra):
     if w.shock_capturing and "alpha_fixed" not in extra:
         alpha = gpu.indicator(U).cpu().numpy()
         np.testing.assert_allclose(alpha[sample], alpha_ref[sample], rtol=0, atol=1e-12)
-    spread, _ = ulp_spread(lambda V: ref.rhs(V, mask=sample)[sample], U0, base=Ut_ref[sample])
+    spread = full_size_ulp_spread(name, extra, sample, Ut_ref[sample])
     scale = flux_scale(U0[sample], ref.Ja[sample], ref.J[sample], orc.dmatrix(w.N))
     check_fp64(f"full-size {name} {extra}", Ut[sample], Ut_ref[sample], spread, scale)
 
