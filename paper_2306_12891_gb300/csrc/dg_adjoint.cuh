@@ -482,49 +482,92 @@ constexpr int ADJ_SLOTS = ADJ_NP + 5 + 18;
 // Transposed flux differencing along one line. The forward pair term (scaled by the folded
 // 1/2 factors) is c.F with F0 = S_rho V, F_k = F0 S_u,k + S_p S_j,k, F4 = F0 S_X (+ S_p V / 2 for KG),
 // V = S_u . S_j and c_v = D'_im l_i,v + D'_mi l_m,v (D' = D/4 for mass, D/8 otherwise).
+// one node's staged values for the transposed pair terms
+struct AdjNode {
+  double r, u, v, w, p, x, l[5], jx, jy, jz;
+};
+
+__device__ __forceinline__ AdjNode adj_node(const double *__restrict__ P, const double *__restrict__ Lm, int a,
+                                            const double *__restrict__ Jd, int g) {
+  AdjNode q;
+  q.r = P[a]; q.u = P[PS + a]; q.v = P[2 * PS + a]; q.w = P[3 * PS + a]; q.p = P[4 * PS + a]; q.x = P[5 * PS + a];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) q.l[k] = Lm[k * PS + a];
+  q.jx = __ldg(Jd + g); q.jy = __ldg(Jd + nnn + g); q.jz = __ldg(Jd + 2 * nnn + g);
+  return q;
+}
+
+// the six primitive cotangents of the pair (i, m), shared by both nodes
+template <int VF>
+__device__ __forceinline__ void adj_pair(const AdjNode &a, const AdjNode &b, double dqi, double dqm, double dei,
+                                         double dem, double g[6]) {
+  const double Sr = a.r + b.r, Su = a.u + b.u, Sv = a.v + b.v, Sw = a.w + b.w;
+  const double Sp = a.p + b.p, Sx = a.x + b.x;
+  const double Sjx = a.jx + b.jx, Sjy = a.jy + b.jy, Sjz = a.jz + b.jz;
+  const double c0 = dqi * a.l[0] + dqm * b.l[0];
+  const double c1 = dei * a.l[1] + dem * b.l[1];
+  const double c2 = dei * a.l[2] + dem * b.l[2];
+  const double c3 = dei * a.l[3] + dem * b.l[3];
+  const double c4 = dei * a.l[4] + dem * b.l[4];
+  const double Vp = Su * Sjx + Sv * Sjy + Sw * Sjz;
+  const double F0 = Sr * Vp;
+  const double phi = c0 + c1 * Su + c2 * Sv + c3 * Sw + c4 * Sx;  // d(c.F)/dF0
+  double gV = phi * Sr, gP = c1 * Sjx + c2 * Sjy + c3 * Sjz;
+  if (VF == VF_KG) {
+    gV += 0.5 * c4 * Sp;
+    gP += 0.5 * c4 * Vp;
+  }
+  g[0] = phi * Vp;
+  g[1] = c1 * F0 + gV * Sjx;
+  g[2] = c2 * F0 + gV * Sjy;
+  g[3] = c3 * F0 + gV * Sjz;
+  g[4] = gP;
+  g[5] = c4 * F0;
+}
+
+// Transposed flux differencing along one line, two rows at a time (as the forward line_fluxdiff2):
+// the cotangent sums of nodes i and i+1 stay in registers while partner m runs over i+2..N, so each
+// partner's staged values and partial sums are read (and written back) once for two pairs.
 template <int VF>
 __device__ __forceinline__ void adj_line(const double *__restrict__ P, const double *__restrict__ Lm, int pb, int ps,
                                          const double *__restrict__ Jd, int gb, int gs, double *__restrict__ Ac) {
 #pragma unroll 1
-  for (int i = 0; i < n; ++i) {
-    const int ai = pb + i * ps, gi = gb + i * gs;
-    const double ri = P[ai], ui = P[PS + ai], vi = P[2 * PS + ai], wi = P[3 * PS + ai];
-    const double pi = P[4 * PS + ai], xi_ = P[5 * PS + ai];
-    const double li0 = Lm[ai], li1 = Lm[PS + ai], li2 = Lm[2 * PS + ai], li3 = Lm[3 * PS + ai], li4 = Lm[4 * PS + ai];
-    const double jxi = __ldg(Jd + gi), jyi = __ldg(Jd + nnn + gi), jzi = __ldg(Jd + 2 * nnn + gi);
-    double ac[6];
+  for (int i = 0; i < n - 1; i += 2) {
+    const int a0 = pb + i * ps, a1 = a0 + ps;
+    const AdjNode n0 = adj_node(P, Lm, a0, Jd, gb + i * gs), n1 = adj_node(P, Lm, a1, Jd, gb + (i + 1) * gs);
+    double ac0[6], ac1[6];
 #pragma unroll
-    for (int v = 0; v < 6; ++v) ac[v] = (i == 0) ? 0.0 : Ac[v * PS + ai];
+    for (int v = 0; v < 6; ++v) {
+      ac0[v] = (i == 0) ? 0.0 : Ac[v * PS + a0];
+      ac1[v] = (i == 0) ? 0.0 : Ac[v * PS + a1];
+    }
+    {
+      double g[6];
+      adj_pair<VF>(n0, n1, c_Dq[i * n + i + 1], c_Dq[(i + 1) * n + i], c_De[i * n + i + 1], c_De[(i + 1) * n + i], g);
 #pragma unroll
-    for (int m = i + 1; m < n; ++m) {
-      const int am = pb + m * ps, gm = gb + m * gs;
-      const double Sr = ri + P[am], Su = ui + P[PS + am], Sv = vi + P[2 * PS + am], Sw = wi + P[3 * PS + am];
-      const double Sp = pi + P[4 * PS + am], Sx = xi_ + P[5 * PS + am];
-      const double Sjx = jxi + __ldg(Jd + gm), Sjy = jyi + __ldg(Jd + nnn + gm), Sjz = jzi + __ldg(Jd + 2 * nnn + gm);
-      const double dqi = c_Dq[i * n + m], dqm = c_Dq[m * n + i], dei = c_De[i * n + m], dem = c_De[m * n + i];
-      const double c0 = dqi * li0 + dqm * Lm[am];
-      const double c1 = dei * li1 + dem * Lm[PS + am];
-      const double c2 = dei * li2 + dem * Lm[2 * PS + am];
-      const double c3 = dei * li3 + dem * Lm[3 * PS + am];
-      const double c4 = dei * li4 + dem * Lm[4 * PS + am];
-      const double Vp = Su * Sjx + Sv * Sjy + Sw * Sjz;
-      const double F0 = Sr * Vp;
-      const double phi = c0 + c1 * Su + c2 * Sv + c3 * Sw + c4 * Sx;  // d(c.F)/dF0
-      double gV = phi * Sr, gP = c1 * Sjx + c2 * Sjy + c3 * Sjz;
-      if (VF == VF_KG) {
-        gV += 0.5 * c4 * Sp;
-        gP += 0.5 * c4 * Vp;
-      }
-      const double g[6] = {phi * Vp, c1 * F0 + gV * Sjx, c2 * F0 + gV * Sjy, c3 * F0 + gV * Sjz, gP, c4 * F0};
+      for (int v = 0; v < 6; ++v) { ac0[v] += g[v]; ac1[v] += g[v]; }
+    }
+#pragma unroll
+    for (int m = i + 2; m < n; ++m) {
+      const int am = pb + m * ps;
+      const AdjNode nm = adj_node(P, Lm, am, Jd, gb + m * gs);
+      double g0[6], g1[6];
+      adj_pair<VF>(n0, nm, c_Dq[i * n + m], c_Dq[m * n + i], c_De[i * n + m], c_De[m * n + i], g0);
+      adj_pair<VF>(n1, nm, c_Dq[(i + 1) * n + m], c_Dq[m * n + i + 1], c_De[(i + 1) * n + m], c_De[m * n + i + 1], g1);
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
-        ac[v] += g[v];
-        if (i == 0) Ac[v * PS + am] = g[v];
-        else Ac[v * PS + am] += g[v];
+        ac0[v] += g0[v];
+        ac1[v] += g1[v];
+        const double gm = g0[v] + g1[v];
+        if (i == 0) Ac[v * PS + am] = gm;
+        else Ac[v * PS + am] += gm;
       }
     }
 #pragma unroll
-    for (int v = 0; v < 6; ++v) Ac[v * PS + ai] = ac[v];
+    for (int v = 0; v < 6; ++v) {
+      Ac[v * PS + a0] = ac0[v];
+      Ac[v * PS + a1] = ac1[v];
+    }
   }
 }
 

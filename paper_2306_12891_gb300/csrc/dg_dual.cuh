@@ -76,6 +76,16 @@ __device__ __forceinline__ Dual<K> sqrt(const Dual<K> &a) {
   for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * h;
   return r;
 }
+// 1/sqrt(a); d/da a^(-1/2) = -a^(-3/2) / 2
+template <int K>
+__device__ __forceinline__ Dual<K> rsq(const Dual<K> &a) {
+  Dual<K> r;
+  r.v = ::rsqrt(a.v);
+  const double h = -0.5 * r.v * r.v * r.v;
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * h;
+  return r;
+}
 template <int K>
 __device__ __forceinline__ Dual<K> log(const Dual<K> &a) {
   Dual<K> r;

@@ -212,10 +212,14 @@ __global__ void __launch_bounds__(256) k_shadow(const DgDevice d, const double *
 // pointwise physics (pressure p' = p - p_ref enters the momentum flux; p_ref = 0 in FP64)
 // ---------------------------------------------------------------------------------------------
 
-// Euler flux through the (unit or metric) vector a; returns u.a and the true pressure p
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+
+// Euler flux through the (unit or metric) vector a, given ir = 1/rho; returns u.a and the true
+// pressure p
 template <typename R>
-__device__ __forceinline__ void euler_flux_n(const R U[5], R gam, R pref, R href, const R a[3], R F[5], R &un, R &p) {
-  const R ir = R(1) / U[0];
+__device__ __forceinline__ void euler_flux_ir(const R U[5], R ir, R gam, R pref, R href, const R a[3], R F[5], R &un,
+                                              R &p) {
   const R u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
   const R pm = (gam - R(1)) * (U[4] - R(0.5) * (U[1] * u + U[2] * v + U[3] * w));  // p'
   un = u * a[0] + v * a[1] + w * a[2];
@@ -262,43 +266,50 @@ __device__ __forceinline__ void ec_flux(R rL, R uL, R vL, R wL, R pL, R rR, R uR
          pref * (um * a[0] + vm * a[1] + wm * a[2]);
 }
 
-// Riemann flux F*(UL, UR, nv) for a unit normal nv
+// Riemann flux F*(UL, UR, nv) for a unit normal nv; also returns each side's 1/rho and true pressure
+// (the face kernel's BR1 face values reuse them)
 template <typename R>
 __device__ __forceinline__ void riemann(int sf, const R UL[5], const R UR[5], const R nv[3], R gam, R pref, R href,
-                                        R F[5]) {
+                                        R F[5], R &irL, R &irR, R &pL, R &pR) {
   const R gm1 = gam - R(1);
+  // one reciprocal square root per side: 1/sqrt(rho); 1/rho is its square and sqrt(rho) = rho/sqrt(rho)
+  const R rsL = rsq(UL[0]), rsR = rsq(UR[0]);
+  irL = rsL * rsL;
+  irR = rsR * rsR;
   if (sf == SF_EC) {
-    const R irL = R(1) / UL[0], irR = R(1) / UR[0];
     const R uL = UL[1] * irL, vL = UL[2] * irL, wL = UL[3] * irL;
     const R uR = UR[1] * irR, vR = UR[2] * irR, wR = UR[3] * irR;
-    const R pL = gm1 * (UL[4] - R(0.5) * (UL[1] * uL + UL[2] * vL + UL[3] * wL)) + (kShift<R> ? pref : R(0));
-    const R pR = gm1 * (UR[4] - R(0.5) * (UR[1] * uR + UR[2] * vR + UR[3] * wR)) + (kShift<R> ? pref : R(0));
+    pL = gm1 * (UL[4] - R(0.5) * (UL[1] * uL + UL[2] * vL + UL[3] * wL)) + (kShift<R> ? pref : R(0));
+    pR = gm1 * (UR[4] - R(0.5) * (UR[1] * uR + UR[2] * vR + UR[3] * wR)) + (kShift<R> ? pref : R(0));
     ec_flux<R>(UL[0], uL, vL, wL, pL, UR[0], uR, vR, wR, pR, nv, gam, kShift<R> ? pref : R(0), F);
     return;
   }
-  R FL[5], FR[5], unL, unR, pL, pR;
-  euler_flux_n<R>(UL, gam, pref, href, nv, FL, unL, pL);
-  euler_flux_n<R>(UR, gam, pref, href, nv, FR, unR, pR);
+  R FL[5], FR[5], unL, unR;
+  euler_flux_ir<R>(UL, irL, gam, pref, href, nv, FL, unL, pL);
+  euler_flux_ir<R>(UR, irR, gam, pref, href, nv, FR, unR, pR);
   if (sf == SF_LLF) {
-    const R cL = sqrt(gam * pL / UL[0]), cR = sqrt(gam * pR / UR[0]);
+    const R cL = sqrt(gam * pL * irL), cR = sqrt(gam * pR * irR);
     const R lam = fmax(fabs(unL) + cL, fabs(unR) + cR);
 #pragma unroll
     for (int v = 0; v < 5; ++v) F[v] = R(0.5) * (FL[v] + FR[v] - lam * (UR[v] - UL[v]));
     return;
   }
-  // Roe: sqrt(rho)-weighted average state, three wave families, no entropy fix
-  const R sL = sqrt(UL[0]), sR = sqrt(UR[0]);
+  // Roe: sqrt(rho)-weighted average state, three wave families, no entropy fix. With
+  // s = sqrt(rho), the weight of side k is s_k / (s_L + s_R), so the averages of u and H are
+  // sum_k (m_k / s_k) / (s_L + s_R) = sum_k a_k m_k with a_k = (1/sqrt(rho_k)) / (s_L + s_R).
+  const R sL = UL[0] * rsL, sR = UR[0] * rsR;
   const R iw = R(1) / (sL + sR);
-  const R irL = R(1) / UL[0], irR = R(1) / UR[0];
+  const R aL = rsL * iw, aR = rsR * iw;
   const R uL = UL[1] * irL, vL = UL[2] * irL, wL = UL[3] * irL;
   const R uR = UR[1] * irR, vR = UR[2] * irR, wR = UR[3] * irR;
-  const R ut = (sL * uL + sR * uR) * iw, vt = (sL * vL + sR * vR) * iw, wt = (sL * wL + sR * wR) * iw;
+  const R ut = aL * UL[1] + aR * UR[1], vt = aL * UL[2] + aR * UR[2], wt = aL * UL[3] + aR * UR[3];
   const R EpL = kShift<R> ? UL[4] + pL - pref + href : UL[4] + pL;  // E + p
   const R EpR = kShift<R> ? UR[4] + pR - pref + href : UR[4] + pR;
-  const R Ht = (sL * EpL * irL + sR * EpR * irR) * iw;
+  const R Ht = aL * EpL + aR * EpR;
   const R q2 = ut * ut + vt * vt + wt * wt;
   const R c2 = gm1 * (Ht - R(0.5) * q2);
-  const R ct = sqrt(c2), ic2 = R(1) / c2;
+  const R rc = rsq(c2);  // 1/c; c = c^2/c and 1/c^2 = (1/c)^2
+  const R ct = c2 * rc, ic2 = rc * rc;
   const R rt = sL * sR;
   const R unt = ut * nv[0] + vt * nv[1] + wt * nv[2];
   const R dr = UR[0] - UL[0], dp = pR - pL;
@@ -318,6 +329,13 @@ __device__ __forceinline__ void riemann(int sf, const R UL[5], const R UR[5], co
   D[4] = l1a1 * (Ht - unt * ct) + l5a5 * (Ht + unt * ct) + l2a2 * R(0.5) * q2 + l2r * (ut * dut + vt * dvt + wt * dwt);
 #pragma unroll
   for (int v = 0; v < 5; ++v) F[v] = R(0.5) * (FL[v] + FR[v] - D[v]);
+}
+
+template <typename R>
+__device__ __forceinline__ void riemann(int sf, const R UL[5], const R UR[5], const R nv[3], R gam, R pref, R href,
+                                        R F[5]) {
+  R irL, irR, pL, pR;
+  riemann<R>(sf, UL, UR, nv, gam, pref, href, F, irL, irR, pL, pR);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -506,8 +524,8 @@ __global__ void __launch_bounds__(256) k_face(const DgDevice d, const double *__
   nv[1] = nr[nn];
   nv[2] = nr[2 * nn];
   const R s = nr[3 * nn];
-  R Fs[5];
-  riemann<R>(SF, UL, UR, nv, gam, pref, href, Fs);
+  R Fs[5], irL, irR, pL, pR;
+  riemann<R>(SF, UL, UR, nv, gam, pref, href, Fs, irL, irR, pL, pR);
   R *oL = Buf<R>::Fsurf(d) + ((size_t)eL * 6 + fL) * 5 * nn;
   R *oR = Buf<R>::Fsurf(d) + ((size_t)eR * 6 + fR) * 5 * nn;
 #pragma unroll
@@ -515,14 +533,9 @@ __global__ void __launch_bounds__(256) k_face(const DgDevice d, const double *__
     oL[v * nn + pq] = s * Fs[v];
     oR[v * nn + pqR] = -s * Fs[v];
   }
-  if (d.equations == 1) {
-    const R irL = R(1) / UL[0], irR = R(1) / UR[0];
+  if (d.equations == 1) {  // BR1 face values of (u, v, w, T), from the Riemann solver's 1/rho and p
     const R wL[3] = {UL[1] * irL, UL[2] * irL, UL[3] * irL};
     const R wR[3] = {UR[1] * irR, UR[2] * irR, UR[3] * irR};
-    const R gm1 = gam - R(1);
-    R pL = gm1 * (UL[4] - R(0.5) * (UL[1] * wL[0] + UL[2] * wL[1] + UL[3] * wL[2]));
-    R pR = gm1 * (UR[4] - R(0.5) * (UR[1] * wR[0] + UR[2] * wR[1] + UR[3] * wR[2]));
-    if (kShift<R>) { pL += pref; pR += pref; }
     const R iR = Cst<R>::iR(d);
     const R jump[4] = {R(0.5) * (wR[0] - wL[0]), R(0.5) * (wR[1] - wL[1]), R(0.5) * (wR[2] - wL[2]),
                        R(0.5) * (pR * irR - pL * irL) * iR};
@@ -726,6 +739,92 @@ __device__ __forceinline__ void line_fluxdiff(const R *__restrict__ P, int pb, i
   }
 }
 
+// Kennedy-Gruber / Pirozzoli pair flux from plain sums (see line_fluxdiff): i's staged values and
+// metric terms against partner m's, with the 1/2 factors folded into the coefficients
+template <typename R, int VF>
+__device__ __forceinline__ void kgp_pair(R ri, R ui, R vi, R wi, R p4i, R xi_, R yi, R jxi, R jyi, R jzi,
+                                         const R *__restrict__ P, int am, R jxm, R jym, R jzm, R F[5], R &Vp) {
+  const R Sjx = jxi + jxm, Sjy = jyi + jym, Sjz = jzi + jzm;
+  const R Su = ui + P[PS + am], Sv = vi + P[2 * PS + am], Sw = wi + P[3 * PS + am];
+  Vp = Su * Sjx + Sv * Sjy + Sw * Sjz;  // 4 {u}.{Ja}
+  F[0] = (ri + P[am]) * Vp;             // 8 F_rho
+  const R Sp = p4i + P[4 * PS + am];    // 4 (p'_i + p'_m)
+  F[1] = F[0] * Su + Sp * Sjx;          // 16 F_rho u
+  F[2] = F[0] * Sv + Sp * Sjy;
+  F[3] = F[0] * Sw + Sp * Sjz;
+  if (VF == VF_PIR) F[4] = F[0] * (xi_ + P[5 * PS + am]);                     // 16 {rho}V{h}
+  else F[4] = F[0] * (xi_ + P[5 * PS + am]) + (yi + P[6 * PS + am]) * Vp;   // 16 ({rho}V{e} + {p}V)
+}
+
+// The same flux differencing for the Kennedy-Gruber and Pirozzoli fluxes, two rows at a time: the
+// sums of nodes i and i+1 stay in registers while partner m runs over i+2..N, so each partner's
+// staged values, metric terms and partial sums are read (and its sums written back) once for two
+// pairs instead of once per pair.
+template <typename R, int VF>
+__device__ __forceinline__ void line_fluxdiff2(const R *__restrict__ P, int pb, int ps, const R *__restrict__ Jd,
+                                               int gb, int gs, R *__restrict__ Ac) {
+  static_assert(VF == VF_PIR || VF == VF_KG, "split forms with plain sums only");
+#pragma unroll 1
+  for (int i = 0; i < n - 1; i += 2) {
+    const int a0 = pb + i * ps, a1 = a0 + ps, g0 = gb + i * gs, g1 = g0 + gs;
+    const R r0 = P[a0], u0 = P[PS + a0], v0 = P[2 * PS + a0], w0 = P[3 * PS + a0];
+    const R q0 = P[4 * PS + a0], x0 = P[5 * PS + a0], y0 = VF == VF_KG ? P[6 * PS + a0] : R(0);
+    const R jx0 = __ldg(Jd + g0), jy0 = __ldg(Jd + nnn + g0), jz0 = __ldg(Jd + 2 * nnn + g0);
+    const R r1 = P[a1], u1 = P[PS + a1], v1 = P[2 * PS + a1], w1 = P[3 * PS + a1];
+    const R q1 = P[4 * PS + a1], x1 = P[5 * PS + a1], y1 = VF == VF_KG ? P[6 * PS + a1] : R(0);
+    const R jx1 = __ldg(Jd + g1), jy1 = __ldg(Jd + nnn + g1), jz1 = __ldg(Jd + 2 * nnn + g1);
+    R c0[5], c1[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      c0[v] = (i == 0) ? R(0) : Ac[v * PS + a0];
+      c1[v] = (i == 0) ? R(0) : Ac[v * PS + a1];
+    }
+    {  // the pair (i, i+1)
+      R F[5], Vp;
+      kgp_pair<R, VF>(r0, u0, v0, w0, q0, x0, y0, jx0, jy0, jz0, P, a1, jx1, jy1, jz1, F, Vp);
+      c0[0] += Tab<R>::Dq(i * n + i + 1) * F[0];
+      c1[0] += Tab<R>::Dq((i + 1) * n + i) * F[0];
+#pragma unroll
+      for (int v = 1; v < 5; ++v) {
+        c0[v] += Tab<R>::De(i * n + i + 1) * F[v];
+        c1[v] += Tab<R>::De((i + 1) * n + i) * F[v];
+      }
+    }
+#pragma unroll
+    for (int m = i + 2; m < n; ++m) {
+      const int am = pb + m * ps, gm = gb + m * gs;
+      const R jxm = __ldg(Jd + gm), jym = __ldg(Jd + nnn + gm), jzm = __ldg(Jd + 2 * nnn + gm);
+      R F0[5], F1[5], Vp0, Vp1;
+      kgp_pair<R, VF>(r0, u0, v0, w0, q0, x0, y0, jx0, jy0, jz0, P, am, jxm, jym, jzm, F0, Vp0);
+      kgp_pair<R, VF>(r1, u1, v1, w1, q1, x1, y1, jx1, jy1, jz1, P, am, jxm, jym, jzm, F1, Vp1);
+      const R d0 = Tab<R>::Dq(i * n + m), d1 = Tab<R>::Dq((i + 1) * n + m);
+      const R dm0 = Tab<R>::Dq(m * n + i), dm1 = Tab<R>::Dq(m * n + i + 1);
+      const R e0 = Tab<R>::De(i * n + m), e1 = Tab<R>::De((i + 1) * n + m);
+      const R em0 = Tab<R>::De(m * n + i), em1 = Tab<R>::De(m * n + i + 1);
+      c0[0] += d0 * F0[0];
+      c1[0] += d1 * F1[0];
+      R am_[5];
+      am_[0] = dm0 * F0[0] + dm1 * F1[0];
+#pragma unroll
+      for (int v = 1; v < 5; ++v) {
+        c0[v] += e0 * F0[v];
+        c1[v] += e1 * F1[v];
+        am_[v] = em0 * F0[v] + em1 * F1[v];
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        if (i == 0) Ac[v * PS + am] = am_[v];
+        else Ac[v * PS + am] += am_[v];
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      Ac[v * PS + a0] = c0[v];
+      Ac[v * PS + a1] = c1[v];
+    }
+  }
+}
+
 // Viscous divergence along one line: Ac[1+q]_i -= sum_{m != i} D_im Fv^d_q(m) for the line's n
 // nodes (the diagonal cancels against the surface term, see the file header). Fvd points at the
 // element's contravariant viscous flux of this direction [4][nnn].
@@ -888,10 +987,15 @@ __global__ void __launch_bounds__(vol_threads<R, SC>(), vol_min_blocks<R, SC>())
     if (e >= d.nE) continue;
     int pb, ps, gb, gs, a, b;
     line_geom(dir, line, pb, ps, gb, gs, a, b);
-    line_fluxdiff<R, VF>(P + le * NP * PS, pb, ps, Jab + ((size_t)e * 3 + dir) * 3 * nnn, gb, gs, gam, pref,
-                         Acc + (le * 3 + dir) * 5 * PS);
     // viscous divergence joins the line sums, except under the blend (which must not weight it)
-    if (!SC && d.equations == 1)
+    const bool visc = !SC && d.equations == 1;
+    if constexpr (VF == VF_PIR || VF == VF_KG)
+      line_fluxdiff2<R, VF>(P + le * NP * PS, pb, ps, Jab + ((size_t)e * 3 + dir) * 3 * nnn, gb, gs,
+                            Acc + (le * 3 + dir) * 5 * PS);
+    else
+      line_fluxdiff<R, VF>(P + le * NP * PS, pb, ps, Jab + ((size_t)e * 3 + dir) * 3 * nnn, gb, gs, gam, pref,
+                           Acc + (le * 3 + dir) * 5 * PS);
+    if (visc)
       line_viscous<R>(Buf<R>::Fv(d) + ((size_t)e * 12 + dir * 4) * nnn, gb, gs, pb, ps, Acc + (le * 3 + dir) * 5 * PS);
   }
   __syncthreads();

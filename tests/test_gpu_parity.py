@@ -14,7 +14,8 @@ stage.
 import numpy as np
 import pytest
 
-from helpers import TOL, check_fp64, flux_scale, full_size_ulp_spread, parity, ulp_spread
+from helpers import (TOL, check_fp64, face_jump_magnitude, flux_scale, full_size_ulp_spread, parity,
+                     subcell_range_magnitude, ulp_spread)
 from paper_2306_12891_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -49,7 +50,8 @@ def check_rhs(env, N, xyz, faces, U0, period=2 * np.pi, **phys):
     Ut = gpu.rhs(U).cpu().numpy()
     spread, Ut_ref = ulp_spread(lambda X, V: orc.Oracle(N, X, faces, **phys).rhs(V), xyz, U0, period=period,
                                 base=ref.rhs(U0))
-    scale = flux_scale(U0, ref.Ja, ref.J, orc.dmatrix(N))
+    sub = subcell_range_magnitude(U0, ref.Ja) if phys.get("shock_capturing") else None
+    scale = flux_scale(U0, ref.Ja, ref.J, orc.dmatrix(N), faces=faces, N=N, jump=sub)
     err, _ = check_fp64(f"N={N} nE={xyz.shape[0]} {phys}", Ut, Ut_ref, spread, scale)
     gpu.check()
     return gpu, ref, err
@@ -236,7 +238,10 @@ def test_full_size_rhs_sampled(env, name, extra):
         alpha = gpu.indicator(U).cpu().numpy()
         np.testing.assert_allclose(alpha[sample], alpha_ref[sample], rtol=0, atol=1e-12)
     spread = full_size_ulp_spread(name, extra, sample, Ut_ref[sample])
-    scale = flux_scale(U0[sample], ref.Ja[sample], ref.J[sample], orc.dmatrix(w.N))
+    jump = face_jump_magnitude(U0, faces, w.N, ref.Ja, elements=sample)[sample]
+    if phys.get("shock_capturing"):
+        jump = jump + subcell_range_magnitude(U0[sample], ref.Ja[sample])
+    scale = flux_scale(U0[sample], ref.Ja[sample], ref.J[sample], orc.dmatrix(w.N), jump=jump)
     check_fp64(f"full-size {name} {extra}", Ut[sample], Ut_ref[sample], spread, scale)
 
 
