@@ -661,6 +661,8 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     p_ref = P0_TGV if w.initial == "tgv" else 0.0
     prec = dict(precision="fp32_bulk", p_ref=p_ref) if fp32_main else {}
+    if args.alpha_fixed is not None:  # profiling runs of the blended volume kernel: alpha fixed on every element
+        prec["alpha_fixed"] = args.alpha_fixed
     solver = dg.DG(w.N, xyz, faces, stream=stream, **prec, **w.physics())
     solver.use_tma(args.tma_mode)
     U = torch.from_numpy(U0).cuda()
@@ -786,7 +788,8 @@ def run_gpu(args):
         "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if fp32_main else "f64", "data": "synthetic",
-        "config": {"workload": args.workload if not args.nel else f"{args.workload} reduced to {args.nel}^3",
+        "config": {"workload": (args.workload if not args.nel else f"{args.workload} reduced to {args.nel}^3")
+                   + (f", alpha fixed at {args.alpha_fixed}" if args.alpha_fixed is not None else ""),
                    "N": w.N, "elements": w.n_elems, "dofs": dofs,
                    "physics": "Navier-Stokes, Pirozzoli split form, Roe, BR1, curved mesh, TGV Re 1600 Ma 0.1",
                    "precision": args.precision, "dt": dt, "cfl": w.cfl,
@@ -837,6 +840,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk"])
     ap.add_argument("--nel", type=int, default=None, help="elements per direction (default: the workload's 32)")
+    ap.add_argument("--alpha-fixed", type=float, default=None,
+                    help="shock-capturing workloads: a fixed blending coefficient on every element (profiling)")
     ap.add_argument("--tma-mode", type=int, default=3, choices=[0, 1, 2, 3],
                     help="FP32-bulk kernel form (dg_use_tma): 3 pair-symmetric line kernel (default), "
                          "2 warp-specialised node kernel, 1 TMA node kernel, 0 plain kernels")

@@ -478,6 +478,13 @@ __global__ void __launch_bounds__(LIFT_THREADS) k_adj_visc(const DgDevice d, con
 // ---------------------------------------------------------------------------------------------
 constexpr int ADJ_NP = 6;
 constexpr int ADJ_SLOTS = ADJ_NP + 5 + 18;
+// elements per CTA and CTAs per SM of the adjoint volume kernel: its shared memory (29 staged slots
+// per element) is 1.4x the forward's, so at N = 5 one element per CTA lets three CTAs share an SM
+// (12 warps) where two elements per CTA fitted only one (7 warps)
+__host__ __device__ constexpr int adj_epb() { return N == 1 ? 8 : N == 2 ? 4 : N == 3 ? 2 : N == 4 ? 3 : 1; }
+constexpr int ADJ_EPB = adj_epb();
+constexpr int ADJ_THREADS = round32(3 * nn * ADJ_EPB);
+constexpr int ADJ_MINB = N == 5 ? 3 : N == 6 ? 2 : 1;
 
 // Transposed flux differencing along one line. The forward pair term (scaled by the folded
 // 1/2 factors) is c.F with F0 = S_rho V, F_k = F0 S_u,k + S_p S_j,k, F4 = F0 S_X (+ S_p V / 2 for KG),
@@ -572,7 +579,7 @@ __device__ __forceinline__ void adj_line(const double *__restrict__ P, const dou
 }
 
 template <int VF>
-__global__ void __launch_bounds__(VOL_THREADS, 1) k_adj_volume(const DgDevice d, const double *__restrict__ U,
+__global__ void __launch_bounds__(ADJ_THREADS, ADJ_MINB) k_adj_volume(const DgDevice d, const double *__restrict__ U,
                                                               const double *lam, const double *__restrict__ fslots,
                                                               const double *__restrict__ cotW,
                                                               const double *__restrict__ sigma, double *out,
@@ -580,11 +587,11 @@ __global__ void __launch_bounds__(VOL_THREADS, 1) k_adj_volume(const DgDevice d,
                                                               int update_g) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   double *P = reinterpret_cast<double *>(sm_raw);  // [EPB][6][PS]
-  double *Lm = P + VOL_EPB * ADJ_NP * PS;          // [EPB][5][PS]
-  double *Acc = Lm + VOL_EPB * 5 * PS;             // [EPB][3][6][PS]
-  const int e0 = blockIdx.x * VOL_EPB;
+  double *Lm = P + ADJ_EPB * ADJ_NP * PS;          // [EPB][5][PS]
+  double *Acc = Lm + ADJ_EPB * 5 * PS;             // [EPB][3][6][PS]
+  const int e0 = blockIdx.x * ADJ_EPB;
   const double gam = d.gamma, gm1 = gam - 1.0;
-  for (int t = threadIdx.x; t < VOL_EPB * nnn; t += blockDim.x) {
+  for (int t = threadIdx.x; t < ADJ_EPB * nnn; t += blockDim.x) {
     const int le = t / nnn, node = t % nnn, e = e0 + le;
     if (e >= d.nE) continue;
     double Uv[5];
@@ -602,7 +609,7 @@ __global__ void __launch_bounds__(VOL_THREADS, 1) k_adj_volume(const DgDevice d,
     for (int k = 0; k < 5; ++k) Lm[(le * 5 + k) * PS + pn] = miJ * lam[((size_t)e * 5 + k) * nnn + node];
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < VOL_EPB * 3 * nn; t += blockDim.x) {
+  for (int t = threadIdx.x; t < ADJ_EPB * 3 * nn; t += blockDim.x) {
     const int le = t / (3 * nn), r = t % (3 * nn), dir = r / nn, line = r % nn, e = e0 + le;
     if (e >= d.nE) continue;
     int pb, ps, gb, gs, a, b;
@@ -613,7 +620,7 @@ __global__ void __launch_bounds__(VOL_THREADS, 1) k_adj_volume(const DgDevice d,
   __syncthreads();
   const bool ns = d.equations == 1;
   const double iR = 1.0 / d.R;
-  for (int t = threadIdx.x; t < VOL_EPB * nnn; t += blockDim.x) {
+  for (int t = threadIdx.x; t < ADJ_EPB * nnn; t += blockDim.x) {
     const int le = t / nnn, node = t % nnn, e = e0 + le;
     if (e >= d.nE) continue;
     const int ijk[3] = {node % n, (node / n) % n, node / nn};
@@ -741,13 +748,13 @@ template <int VF>
 void launch_adj_volume_t(const DgDevice &d, const double *U, const double *lam, const double *fslots,
                          const double *cotW, const double *sigma, double *out, double *gbar, int mode, double dt,
                          double A, double B, int update_g, cudaStream_t s) {
-  const size_t smem = sizeof(double) * VOL_EPB * ADJ_SLOTS * PS;
+  const size_t smem = sizeof(double) * ADJ_EPB * ADJ_SLOTS * PS;
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_adj_volume<VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_set = true;
   }
-  k_adj_volume<VF><<<(d.nE + VOL_EPB - 1) / VOL_EPB, VOL_THREADS, smem, s>>>(d, U, lam, fslots, cotW, sigma, out,
+  k_adj_volume<VF><<<(d.nE + ADJ_EPB - 1) / ADJ_EPB, ADJ_THREADS, smem, s>>>(d, U, lam, fslots, cotW, sigma, out,
                                                                             gbar, mode, dt, A, B, update_g);
 }
 

@@ -407,6 +407,8 @@ dg_status dg_init(const dg_mesh *mesh, int N, int nodes, const dg_params *prm, v
   d.alpha_fixed = prm->alpha_fixed;
   d.p_ref = prm->precision == DG_FP32_BULK ? prm->p_ref : 0.0;
   d.gm1 = d.gamma - 1.0;
+  d.igm1 = 1.0 / d.gm1;
+  d.igm1_f = (float)d.igm1;
   d.iR = 1.0 / d.R;
   d.href = d.p_ref * d.gamma / (d.gamma - 1.0);
   d.eref = d.p_ref / (d.gamma - 1.0);

@@ -27,8 +27,8 @@ struct DgDevice {
   // per-context constants computed once on the host (the FP32 kernels would otherwise form them
   // per thread on the FP64 pipe): gamma-1, 1/R, p_ref gamma/(gamma-1), p_ref/(gamma-1), and their
   // FP32 roundings
-  double gm1, iR, href, eref;
-  float gamma_f, gm1_f, iR_f, p_ref_f, href_f, mu_f, kappa_f;
+  double gm1, iR, href, eref, igm1;
+  float gamma_f, gm1_f, iR_f, p_ref_f, href_f, mu_f, kappa_f, igm1_f;
   // wall-modelled walls (faces with elemR = -1; Sec. 3): exchange node index, van Driest on/off
   // with b = sqrt(r m)/sqrt(1 + r m), m = (gamma-1)/2 Ma_inf^2, r = Pr^(1/3), and freestream speed
   int use_tma;         // FP32-bulk volume operator through the TMA-fed persistent kernel (N = 3, 5, 7)

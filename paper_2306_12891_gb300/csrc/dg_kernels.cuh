@@ -52,9 +52,10 @@ __constant__ double c_D2[nn];     // 2 D_im, zero diagonal
 __constant__ double c_Dq[nn];     // D_im / 4 (scaled mass flux), zero diagonal
 __constant__ double c_De[nn];     // D_im / 8 (scaled momentum / energy flux), zero diagonal
 __constant__ double c_w[n], c_invw[n], c_xi[n], c_xh[n + 1];
+__constant__ double c_ihx[n];  // 1 / (xi_i - xi_{i-1}), i = 1..N (minmod slopes)
 __constant__ double c_Vinv[nn];
 __constant__ float f_D[nn], f_D2[nn], f_Dq[nn], f_De[nn];
-__constant__ float f_w[n], f_invw[n], f_xi[n], f_xh[n + 1];
+__constant__ float f_w[n], f_invw[n], f_xi[n], f_xh[n + 1], f_ihx[n];
 
 // basis tables in the arithmetic type
 template <typename R> struct Tab;
@@ -67,6 +68,7 @@ template <> struct Tab<double> {
   static __device__ __forceinline__ double invw(int k) { return c_invw[k]; }
   static __device__ __forceinline__ double xi(int k) { return c_xi[k]; }
   static __device__ __forceinline__ double xh(int k) { return c_xh[k]; }
+  static __device__ __forceinline__ double ihx(int k) { return c_ihx[k]; }
 };
 template <> struct Tab<float> {
   static __device__ __forceinline__ float D(int k) { return f_D[k]; }
@@ -77,6 +79,7 @@ template <> struct Tab<float> {
   static __device__ __forceinline__ float invw(int k) { return f_invw[k]; }
   static __device__ __forceinline__ float xi(int k) { return f_xi[k]; }
   static __device__ __forceinline__ float xh(int k) { return f_xh[k]; }
+  static __device__ __forceinline__ float ihx(int k) { return f_ihx[k]; }
 };
 
 // per-context constants in the arithmetic type (precomputed on the host)
@@ -84,6 +87,7 @@ template <typename R> struct Cst;
 template <> struct Cst<double> {
   static __device__ __forceinline__ double gam(const DgDevice &d) { return d.gamma; }
   static __device__ __forceinline__ double gm1(const DgDevice &d) { return d.gm1; }
+  static __device__ __forceinline__ double igm1(const DgDevice &d) { return d.igm1; }
   static __device__ __forceinline__ double iR(const DgDevice &d) { return d.iR; }
   static __device__ __forceinline__ double pref(const DgDevice &d) { return d.p_ref; }
   static __device__ __forceinline__ double href(const DgDevice &d) { return d.href; }
@@ -93,6 +97,7 @@ template <> struct Cst<double> {
 template <> struct Cst<float> {
   static __device__ __forceinline__ float gam(const DgDevice &d) { return d.gamma_f; }
   static __device__ __forceinline__ float gm1(const DgDevice &d) { return d.gm1_f; }
+  static __device__ __forceinline__ float igm1(const DgDevice &d) { return d.igm1_f; }
   static __device__ __forceinline__ float iR(const DgDevice &d) { return d.iR_f; }
   static __device__ __forceinline__ float pref(const DgDevice &d) { return d.p_ref_f; }
   static __device__ __forceinline__ float href(const DgDevice &d) { return d.href_f; }
@@ -739,92 +744,6 @@ __device__ __forceinline__ void line_fluxdiff(const R *__restrict__ P, int pb, i
   }
 }
 
-// Kennedy-Gruber / Pirozzoli pair flux from plain sums (see line_fluxdiff): i's staged values and
-// metric terms against partner m's, with the 1/2 factors folded into the coefficients
-template <typename R, int VF>
-__device__ __forceinline__ void kgp_pair(R ri, R ui, R vi, R wi, R p4i, R xi_, R yi, R jxi, R jyi, R jzi,
-                                         const R *__restrict__ P, int am, R jxm, R jym, R jzm, R F[5], R &Vp) {
-  const R Sjx = jxi + jxm, Sjy = jyi + jym, Sjz = jzi + jzm;
-  const R Su = ui + P[PS + am], Sv = vi + P[2 * PS + am], Sw = wi + P[3 * PS + am];
-  Vp = Su * Sjx + Sv * Sjy + Sw * Sjz;  // 4 {u}.{Ja}
-  F[0] = (ri + P[am]) * Vp;             // 8 F_rho
-  const R Sp = p4i + P[4 * PS + am];    // 4 (p'_i + p'_m)
-  F[1] = F[0] * Su + Sp * Sjx;          // 16 F_rho u
-  F[2] = F[0] * Sv + Sp * Sjy;
-  F[3] = F[0] * Sw + Sp * Sjz;
-  if (VF == VF_PIR) F[4] = F[0] * (xi_ + P[5 * PS + am]);                     // 16 {rho}V{h}
-  else F[4] = F[0] * (xi_ + P[5 * PS + am]) + (yi + P[6 * PS + am]) * Vp;   // 16 ({rho}V{e} + {p}V)
-}
-
-// The same flux differencing for the Kennedy-Gruber and Pirozzoli fluxes, two rows at a time: the
-// sums of nodes i and i+1 stay in registers while partner m runs over i+2..N, so each partner's
-// staged values, metric terms and partial sums are read (and its sums written back) once for two
-// pairs instead of once per pair.
-template <typename R, int VF>
-__device__ __forceinline__ void line_fluxdiff2(const R *__restrict__ P, int pb, int ps, const R *__restrict__ Jd,
-                                               int gb, int gs, R *__restrict__ Ac) {
-  static_assert(VF == VF_PIR || VF == VF_KG, "split forms with plain sums only");
-#pragma unroll 1
-  for (int i = 0; i < n - 1; i += 2) {
-    const int a0 = pb + i * ps, a1 = a0 + ps, g0 = gb + i * gs, g1 = g0 + gs;
-    const R r0 = P[a0], u0 = P[PS + a0], v0 = P[2 * PS + a0], w0 = P[3 * PS + a0];
-    const R q0 = P[4 * PS + a0], x0 = P[5 * PS + a0], y0 = VF == VF_KG ? P[6 * PS + a0] : R(0);
-    const R jx0 = __ldg(Jd + g0), jy0 = __ldg(Jd + nnn + g0), jz0 = __ldg(Jd + 2 * nnn + g0);
-    const R r1 = P[a1], u1 = P[PS + a1], v1 = P[2 * PS + a1], w1 = P[3 * PS + a1];
-    const R q1 = P[4 * PS + a1], x1 = P[5 * PS + a1], y1 = VF == VF_KG ? P[6 * PS + a1] : R(0);
-    const R jx1 = __ldg(Jd + g1), jy1 = __ldg(Jd + nnn + g1), jz1 = __ldg(Jd + 2 * nnn + g1);
-    R c0[5], c1[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      c0[v] = (i == 0) ? R(0) : Ac[v * PS + a0];
-      c1[v] = (i == 0) ? R(0) : Ac[v * PS + a1];
-    }
-    {  // the pair (i, i+1)
-      R F[5], Vp;
-      kgp_pair<R, VF>(r0, u0, v0, w0, q0, x0, y0, jx0, jy0, jz0, P, a1, jx1, jy1, jz1, F, Vp);
-      c0[0] += Tab<R>::Dq(i * n + i + 1) * F[0];
-      c1[0] += Tab<R>::Dq((i + 1) * n + i) * F[0];
-#pragma unroll
-      for (int v = 1; v < 5; ++v) {
-        c0[v] += Tab<R>::De(i * n + i + 1) * F[v];
-        c1[v] += Tab<R>::De((i + 1) * n + i) * F[v];
-      }
-    }
-#pragma unroll
-    for (int m = i + 2; m < n; ++m) {
-      const int am = pb + m * ps, gm = gb + m * gs;
-      const R jxm = __ldg(Jd + gm), jym = __ldg(Jd + nnn + gm), jzm = __ldg(Jd + 2 * nnn + gm);
-      R F0[5], F1[5], Vp0, Vp1;
-      kgp_pair<R, VF>(r0, u0, v0, w0, q0, x0, y0, jx0, jy0, jz0, P, am, jxm, jym, jzm, F0, Vp0);
-      kgp_pair<R, VF>(r1, u1, v1, w1, q1, x1, y1, jx1, jy1, jz1, P, am, jxm, jym, jzm, F1, Vp1);
-      const R d0 = Tab<R>::Dq(i * n + m), d1 = Tab<R>::Dq((i + 1) * n + m);
-      const R dm0 = Tab<R>::Dq(m * n + i), dm1 = Tab<R>::Dq(m * n + i + 1);
-      const R e0 = Tab<R>::De(i * n + m), e1 = Tab<R>::De((i + 1) * n + m);
-      const R em0 = Tab<R>::De(m * n + i), em1 = Tab<R>::De(m * n + i + 1);
-      c0[0] += d0 * F0[0];
-      c1[0] += d1 * F1[0];
-      R am_[5];
-      am_[0] = dm0 * F0[0] + dm1 * F1[0];
-#pragma unroll
-      for (int v = 1; v < 5; ++v) {
-        c0[v] += e0 * F0[v];
-        c1[v] += e1 * F1[v];
-        am_[v] = em0 * F0[v] + em1 * F1[v];
-      }
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        if (i == 0) Ac[v * PS + am] = am_[v];
-        else Ac[v * PS + am] += am_[v];
-      }
-    }
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      Ac[v * PS + a0] = c0[v];
-      Ac[v * PS + a1] = c1[v];
-    }
-  }
-}
-
 // Viscous divergence along one line: Ac[1+q]_i -= sum_{m != i} D_im Fv^d_q(m) for the line's n
 // nodes (the diagonal cancels against the surface term, see the file header). Fvd points at the
 // element's contravariant viscous flux of this direction [4][nnn].
@@ -865,7 +784,7 @@ __device__ __forceinline__ void subcell_states(const R *__restrict__ P, int pb, 
     R qb[5], qf[5];
     staged_prim<R>(P, pb + (i - 1) * ps, qb);
     staged_prim<R>(P, pb + (i + 1) * ps, qf);
-    const R hb = R(1) / (Tab<R>::xi(i) - Tab<R>::xi(i - 1)), hf = R(1) / (Tab<R>::xi(i + 1) - Tab<R>::xi(i));
+    const R hb = Tab<R>::ihx(i), hf = Tab<R>::ihx(i + 1);
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       const R sb = (q[v] - qb[v]) * hb, sf_ = (qf[v] - q[v]) * hf;
@@ -884,9 +803,9 @@ __device__ __forceinline__ void subcell_states(const R *__restrict__ P, int pb, 
 
 // conservative state from (rho, u, v, w, p') in the kernel's representation (E' in FP32)
 template <typename R>
-__device__ __forceinline__ void cons_of(const R q[5], R gm1, R U[5]) {
+__device__ __forceinline__ void cons_of(const R q[5], R igm1, R U[5]) {
   U[0] = q[0]; U[1] = q[0] * q[1]; U[2] = q[0] * q[2]; U[3] = q[0] * q[3];
-  U[4] = q[4] / gm1 + R(0.5) * q[0] * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  U[4] = q[4] * igm1 + R(0.5) * q[0] * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
 }
 
 // FV subcell operator along one line (Sec. 4.1): Riemann fluxes at the N interior subcell
@@ -894,9 +813,8 @@ __device__ __forceinline__ void cons_of(const R q[5], R gm1, R U[5]) {
 // fluxes at the element faces, and Ac_i = (f_{i+1/2} - f_{i-1/2}) / w_i written to shared memory.
 template <typename R>
 __device__ __forceinline__ void line_fv(const R *__restrict__ P, int pb, int ps, const R *__restrict__ Jd, int gb,
-                                        int gs, const R *Fm, const R *Fp, int sf, R gam, R pref, R href,
+                                        int gs, const R *Fm, const R *Fp, int sf, R gam, R igm1, R pref, R href,
                                         R *__restrict__ Ac) {
-  const R gm1 = gam - R(1);
   R fl[5];  // flux at the left interface of the current subcell, +xi direction
 #pragma unroll
   for (int v = 0; v < 5; ++v) fl[v] = -Fm[v * nn];
@@ -916,12 +834,13 @@ __device__ __forceinline__ void line_fv(const R *__restrict__ P, int pb, int ps,
         for (int m = 0; m < n; ++m) dj += Tab<R>::D(i * n + m) * __ldg(Jd + c * nnn + gb + m * gs);
         a[c] += Tab<R>::w(i) * dj;
       }
-      const R s = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-      const R is = R(1) / s;
+      const R a2 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+      const R is = rsq(a2);  // 1/|a|; |a| = |a|^2 / |a|
+      const R s = a2 * is;
       const R nv[3] = {a[0] * is, a[1] * is, a[2] * is};
       R UL[5], UR[5], Fs[5];
-      cons_of<R>(qRi, gm1, UL);
-      cons_of<R>(qLn, gm1, UR);
+      cons_of<R>(qRi, igm1, UL);
+      cons_of<R>(qLn, igm1, UR);
       riemann<R>(sf, UL, UR, nv, gam, pref, href, Fs);
 #pragma unroll
       for (int v = 0; v < 5; ++v) fr[v] = s * Fs[v];
@@ -989,12 +908,8 @@ __global__ void __launch_bounds__(vol_threads<R, SC>(), vol_min_blocks<R, SC>())
     line_geom(dir, line, pb, ps, gb, gs, a, b);
     // viscous divergence joins the line sums, except under the blend (which must not weight it)
     const bool visc = !SC && d.equations == 1;
-    if constexpr (VF == VF_PIR || VF == VF_KG)
-      line_fluxdiff2<R, VF>(P + le * NP * PS, pb, ps, Jab + ((size_t)e * 3 + dir) * 3 * nnn, gb, gs,
-                            Acc + (le * 3 + dir) * 5 * PS);
-    else
-      line_fluxdiff<R, VF>(P + le * NP * PS, pb, ps, Jab + ((size_t)e * 3 + dir) * 3 * nnn, gb, gs, gam, pref,
-                           Acc + (le * 3 + dir) * 5 * PS);
+    line_fluxdiff<R, VF>(P + le * NP * PS, pb, ps, Jab + ((size_t)e * 3 + dir) * 3 * nnn, gb, gs, gam, pref,
+                         Acc + (le * 3 + dir) * 5 * PS);
     if (visc)
       line_viscous<R>(Buf<R>::Fv(d) + ((size_t)e * 12 + dir * 4) * nnn, gb, gs, pb, ps, Acc + (le * 3 + dir) * 5 * PS);
   }
@@ -1034,8 +949,8 @@ __global__ void __launch_bounds__(vol_threads<R, SC>(), vol_min_blocks<R, SC>())
       line_geom(dir, line, pb, ps, gb, gs, a, b);
       const R *Fm = Fsb + ((size_t)e * 6 + 2 * dir) * 5 * nn + a + n * b;
       const R *Fp = Fsb + ((size_t)e * 6 + 2 * dir + 1) * 5 * nn + a + n * b;
-      line_fv<R>(P + le * NP * PS, pb, ps, Jab + ((size_t)e * 3 + dir) * 3 * nnn, gb, gs, Fm, Fp, d.sflux, gam, pref,
-                 href, Acc + (le * 3 + dir) * 5 * PS);
+      line_fv<R>(P + le * NP * PS, pb, ps, Jab + ((size_t)e * 3 + dir) * 3 * nnn, gb, gs, Fm, Fp, d.sflux, gam,
+                 Cst<R>::igm1(d), pref, href, Acc + (le * 3 + dir) * 5 * PS);
     }
     __syncthreads();
   }
@@ -1147,58 +1062,64 @@ namespace {
 // ---------------------------------------------------------------------------------------------
 // modified Persson indicator (Sec. 4.1, Eq. (7)) and the neighbour extension (FP64)
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_indicator(const DgDevice d, const double *__restrict__ U) {
-  __shared__ double q[nnn], t1[nnn];
-  __shared__ double red[3][128];
-  const int e = blockIdx.x;
+// One warp per element (IND_WARPS elements per CTA): q = rho p staged in shared memory, its modal
+// coefficients by three tensor-product passes with the inverse Vandermonde (from a padded
+// shared-memory copy, so lanes reading different rows do not serialise on constant memory), the
+// shell energies reduced with warp shuffles; no block-wide barrier after the table load.
+constexpr int IND_WARPS = 4;
+__global__ void __launch_bounds__(32 * IND_WARPS) k_indicator(const DgDevice d, const double *__restrict__ U) {
+  __shared__ double sV[n][n + 1];
+  __shared__ double q[IND_WARPS][nnn], t1[IND_WARPS][nnn];
+  for (int t = threadIdx.x; t < nn; t += blockDim.x) sV[t / n][t % n] = c_Vinv[t];
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * IND_WARPS + w;
+  if (e >= d.nE) return;
   const double gm1 = d.gamma - 1.0;
-  for (int node = threadIdx.x; node < nnn; node += blockDim.x) {
+  double *qw = q[w], *tw = t1[w];
+  for (int node = lane; node < nnn; node += 32) {
     const double *Ue = U + (size_t)e * 5 * nnn + node;
     const double r = Ue[0];
     const double p = gm1 * (Ue[4 * nnn] - 0.5 * (Ue[nnn] * Ue[nnn] + Ue[2 * nnn] * Ue[2 * nnn] + Ue[3 * nnn] * Ue[3 * nnn]) / r);
-    q[node] = r * p;
+    qw[node] = r * p;
   }
-  __syncthreads();
-  // modal coefficients: three tensor-product passes with the inverse Vandermonde
-  for (int node = threadIdx.x; node < nnn; node += blockDim.x) {  // xi: (i,j,k) -> (a,j,k)
+  __syncwarp();
+  for (int node = lane; node < nnn; node += 32) {  // xi: (i,j,k) -> (a,j,k)
     const int a = node % n, base = node - a;
     double s = 0.0;
 #pragma unroll
-    for (int i = 0; i < n; ++i) s += c_Vinv[a * n + i] * q[base + i];
-    t1[node] = s;
+    for (int i = 0; i < n; ++i) s += sV[a][i] * qw[base + i];
+    tw[node] = s;
   }
-  __syncthreads();
-  for (int node = threadIdx.x; node < nnn; node += blockDim.x) {  // eta
+  __syncwarp();
+  for (int node = lane; node < nnn; node += 32) {  // eta
     const int b = (node / n) % n, base = node - b * n;
     double s = 0.0;
 #pragma unroll
-    for (int j = 0; j < n; ++j) s += c_Vinv[b * n + j] * t1[base + j * n];
-    q[node] = s;
+    for (int j = 0; j < n; ++j) s += sV[b][j] * tw[base + j * n];
+    qw[node] = s;
   }
-  __syncthreads();
+  __syncwarp();
   double all = 0.0, shN = 0.0, shN1 = 0.0;
-  for (int node = threadIdx.x; node < nnn; node += blockDim.x) {  // zeta, then the shell energies
+  for (int node = lane; node < nnn; node += 32) {  // zeta, then the shell energies
     const int a = node % n, b = (node / n) % n, c = node / nn, base = node - c * nn;
     double s = 0.0;
 #pragma unroll
-    for (int k = 0; k < n; ++k) s += c_Vinv[c * n + k] * q[base + k * nn];
+    for (int k = 0; k < n; ++k) s += sV[c][k] * qw[base + k * nn];
     const int M = max(a, max(b, c));
     const double m2 = s * s;
     all += m2;
     if (M == N) shN += m2;
     if (M == N - 1) shN1 += m2;
   }
-  red[0][threadIdx.x] = all;
-  red[1][threadIdx.x] = shN;
-  red[2][threadIdx.x] = shN1;
-  __syncthreads();
-  for (int w = 64; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
-      for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
-    __syncthreads();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    all += __shfl_down_sync(0xffffffffu, all, o);
+    shN += __shfl_down_sync(0xffffffffu, shN, o);
+    shN1 += __shfl_down_sync(0xffffffffu, shN1, o);
   }
-  if (threadIdx.x == 0) {
-    const double tot = red[0][0], sN = red[1][0], sN1 = red[2][0];
+  if (lane == 0) {
+    const double tot = all, sN = shN, sN1 = shN1;
     double E = tot > 1e-300 ? sN / tot : 0.0;
     if (N >= 2) {
       const double tot1 = tot - sN;
@@ -1318,7 +1239,14 @@ cudaError_t upload(const DgTables &t) {
     }
   for (int i = 0; i < n; ++i) { fw[i] = (float)t.w[i]; finvw[i] = (float)t.invw[i]; fxi[i] = (float)t.xi[i]; }
   for (int i = 0; i <= n; ++i) fxh[i] = (float)t.xh[i];
+  double ihx[n];
+  float fihx[n];
+  ihx[0] = 0.0;
+  for (int i = 1; i < n; ++i) ihx[i] = 1.0 / (t.xi[i] - t.xi[i - 1]);
+  for (int i = 0; i < n; ++i) fihx[i] = (float)ihx[i];
   cudaError_t err = cudaSuccess;
+  err = err ? err : cudaMemcpyToSymbol(c_ihx, ihx, sizeof(double) * n);
+  err = err ? err : cudaMemcpyToSymbol(f_ihx, fihx, sizeof(float) * n);
   err = err ? err : cudaMemcpyToSymbol(c_D, t.D, sizeof(double) * nn);
   err = err ? err : cudaMemcpyToSymbol(c_D2, D2, sizeof(double) * nn);
   err = err ? err : cudaMemcpyToSymbol(c_Dq, Dq, sizeof(double) * nn);
@@ -1502,7 +1430,9 @@ void launch_volume(const DgDevice &d, const double *U, double *out, double *g, i
   else launch_volume_r<double>(d, U, out, g, mode, first, dt, A, B, s);
 }
 
-void launch_indicator(const DgDevice &d, const double *U, cudaStream_t s) { k_indicator<<<d.nE, 128, 0, s>>>(d, U); }
+void launch_indicator(const DgDevice &d, const double *U, cudaStream_t s) {
+  k_indicator<<<(d.nE + IND_WARPS - 1) / IND_WARPS, 32 * IND_WARPS, 0, s>>>(d, U);
+}
 
 void launch_shadow(const DgDevice &d, const double *U, cudaStream_t s) { k_shadow<<<8 * 152, 256, 0, s>>>(d, U); }
 
