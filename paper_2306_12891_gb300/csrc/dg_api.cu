@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/dg.h"
+#include "dg_convert.cuh"
 #include "dg_internal.h"
 
 namespace {
@@ -78,6 +79,7 @@ struct dg_ctx {
   int tape_steps = 0, tape_interval = 0;
   bool tape_all = false;
   double tape_dt = 0.0;
+  double fac_dt = std::nan("");  // step size of the FP32-bulk stage factor d.facf (NaN: not formed yet)
   // CUDA graph of one LSERK step, replayed by the multi-step calls on a library stream that is
   // ordered after (and before) the caller's stream with events
   int use_graphs = 1;
@@ -404,6 +406,8 @@ dg_status dg_init(const dg_mesh *mesh, int N, int nodes, const dg_params *prm, v
   d.gamma = prm->gamma; d.R = prm->R; d.mu = prm->mu;
   d.kappa = prm->mu * prm->gamma * prm->R / ((prm->gamma - 1.0) * prm->Pr);
   d.alpha_min = prm->alpha_min; d.alpha_max = prm->alpha_max; d.sharpness = prm->sharpness;
+  d.ind_T = 0.5 * std::pow(10.0, -1.8 * std::pow((double)(N + 1), 0.25));
+  d.ind_k = -prm->sharpness / d.ind_T;
   d.alpha_fixed = prm->alpha_fixed;
   d.p_ref = prm->precision == DG_FP32_BULK ? prm->p_ref : 0.0;
   d.gm1 = d.gamma - 1.0;
@@ -449,6 +453,7 @@ dg_status dg_init(const dg_mesh *mesh, int N, int nodes, const dg_params *prm, v
     DG_ALLOC(d.Jaf, (size_t)nE * 9 * nnn);
     DG_ALLOC(d.nrm_f, (size_t)nF * 4 * nn);
     DG_ALLOC(d.invJf, (size_t)nE * nnn);
+    DG_ALLOC(d.facf, (size_t)nE * nnn);
     DG_ALLOC(d.Uf, (size_t)nE * 5 * nnn);
     DG_ALLOC(d.Fsurf_f, (size_t)nE * 6 * 5 * nn);
     if (prm->equations == DG_NAVIER_STOKES) {
@@ -516,6 +521,21 @@ dg_status refresh_shadow(dg_ctx *c, const double *U) {
   if (c->d.precision != DG_FP32_BULK) return DG_OK;
   return launch(c, KC_OTHER, [&] { c->K->shadow(c->d, U, c->stream); });
 }
+
+// FP32-bulk: the epilogue's stage factor float(dt (-1/J)) per node, formed in FP64 and rounded once,
+// whenever the step size changes (outside any graph capture: steps_impl calls this first)
+__global__ void k_stage_factor(float *__restrict__ fac, const double *__restrict__ invJ, double dt, size_t count) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    fac[i] = d2f_int(__dmul_rn(dt, -invJ[i]));
+}
+
+dg_status ensure_stage_factor(dg_ctx *c, double dt) {
+  if (c->d.precision != DG_FP32_BULK || c->fac_dt == dt) return DG_OK;
+  const size_t n = (size_t)c->d.N + 1, count = (size_t)c->d.nE * n * n * n;
+  DG_TRY(launch(c, KC_OTHER, [&] { k_stage_factor<<<8 * 152, 256, 0, c->stream>>>(c->d.facf, c->d.invJ, dt, count); }));
+  c->fac_dt = dt;
+  return DG_OK;
+}
 dg_status plain_steps(dg_ctx *c, double *U, double dt, int n_steps) {
   for (int k = 0; k < n_steps; ++k)
     for (int st = 0; st < 5; ++st) DG_TRY(stage(c, U, U, 1, st, dt));
@@ -557,6 +577,7 @@ dg_status capture_step(dg_ctx *c, double *U, double dt) {
 // launches, which is what bounds small meshes.
 dg_status steps_impl(dg_ctx *c, double *U, double dt, int n_steps) {
   DG_TRY(refresh_shadow(c, U));
+  DG_TRY(ensure_stage_factor(c, dt));
   if (n_steps <= 0) return DG_OK;
   if (!c->use_graphs || c->timing || n_steps < 2) return plain_steps(c, U, dt, n_steps);
   cudaError_t e = cudaSuccess;

@@ -165,23 +165,24 @@ __device__ __forceinline__ void f32_node_terms(const DgDevice &d, const float *_
 // -1/J and the output / LSERK(5,4) stage in FP64 for one node; Ue, ge point at this element's state
 // and register slices [5][nnn] to read (shared or global memory), out and g are global
 __device__ __forceinline__ void f32_finish_reg(const DgDevice &d, const double Uv[5], const double gv0[5],
-                                               double iJ, double *out, double *__restrict__ g, int e, int node,
+                                               float cf, double *out, double *__restrict__ g, int e, int node,
                                                const float s[5], int mode, int first, double dt, double A,
                                                double B) {
-  // Uv, gv0, iJ: this node's U, g and 1/J.
+  // Uv, gv0: this node's U and g; cf: its float(1/J) (mode 0) or float(dt (-1/J)) (mode 1, formed in
+  // FP64 and rounded once per step size by dg_api's k_stage_factor).
   // The right-hand side -s/J, or the stage increment dt (-1/J) s, is one FP32 product of the FP32 sum
-  // s with the factor -1/J or dt (-1/J), formed in FP64 and rounded once (GB300 issues FP64 at 1/64
-  // of the FP32 rate, and this epilogue bounds the kernel); the LSERK register and the state
-  // accumulate in FP64. Explicit roundings (no compiler contraction) keep every kernel variant's bits.
-  const double miJ = -iJ;
+  // s with the factor -1/J or dt (-1/J) (GB300 issues FP64 at 1/64 of the FP32 rate, and this
+  // epilogue bounds the kernel); the LSERK register and the state accumulate in FP64. Explicit
+  // roundings (no compiler contraction) keep every kernel variant's bits.
+  (void)dt;
   const size_t gi = (size_t)e * 5 * nnn + node;
   if (mode == 0) {
-    const float c = d2f_int(miJ);
+    const float c = -cf;  // float(-1/J) = -float(1/J): rounding to nearest is symmetric
 #pragma unroll
     for (int v = 0; v < 5; ++v) out[gi + v * nnn] = f2d_int(__fmul_rn(s[v], c));
     return;
   }
-  const float c = d2f_int(__dmul_rn(dt, miJ));
+  const float c = cf;
   const double eref = d.eref;
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
@@ -196,7 +197,7 @@ __device__ __forceinline__ void f32_finish_reg(const DgDevice &d, const double U
 
 // the same with this element's U, g and 1/J read from global memory or a shared-memory copy
 __device__ __forceinline__ void f32_finish(const DgDevice &d, const double *Ue, const double *ge,
-                                           const double *iJe, double *out, double *__restrict__ g, int e,
+                                           const float *ce, double *out, double *__restrict__ g, int e,
                                            int node, const float s[5], int mode, int first, double dt,
                                            double A, double B) {
   double Uv[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, gv0[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -207,7 +208,7 @@ __device__ __forceinline__ void f32_finish(const DgDevice &d, const double *Ue, 
       if (!first) gv0[v] = ge[node + v * nnn];
     }
   }
-  f32_finish_reg(d, Uv, gv0, iJe[node], out, g, e, node, s, mode, first, dt, A, B);
+  f32_finish_reg(d, Uv, gv0, ce[node], out, g, e, node, s, mode, first, dt, A, B);
 }
 
 template <int VF>
@@ -246,7 +247,8 @@ __global__ void __launch_bounds__(NODE_THREADS, 2) k_volume_f32(const DgDevice d
     f32_node_terms<VF>(d, P + le * 7 * nnn, JS + le * 9 * nnn, FS + le * 12 * nnn,
                        d.Fsurf_f + (size_t)e * 6 * 5 * nn, s_Dz, e, node, s);
     const size_t ge0 = (size_t)e * 5 * nnn;
-    f32_finish(d, U + ge0, g + ge0, d.invJ + (size_t)e * nnn, out, g, e, node, s, mode, first, dt, A, B);
+    f32_finish(d, U + ge0, g + ge0, (mode ? d.facf : d.invJf) + (size_t)e * nnn, out, g, e, node, s, mode, first,
+               dt, A, B);
   }
 }
 
@@ -261,7 +263,8 @@ __global__ void __launch_bounds__(NODE_THREADS, 2) k_volume_f32(const DgDevice d
 constexpr bool TMA_OK = (N == 3 || N == 5 || N == 7);
 constexpr int TMA_THREADS = round32(nnn);
 constexpr unsigned TB_UF = 5u * nnn * 4u, TB_JA = 9u * nnn * 4u, TB_FV = 12u * nnn * 4u, TB_FS = 30u * nn * 4u;
-constexpr unsigned TB_U = 5u * nnn * 8u, TB_G = 5u * nnn * 8u, TB_IJ = nnn * 8u;
+// TB_IJ: the node factor of the epilogue, float(1/J) or float(dt (-1/J)) (f32_finish_reg)
+constexpr unsigned TB_U = 5u * nnn * 8u, TB_G = 5u * nnn * 8u, TB_IJ = nnn * 4u;
 constexpr unsigned TB_BUF = TB_UF + TB_JA + TB_FV + TB_FS + TB_U + TB_G + TB_IJ;
 constexpr unsigned TB_P = 7u * nnn * 4u;
 constexpr unsigned TB_SMEM = 2u * TB_BUF + TB_P + 16u;
@@ -331,7 +334,8 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) k_volume_f32_tma(const DgDevic
     bulk_g2s(smem_addr(b + TB_UF + TB_JA + TB_FV), d.Fsurf_f + e * 30 * nn, TB_FS, mb);
     if (needU) bulk_g2s(smem_addr(b + TB_UF + TB_JA + TB_FV + TB_FS), U + e * 5 * nnn, TB_U, mb);
     if (needG) bulk_g2s(smem_addr(b + TB_UF + TB_JA + TB_FV + TB_FS + TB_U), g + e * 5 * nnn, TB_G, mb);
-    bulk_g2s(smem_addr(b + TB_UF + TB_JA + TB_FV + TB_FS + TB_U + TB_G), d.invJ + e * nnn, TB_IJ, mb);
+    bulk_g2s(smem_addr(b + TB_UF + TB_JA + TB_FV + TB_FS + TB_U + TB_G), (mode ? d.facf : d.invJf) + e * nnn,
+             TB_IJ, mb);
   };
   if (tid == 0) {
     issue(0);
@@ -358,7 +362,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) k_volume_f32_tma(const DgDevic
     const float *Sb = reinterpret_cast<const float *>(b + TB_UF + TB_JA + TB_FV);
     const double *Ub = reinterpret_cast<const double *>(b + TB_UF + TB_JA + TB_FV + TB_FS);
     const double *Gb = reinterpret_cast<const double *>(b + TB_UF + TB_JA + TB_FV + TB_FS + TB_U);
-    const double *Ib = reinterpret_cast<const double *>(b + TB_UF + TB_JA + TB_FV + TB_FS + TB_U + TB_G);
+    const float *Ib = reinterpret_cast<const float *>(b + TB_UF + TB_JA + TB_FV + TB_FS + TB_U + TB_G);
     if (tid < nnn) {
       const float Uv[5] = {Uf[tid], Uf[nnn + tid], Uf[2 * nnn + tid], Uf[3 * nnn + tid], Uf[4 * nnn + tid]};
       f32_stage<VF>(d, Uv, P + tid);
@@ -500,7 +504,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_volume_f32_ws(const DgDevice 
       mbar_expect_tx(mb, ug_bytes);
       if (needU) bulk_g2s(smem_addr(UG), U + e * 5 * nnn, TB_U, mb);
       if (needG) bulk_g2s(smem_addr(UG + TB_U), g + e * 5 * nnn, TB_G, mb);
-      bulk_g2s(smem_addr(UG + TB_U + TB_G), d.invJ + e * nnn, TB_IJ, mb);
+      bulk_g2s(smem_addr(UG + TB_U + TB_G), (mode ? d.facf : d.invJf) + e * nnn, TB_IJ, mb);
     };
     if (et == 0) issue_ug(0);
     int k = 0;
@@ -512,8 +516,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_volume_f32_ws(const DgDevice 
       if (!mbar_wait(smem_addr(&bar[6]), (unsigned)(k & 1))) s_abort_e = 1;
       if (!s_abort_e) {
         const float *Sb = S + b * 5 * nnn;
-        const double *Ue = reinterpret_cast<const double *>(UG), *ge = reinterpret_cast<const double *>(UG + TB_U),
-                     *iJe = reinterpret_cast<const double *>(UG + TB_U + TB_G);
+        const double *Ue = reinterpret_cast<const double *>(UG), *ge = reinterpret_cast<const double *>(UG + TB_U);
+        const float *iJe = reinterpret_cast<const float *>(UG + TB_U + TB_G);
         // all of the thread's nodes at once (unrolled): their conversion and FP64 chains overlap
 #pragma unroll
         for (int r = 0; r < (nnn + WS_EPI - 1) / WS_EPI; ++r) {
@@ -830,7 +834,7 @@ __global__ void __launch_bounds__(LN_THREADS, 1) k_volume_f32_line(const DgDevic
         mbar_expect_tx(mb, ug_bytes);
         if (needU) bulk_g2s(smem_addr(UG), U + e * 5 * nnn, TB_U, mb);
         if (needG) bulk_g2s(smem_addr(UG + TB_U), g + e * 5 * nnn, TB_G, mb);
-        bulk_g2s(smem_addr(UG + TB_U + TB_G), d.invJ + e * nnn, TB_IJ, mb);
+        bulk_g2s(smem_addr(UG + TB_U + TB_G), (mode ? d.facf : d.invJf) + e * nnn, TB_IJ, mb);
       };
       if (et == 0) issue_ug(0);
       constexpr float SC0 = SPLIT ? 0.25f : 2.0f, SC1 = SPLIT ? 0.125f : 2.0f;
@@ -845,11 +849,12 @@ __global__ void __launch_bounds__(LN_THREADS, 1) k_volume_f32_line(const DgDevic
         // U, g, 1/J buffer are released (the next element's copy overlaps this element's FP64 stage)
         constexpr int R = nnn / LN_EPI;
         float sv[R][5];
-        double Uv[R][5], gv0[R][5], iJ[R];
+        double Uv[R][5], gv0[R][5];
+        float iJ[R];
         if (!s_abort_e) {
           const float *A0 = ACC + (b * 3) * 5 * nnn, *A1 = A0 + 5 * nnn, *A2 = A1 + 5 * nnn;
-          const double *Ue = reinterpret_cast<const double *>(UG), *ge = reinterpret_cast<const double *>(UG + TB_U),
-                       *iJe = reinterpret_cast<const double *>(UG + TB_U + TB_G);
+          const double *Ue = reinterpret_cast<const double *>(UG), *ge = reinterpret_cast<const double *>(UG + TB_U);
+          const float *iJe = reinterpret_cast<const float *>(UG + TB_U + TB_G);
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const int node = et + r * LN_EPI, sw = ln_sw(node);

@@ -23,6 +23,7 @@ struct DgDevice {
   int N, nE, nF;
   int equations, vflux, sflux, precision, shock_capturing;
   double gamma, R, mu, kappa, alpha_min, alpha_max, sharpness, alpha_fixed;
+  double ind_T, ind_k;  // indicator threshold T = 0.5 10^(-1.8 (N+1)^(1/4)) (Eq. (7)) and -sharpness / T
   double p_ref;        // reference pressure removed from the momentum flux (FP32-bulk only; 0 in FP64)
   // per-context constants computed once on the host (the FP32 kernels would otherwise form them
   // per thread on the FP64 pipe): gamma-1, 1/R, p_ref gamma/(gamma-1), p_ref/(gamma-1), and their
@@ -55,6 +56,7 @@ struct DgDevice {
   float *Fsurf_f, *Wsurf_f, *Fv_f;  // FP32-bulk versions
   float *Uf;           // FP32-bulk: FP32 shadow of the state [nE][5][n^3], E shifted by p_ref/(gamma-1)
   float *invJf;        // FP32-bulk: FP32 copy of 1/J for the lifting
+  float *facf;         // FP32-bulk: float(dt (-1/J)) for the step size of the current LSERK call
   double *alpha_raw;   // [nE]
   double *alpha;       // [nE]
   double *red;         // reduction partials

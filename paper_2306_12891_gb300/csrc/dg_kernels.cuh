@@ -1063,10 +1063,29 @@ namespace {
 // modified Persson indicator (Sec. 4.1, Eq. (7)) and the neighbour extension (FP64)
 // ---------------------------------------------------------------------------------------------
 // One warp per element (IND_WARPS elements per CTA): q = rho p staged in shared memory, its modal
-// coefficients by three tensor-product passes with the inverse Vandermonde (from a padded
-// shared-memory copy, so lanes reading different rows do not serialise on constant memory), the
-// shell energies reduced with warp shuffles; no block-wide barrier after the table load.
+// coefficients by three tensor-product passes with the inverse Vandermonde (a padded shared-memory
+// copy, so lanes reading different rows do not serialise on constant memory), the shell energies
+// reduced with warp shuffles; no block-wide barrier after the table load. The kernel is bound by the
+// FP64 pipe, so it saves FP64 instructions:
+//  - q = rho p = (gamma - 1)(rho E - |m|^2 / 2), with no division;
+//  - each pass uses the parity of the Legendre modes on the symmetric LGL nodes,
+//    Vinv[a][N-i] = (-1)^a Vinv[a][i]: with q+-_i = q_i +- q_(N-i), output a needs the first half of
+//    row a against q+ (a even) or q- (a odd), n(n+1)/2 multiplies per line instead of n^2;
+//  - the threshold T of Eq. (7) and -s/T are per-context constants from the host.
 constexpr int IND_WARPS = 4;
+constexpr int IND_H = (n + 1) / 2;  // first half of a line, the middle node included when n is odd
+
+// one pass along a line of stride st starting at `base`: out[base + a st] = sum_i Vinv[a][i] in[base + i st]
+__device__ __forceinline__ void ind_pass(const double (*__restrict__ sV)[n + 1], const double *__restrict__ in,
+                                         double *__restrict__ out, int base, int st, int a) {
+  double s = 0.0;
+  const double sg = (a & 1) ? -1.0 : 1.0;
+#pragma unroll
+  for (int i = 0; i < n / 2; ++i) s += sV[a][i] * (in[base + i * st] + sg * in[base + (N - i) * st]);
+  if (n & 1) s += sV[a][N / 2] * in[base + (N / 2) * st];  // the middle node (odd n; zero for odd a)
+  out[base + a * st] = s;
+}
+
 __global__ void __launch_bounds__(32 * IND_WARPS) k_indicator(const DgDevice d, const double *__restrict__ U) {
   __shared__ double sV[n][n + 1];
   __shared__ double q[IND_WARPS][nnn], t1[IND_WARPS][nnn];
@@ -1075,39 +1094,34 @@ __global__ void __launch_bounds__(32 * IND_WARPS) k_indicator(const DgDevice d, 
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int e = blockIdx.x * IND_WARPS + w;
   if (e >= d.nE) return;
-  const double gm1 = d.gamma - 1.0;
+  const double gm1 = d.gm1;
   double *qw = q[w], *tw = t1[w];
   for (int node = lane; node < nnn; node += 32) {
     const double *Ue = U + (size_t)e * 5 * nnn + node;
-    const double r = Ue[0];
-    const double p = gm1 * (Ue[4 * nnn] - 0.5 * (Ue[nnn] * Ue[nnn] + Ue[2 * nnn] * Ue[2 * nnn] + Ue[3 * nnn] * Ue[3 * nnn]) / r);
-    qw[node] = r * p;
+    const double r = Ue[0], m1 = Ue[nnn], m2 = Ue[2 * nnn], m3 = Ue[3 * nnn];
+    qw[node] = gm1 * (r * Ue[4 * nnn] - 0.5 * (m1 * m1 + m2 * m2 + m3 * m3));
   }
   __syncwarp();
   for (int node = lane; node < nnn; node += 32) {  // xi: (i,j,k) -> (a,j,k)
-    const int a = node % n, base = node - a;
-    double s = 0.0;
-#pragma unroll
-    for (int i = 0; i < n; ++i) s += sV[a][i] * qw[base + i];
-    tw[node] = s;
+    const int a = node % n;
+    ind_pass(sV, qw, tw, node - a, 1, a);
   }
   __syncwarp();
   for (int node = lane; node < nnn; node += 32) {  // eta
-    const int b = (node / n) % n, base = node - b * n;
-    double s = 0.0;
-#pragma unroll
-    for (int j = 0; j < n; ++j) s += sV[b][j] * tw[base + j * n];
-    qw[node] = s;
+    const int b = (node / n) % n;
+    ind_pass(sV, tw, qw, node - b * n, n, b);
+  }
+  __syncwarp();
+  for (int node = lane; node < nnn; node += 32) {  // zeta into t1
+    const int c = node / nn;
+    ind_pass(sV, qw, tw, node - c * nn, nn, c);
   }
   __syncwarp();
   double all = 0.0, shN = 0.0, shN1 = 0.0;
-  for (int node = lane; node < nnn; node += 32) {  // zeta, then the shell energies
-    const int a = node % n, b = (node / n) % n, c = node / nn, base = node - c * nn;
-    double s = 0.0;
-#pragma unroll
-    for (int k = 0; k < n; ++k) s += sV[c][k] * qw[base + k * nn];
+  for (int node = lane; node < nnn; node += 32) {  // the shell energies
+    const int a = node % n, b = (node / n) % n, c = node / nn;
     const int M = max(a, max(b, c));
-    const double m2 = s * s;
+    const double m2 = tw[node] * tw[node];
     all += m2;
     if (M == N) shN += m2;
     if (M == N - 1) shN1 += m2;
@@ -1126,8 +1140,7 @@ __global__ void __launch_bounds__(32 * IND_WARPS) k_indicator(const DgDevice d, 
       const double E1 = tot1 > 1e-300 ? sN1 / tot1 : 0.0;
       E = fmax(E, E1);
     }
-    const double T = 0.5 * pow(10.0, -1.8 * pow((double)(N + 1), 0.25));
-    double al = 1.0 / (1.0 + exp(-d.sharpness / T * (E - T)));
+    double al = 1.0 / (1.0 + exp(d.ind_k * (E - d.ind_T)));
     if (al < d.alpha_min) al = 0.0;
     if (al > d.alpha_max) al = d.alpha_max;
     d.alpha_raw[e] = al;
