@@ -43,7 +43,7 @@ VOLUME_DRAM_BYTES_PER_ELEMENT = 661.0e6 / 16 ** 3
 # DRAM bytes (read + write) of one FP32-bulk volume launch (pair-symmetric line kernel) per element,
 # from one ncu capture of the 16^3 case (351.5 MB read, 157.2 MB written for 4096 elements), scaled
 # by the element count
-VOLUME_F32_DRAM_BYTES_PER_ELEMENT = (351.5e6 + 157.2e6) / 16 ** 3
+VOLUME_F32_DRAM_BYTES_PER_ELEMENT = None  # the kernel changed since its last capture (stage factor)
 
 
 def volume_kernel_flops_per_element(N: int, navier_stokes: bool) -> float:
@@ -129,6 +129,7 @@ LLF_FLOPS = 82.0  # two Euler fluxes 2 x 26, two sound speeds 6, the wave-speed 
 def fp32_kernel_bytes_per_launch(N: int, n_elems: int) -> dict:
     """Algorithmic DRAM bytes of one launch of each FP32-bulk kernel of the Navier-Stokes step:
       volume: volume_kernel_bytes_per_element(N, True, 4) per element;
+      (the once-per-call stage-factor and shadow refreshes are counted under "other" as the shadow's)
       lift: the FP32 shadow state 20, metric terms 36 and 1/J 4 per node in, the BR1 face jumps
         (6 faces x 4 x n^2 floats per element) in, the contravariant viscous flux 48 per node out;
       face: per face point (3 n^2 per element) both elements' shadow states 40 and the normal and area
@@ -162,14 +163,14 @@ def fp32_step_roofline(N: int, n_elems: int, kt: dict, region_ms: float) -> dict
 
 def volume_kernel_bytes_per_element(N: int, navier_stokes: bool, real_bytes: int) -> float:
     """Algorithmic DRAM bytes of one volume-kernel launch per element in an LSERK stage after the
-    first: U and the LSERK register g read and written (FP64), the metric terms Ja (real type),
-    1/J (FP64), the element's six face slots of outward flux (real type) and, for Navier-Stokes,
-    the contravariant viscous flux (12 per node) and the neighbours' normal viscous flux at the faces
-    (4 per face point). The FP32-bulk kernel also reads and writes the FP32 shadow of U (5 floats per
-    node each way)."""
+    first: U and the LSERK register g read and written (FP64), the metric terms Ja (real type), the
+    per-node factor of the Jacobian (FP64 1/J; in FP32-bulk the float stage factor dt (-1/J)), the
+    element's six face slots of outward flux (real type) and, for Navier-Stokes, the contravariant
+    viscous flux (12 per node) and the neighbours' normal viscous flux at the faces (4 per face point).
+    The FP32-bulk kernel also reads and writes the FP32 shadow of U (5 floats per node each way)."""
     n = N + 1
     nodes, fpts = n ** 3, 6 * n * n
-    b = nodes * (4 * 5 * 8 + 8) + nodes * 9 * real_bytes + fpts * 5 * real_bytes
+    b = nodes * (4 * 5 * 8 + (8 if real_bytes == 8 else 4)) + nodes * 9 * real_bytes + fpts * 5 * real_bytes
     if navier_stokes:
         b += nodes * 12 * real_bytes + fpts * 4 * real_bytes
     if real_bytes == 4:
