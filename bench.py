@@ -46,6 +46,12 @@ VOLUME_DRAM_BYTES_PER_ELEMENT = 661.0e6 / 16 ** 3
 VOLUME_F32_DRAM_BYTES_PER_ELEMENT = None  # the kernel changed since its last capture (stage factor)
 
 
+def scaled_traffic(bytes_per_element, n_elems: int, applies: bool = True):
+    """A captured per-element DRAM count scaled to a launch by the element count; None when there is no
+    capture of the current kernel (or it does not apply to this configuration)."""
+    return bytes_per_element * n_elems if (bytes_per_element is not None and applies) else None
+
+
 def volume_kernel_flops_per_element(N: int, navier_stokes: bool) -> float:
     """Algorithmic FP64 flops of one volume-kernel launch per element (FMA = 2 flops), counted
     from the formulas the kernel evaluates:
@@ -755,7 +761,7 @@ def run_gpu(args):
             gbs = b32 / (v32_ms / v32_n * 1e-3) / 1e9
             fp32["roofline"] = {"bound": "hbm", "kernel": "volume (FP32-bulk)", "achieved": gbs, "peak": HBM_GBS,
                                 "unit": "GB/s", "frac": gbs / HBM_GBS, "bytes_per_launch": b32,
-                                "traffic": VOLUME_F32_DRAM_BYTES_PER_ELEMENT * w.n_elems if w.N == 7 else None,
+                                "traffic": scaled_traffic(VOLUME_F32_DRAM_BYTES_PER_ELEMENT, w.n_elems, w.N == 7),
                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
         del s32
 
@@ -768,7 +774,7 @@ def run_gpu(args):
         bytes_launch = volume_kernel_bytes_per_element(w.N, True, 4) * w.n_elems
         roofline = {"bound": "hbm", "kernel": "volume (FP32-bulk)", "achieved": bytes_launch / vol_s / 1e9,
                     "peak": HBM_GBS, "unit": "GB/s", "frac": bytes_launch / vol_s / 1e9 / HBM_GBS,
-                    "traffic": VOLUME_F32_DRAM_BYTES_PER_ELEMENT * w.n_elems if w.N == 7 else None,
+                    "traffic": scaled_traffic(VOLUME_F32_DRAM_BYTES_PER_ELEMENT, w.n_elems, w.N == 7),
                     "bytes_per_launch": bytes_launch,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
     else:
@@ -777,7 +783,7 @@ def run_gpu(args):
         roofline = {"bound": "alu", "kernel": "volume (split-form flux differencing, FP64 pipe)",
                     "achieved": achieved / 1e12, "peak": peak_fp64 / 1e12, "unit": "TFLOP/s",
                     "frac": achieved / peak_fp64,
-                    "traffic": (VOLUME_DRAM_BYTES_PER_ELEMENT * w.n_elems if VOLUME_DRAM_BYTES_PER_ELEMENT else None),
+                    "traffic": scaled_traffic(VOLUME_DRAM_BYTES_PER_ELEMENT, w.n_elems),
                     "flops_per_launch": flops_launch, "peak_source": "measured FP64 FMA probe (dg_probe_fma), live"}
     state_bytes = U.numel() * 8
     if rank != 0:
