@@ -85,6 +85,11 @@ struct dg_ctx {
   int use_graphs = 1;
   cudaStream_t gstream = nullptr;
   cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+  // host-buffer entry point: the state's copies are split over library streams (one copy each), so
+  // that several copy engines move it at once
+  static constexpr int kCopyStreams = 4;
+  cudaStream_t cstream[kCopyStreams] = {};
+  cudaEvent_t cev[kCopyStreams + 1] = {};
   cudaGraphExec_t step_graph = nullptr;
   const double *graph_U = nullptr;
   double graph_dt = 0.0;
@@ -330,6 +335,10 @@ void dg_free(dg_ctx *c) {
   if (c->gev_in) cudaEventDestroy(c->gev_in);
   if (c->gev_out) cudaEventDestroy(c->gev_out);
   if (c->gstream) cudaStreamDestroy(c->gstream);
+  for (cudaStream_t st : c->cstream)
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : c->cev)
+    if (ev) cudaEventDestroy(ev);
   for (void *p : c->allocs) cudaFree(p);
   for (auto &pr : c->ev_pool) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   if (c->flag_host) cudaFreeHost(c->flag_host);
@@ -605,6 +614,32 @@ dg_status steps_impl(dg_ctx *c, double *U, double dt, int n_steps) {
   c->launches += c->graph_launches * n_steps;
   return DG_OK;
 }
+// one copy of `bytes` split into dg_ctx::kCopyStreams pieces on the library copy streams, ordered
+// after the work already on the context stream and before the work enqueued on it afterwards
+dg_status copy_split(dg_ctx *c, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind) {
+  constexpr int K = dg_ctx::kCopyStreams;
+  cudaError_t e = cudaSuccess;
+  if (!c->cstream[0]) {
+    for (int k = 0; k < K && !e; ++k) e = cudaStreamCreateWithFlags(&c->cstream[k], cudaStreamNonBlocking);
+    for (int k = 0; k <= K && !e; ++k) e = cudaEventCreateWithFlags(&c->cev[k], cudaEventDisableTiming);
+    if (e) return cuda_fail(c, e, "copy streams");
+  }
+  const size_t chunk = ((bytes + K - 1) / K + 255) / 256 * 256;
+  e = cudaEventRecord(c->cev[K], c->stream);
+  for (int k = 0; k < K && !e; ++k) {
+    const size_t off = (size_t)k * chunk;
+    if (off >= bytes) break;
+    const size_t len = std::min(chunk, bytes - off);
+    e = cudaStreamWaitEvent(c->cstream[k], c->cev[K], 0);
+    if (!e) e = cudaMemcpyAsync(static_cast<char *>(dst) + off, static_cast<const char *>(src) + off, len, kind,
+                                c->cstream[k]);
+    if (!e) e = cudaEventRecord(c->cev[k], c->cstream[k]);
+    if (!e) e = cudaStreamWaitEvent(c->stream, c->cev[k], 0);
+  }
+  if (e) return cuda_fail(c, e, kind == cudaMemcpyHostToDevice ? "H2D" : "D2H");
+  return DG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -632,11 +667,10 @@ dg_status dg_lserk_step_host(dg_ctx *c, double *U_host, double dt, double t) {
   if (!c || !U_host) return fail(c, DG_ERR_ARG, "dg_lserk_step_host: null array");
   if (!c->Ustage) DG_TRY(dev_alloc(c, &c->Ustage, c->n_state));
   const size_t bytes = sizeof(double) * c->n_state;
-  cudaError_t e = cudaMemcpyAsync(c->Ustage, U_host, bytes, cudaMemcpyHostToDevice, c->stream);
-  if (e) return cuda_fail(c, e, "H2D");
+  DG_TRY(copy_split(c, c->Ustage, U_host, bytes, cudaMemcpyHostToDevice));
   DG_TRY(dg_lserk_step(c, c->Ustage, dt, t));
-  e = cudaMemcpyAsync(U_host, c->Ustage, bytes, cudaMemcpyDeviceToHost, c->stream);
-  if (!e) e = cudaStreamSynchronize(c->stream);
+  DG_TRY(copy_split(c, U_host, c->Ustage, bytes, cudaMemcpyDeviceToHost));
+  const cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e) return cuda_fail(c, e, "D2H");
   return DG_OK;
 }
