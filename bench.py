@@ -43,7 +43,10 @@ VOLUME_DRAM_BYTES_PER_ELEMENT = 661.0e6 / 16 ** 3
 # DRAM bytes (read + write) of one FP32-bulk volume launch (pair-symmetric line kernel) per element,
 # from one ncu capture of the 16^3 case (351.5 MB read, 157.2 MB written for 4096 elements), scaled
 # by the element count
-VOLUME_F32_DRAM_BYTES_PER_ELEMENT = None  # the kernel changed since its last capture (stage factor)
+# DRAM bytes (read + write) of one FP32-bulk volume launch (pair-symmetric line kernel, stage factor) per
+# element, from one ncu capture at the full 32^3 size of the second stage of a step (3492.2 MB read,
+# 1625.3 MB written for 32768 elements)
+VOLUME_F32_DRAM_BYTES_PER_ELEMENT = (3492.2e6 + 1625.3e6) / 32 ** 3
 
 
 def scaled_traffic(bytes_per_element, n_elems: int, applies: bool = True):
