@@ -614,6 +614,13 @@ dg_status steps_impl(dg_ctx *c, double *U, double dt, int n_steps) {
   c->launches += c->graph_launches * n_steps;
   return DG_OK;
 }
+// state copy by the SMs through the host-device link, 16 bytes per thread and step; for page-locked host
+// memory, which the device addresses directly
+__global__ void k_copy16(const uint4 *__restrict__ src, uint4 *__restrict__ dst, size_t n16) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
 // one copy of `bytes` split into dg_ctx::kCopyStreams pieces on the library copy streams, ordered
 // after the work already on the context stream and before the work enqueued on it afterwards
 dg_status copy_split(dg_ctx *c, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind) {
@@ -638,6 +645,25 @@ dg_status copy_split(dg_ctx *c, void *dst, const void *src, size_t bytes, cudaMe
   }
   if (e) return cuda_fail(c, e, kind == cudaMemcpyHostToDevice ? "H2D" : "D2H");
   return DG_OK;
+}
+
+// a host <-> device copy of the state: page-locked host memory that the device can address is copied by
+// k_copy16 on the context stream (the SMs keep many 16-byte loads in flight over the host-device link);
+// other host memory, or an unaligned buffer, by copy engines (copy_split)
+dg_status copy_state_host(dg_ctx *c, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind) {
+  const void *host = kind == cudaMemcpyHostToDevice ? src : dst;
+  cudaPointerAttributes a{};
+  void *hdev = nullptr;
+  const cudaError_t qe = cudaPointerGetAttributes(&a, host);
+  if (qe != cudaSuccess) cudaGetLastError();  // the query's own error: not left behind for the caller
+  else if (a.type == cudaMemoryTypeHost && a.devicePointer && bytes % 16 == 0 &&
+           (reinterpret_cast<uintptr_t>(a.devicePointer) & 15u) == 0 &&
+           (reinterpret_cast<uintptr_t>(kind == cudaMemcpyHostToDevice ? dst : src) & 15u) == 0)
+    hdev = a.devicePointer;
+  if (!hdev) return copy_split(c, dst, src, bytes, kind);
+  const uint4 *from = static_cast<const uint4 *>(kind == cudaMemcpyHostToDevice ? hdev : src);
+  uint4 *to = static_cast<uint4 *>(kind == cudaMemcpyHostToDevice ? dst : hdev);
+  return launch(c, KC_OTHER, [&] { k_copy16<<<8 * 152, 256, 0, c->stream>>>(from, to, bytes / 16); });
 }
 
 }  // namespace
@@ -667,9 +693,9 @@ dg_status dg_lserk_step_host(dg_ctx *c, double *U_host, double dt, double t) {
   if (!c || !U_host) return fail(c, DG_ERR_ARG, "dg_lserk_step_host: null array");
   if (!c->Ustage) DG_TRY(dev_alloc(c, &c->Ustage, c->n_state));
   const size_t bytes = sizeof(double) * c->n_state;
-  DG_TRY(copy_split(c, c->Ustage, U_host, bytes, cudaMemcpyHostToDevice));
+  DG_TRY(copy_state_host(c, c->Ustage, U_host, bytes, cudaMemcpyHostToDevice));
   DG_TRY(dg_lserk_step(c, c->Ustage, dt, t));
-  DG_TRY(copy_split(c, U_host, c->Ustage, bytes, cudaMemcpyDeviceToHost));
+  DG_TRY(copy_state_host(c, U_host, c->Ustage, bytes, cudaMemcpyDeviceToHost));
   const cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e) return cuda_fail(c, e, "D2H");
   return DG_OK;

@@ -205,9 +205,12 @@ def test_host_buffer_step_equals_device_step(env):
     gpu = dg.DG(w.N, xyz, faces, **w.physics())
     U = torch.from_numpy(U0).cuda()
     gpu.lserk_step(U, 1e-3)
-    Uh = torch.from_numpy(U0.copy()).pin_memory()
+    Uh = torch.from_numpy(U0.copy()).pin_memory()  # page-locked: copied by the SMs over the host link
     gpu.lserk_step_host(Uh, 1e-3)
     assert torch.equal(Uh, U.cpu())
+    Up = torch.from_numpy(U0.copy())  # pageable: copied by the copy engines, four streams
+    gpu.lserk_step_host(Up, 1e-3)
+    assert torch.equal(Up, U.cpu())
 
 
 # ------------------------------------------------------------------ full-size workloads, sampled outputs
