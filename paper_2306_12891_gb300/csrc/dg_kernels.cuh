@@ -53,6 +53,12 @@ __constant__ double c_Dq[nn];     // D_im / 4 (scaled mass flux), zero diagonal
 __constant__ double c_De[nn];     // D_im / 8 (scaled momentum / energy flux), zero diagonal
 __constant__ double c_w[n], c_invw[n], c_xi[n], c_xh[n + 1];
 __constant__ double c_ihx[n];  // 1 / (xi_i - xi_{i-1}), i = 1..N (minmod slopes)
+// even-odd halves of the zero-diagonal D (n even, h = n/2): the LGL D is centro-antisymmetric,
+// D_{N-i,N-m} = -D_im, so y = D' f splits into VP (f_m + f_{N-m}) and VM (f_m - f_{N-m}), m < h:
+// VP_im = (D'_im + D'_{i,N-m}) / 2, VM_im = (D'_im - D'_{i,N-m}) / 2, y_i = A_i + B_i, y_{N-i} = B_i - A_i
+constexpr int EO_H = (n % 2 == 0) ? n / 2 : 1;
+__constant__ double c_VP[EO_H * EO_H], c_VM[EO_H * EO_H];
+__constant__ float f_VP[EO_H * EO_H], f_VM[EO_H * EO_H];
 __constant__ double c_Vinv[nn];
 __constant__ float f_D[nn], f_D2[nn], f_Dq[nn], f_De[nn];
 __constant__ float f_w[n], f_invw[n], f_xi[n], f_xh[n + 1], f_ihx[n];
@@ -69,6 +75,8 @@ template <> struct Tab<double> {
   static __device__ __forceinline__ double xi(int k) { return c_xi[k]; }
   static __device__ __forceinline__ double xh(int k) { return c_xh[k]; }
   static __device__ __forceinline__ double ihx(int k) { return c_ihx[k]; }
+  static __device__ __forceinline__ double VP(int k) { return c_VP[k]; }
+  static __device__ __forceinline__ double VM(int k) { return c_VM[k]; }
 };
 template <> struct Tab<float> {
   static __device__ __forceinline__ float D(int k) { return f_D[k]; }
@@ -80,6 +88,8 @@ template <> struct Tab<float> {
   static __device__ __forceinline__ float xi(int k) { return f_xi[k]; }
   static __device__ __forceinline__ float xh(int k) { return f_xh[k]; }
   static __device__ __forceinline__ float ihx(int k) { return f_ihx[k]; }
+  static __device__ __forceinline__ float VP(int k) { return f_VP[k]; }
+  static __device__ __forceinline__ float VM(int k) { return f_VM[k]; }
 };
 
 // per-context constants in the arithmetic type (precomputed on the host)
@@ -755,13 +765,30 @@ __device__ __forceinline__ void line_viscous(const R *__restrict__ Fvd, int gb, 
     R f[n];
 #pragma unroll
     for (int m = 0; m < n; ++m) f[m] = __ldg(Fvd + q * nnn + gb + m * gs);
+    if constexpr (n % 2 == 0) {  // even-odd: n^2/2 + 2n operations per line instead of n^2
+      R ev[EO_H], od[EO_H];
 #pragma unroll
-    for (int i = 0; i < n; ++i) {
-      R s = R(0);
+      for (int m = 0; m < EO_H; ++m) { ev[m] = f[m] + f[N - m]; od[m] = f[m] - f[N - m]; }
 #pragma unroll
-      for (int m = 0; m < n; ++m)
-        if (m != i) s += Tab<R>::D(i * n + m) * f[m];
-      Ac[(1 + q) * PS + pb + i * ps] -= s;
+      for (int i = 0; i < EO_H; ++i) {
+        R a = R(0), b = R(0);
+#pragma unroll
+        for (int m = 0; m < EO_H; ++m) {
+          a += Tab<R>::VP(i * EO_H + m) * ev[m];
+          b += Tab<R>::VM(i * EO_H + m) * od[m];
+        }
+        Ac[(1 + q) * PS + pb + i * ps] -= a + b;
+        Ac[(1 + q) * PS + pb + (N - i) * ps] -= b - a;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        R s = R(0);
+#pragma unroll
+        for (int m = 0; m < n; ++m)
+          if (m != i) s += Tab<R>::D(i * n + m) * f[m];
+        Ac[(1 + q) * PS + pb + i * ps] -= s;
+      }
     }
   }
 }
@@ -1252,6 +1279,17 @@ cudaError_t upload(const DgTables &t) {
     }
   for (int i = 0; i < n; ++i) { fw[i] = (float)t.w[i]; finvw[i] = (float)t.invw[i]; fxi[i] = (float)t.xi[i]; }
   for (int i = 0; i <= n; ++i) fxh[i] = (float)t.xh[i];
+  double vp[EO_H * EO_H] = {0.0}, vm[EO_H * EO_H] = {0.0};
+  float fvp[EO_H * EO_H] = {0.0f}, fvm[EO_H * EO_H] = {0.0f};
+  if (n % 2 == 0)
+    for (int i = 0; i < EO_H; ++i)
+      for (int m = 0; m < EO_H; ++m) {
+        const double a = (i == m) ? 0.0 : t.D[i * n + m], b = (i == N - m) ? 0.0 : t.D[i * n + (N - m)];
+        vp[i * EO_H + m] = 0.5 * (a + b);
+        vm[i * EO_H + m] = 0.5 * (a - b);
+        fvp[i * EO_H + m] = (float)vp[i * EO_H + m];
+        fvm[i * EO_H + m] = (float)vm[i * EO_H + m];
+      }
   double ihx[n];
   float fihx[n];
   ihx[0] = 0.0;
@@ -1259,6 +1297,10 @@ cudaError_t upload(const DgTables &t) {
   for (int i = 0; i < n; ++i) fihx[i] = (float)ihx[i];
   cudaError_t err = cudaSuccess;
   err = err ? err : cudaMemcpyToSymbol(c_ihx, ihx, sizeof(double) * n);
+  err = err ? err : cudaMemcpyToSymbol(c_VP, vp, sizeof(vp));
+  err = err ? err : cudaMemcpyToSymbol(c_VM, vm, sizeof(vm));
+  err = err ? err : cudaMemcpyToSymbol(f_VP, fvp, sizeof(fvp));
+  err = err ? err : cudaMemcpyToSymbol(f_VM, fvm, sizeof(fvm));
   err = err ? err : cudaMemcpyToSymbol(f_ihx, fihx, sizeof(float) * n);
   err = err ? err : cudaMemcpyToSymbol(c_D, t.D, sizeof(double) * nn);
   err = err ? err : cudaMemcpyToSymbol(c_D2, D2, sizeof(double) * nn);
