@@ -59,6 +59,8 @@ __constant__ double c_ihx[n];  // 1 / (xi_i - xi_{i-1}), i = 1..N (minmod slopes
 constexpr int EO_H = (n % 2 == 0) ? n / 2 : 1;
 __constant__ double c_VP[EO_H * EO_H], c_VM[EO_H * EO_H];
 __constant__ float f_VP[EO_H * EO_H], f_VM[EO_H * EO_H];
+// the same halves of the full D (diagonal included; D_NN = -D_00 keeps the symmetry), for the lifting
+__constant__ double c_FP[EO_H * EO_H], c_FM[EO_H * EO_H];
 __constant__ double c_Vinv[nn];
 __constant__ float f_D[nn], f_D2[nn], f_Dq[nn], f_De[nn];
 __constant__ float f_w[n], f_invw[n], f_xi[n], f_xh[n + 1], f_ihx[n];
@@ -587,10 +589,12 @@ __device__ __forceinline__ void lift_prim(const R Uv[5], R gm1, R iR, R pref, R 
 // one node's BR1 gradients and contravariant viscous flux: W = the element's lifted quantities
 // [4][nnn] (shared memory), Jae its metric terms [3 d][3 c][nnn], Wse its BR1 face jumps [6][4][nn],
 // iJ this node's 1/J; writes the element's Fv [3 d][4][nnn] at `node` (out = the element's Fv)
-template <typename R>
+template <typename R, bool PRE = false>
 __device__ __forceinline__ void lift_node(const DgDevice &d, int node, const R *__restrict__ W,
                                           const R (*__restrict__ sD)[n + 1], const R *__restrict__ Jae,
-                                          const R *__restrict__ Wse, R iJ, R mu, R kappa, R *__restrict__ out) {
+                                          const R *__restrict__ Wse, R iJ, R mu, R kappa, R *__restrict__ out,
+                                          const R *__restrict__ S = nullptr) {
+  // PRE: the reference derivatives D_dd w_q of this element come precomputed in S [3 dd][4 q][nnn]
   const int ijk[3] = {node % n, (node / n) % n, node / nn};
   R Ja[3][3];
 #pragma unroll
@@ -608,8 +612,12 @@ __device__ __forceinline__ void lift_node(const DgDevice &d, int node, const R *
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       R s = R(0);
+      if constexpr (PRE) {
+        s = S[(dd * 4 + q) * nnn + node];
+      } else {
 #pragma unroll
-      for (int m = 0; m < n; ++m) s += sD[id][m] * W[q * nnn + base + m * st];
+        for (int m = 0; m < n; ++m) s += sD[id][m] * W[q * nnn + base + m * st];
+      }
       g[q][0] += Ja[dd][0] * s;
       g[q][1] += Ja[dd][1] * s;
       g[q][2] += Ja[dd][2] * s;
@@ -678,6 +686,78 @@ __global__ void __launch_bounds__(LIFT_THREADS, lift_min_blocks<R>()) k_lift(con
     const R iJ = kShift<R> ? (R)d.invJf[(size_t)e * nnn + node] : (R)d.invJ[(size_t)e * nnn + node];
     lift_node<R>(d, node, &W[le][0][0], sD, Buf<R>::Ja(d) + (size_t)e * 9 * nnn,
                  Buf<R>::Wsurf(d) + (size_t)e * 6 * 4 * nn, iJ, mu, kappa, Buf<R>::Fv(d) + (size_t)e * 12 * nnn);
+  }
+}
+
+// FP64 lifting with the reference derivatives formed along lines (n even): one thread per line of the
+// element(s) applies D to all four lifted quantities with the even-odd halves of D (the LGL D is
+// centro-antisymmetric), n^2/2 + 2n operations per line and quantity instead of the n^2 of n node-wise
+// sweeps; the derivatives go to shared memory, and the node-wise part (metric contraction, surface
+// terms, viscous flux, contravariant projection) is lift_node's. Dynamic shared memory:
+// W [EPB][4][nnn] and S [EPB][3][4][nnn] doubles.
+constexpr size_t LIFT_LINES_SMEM = sizeof(double) * LIFT_EPB * 16 * nnn;
+__global__ void __launch_bounds__(LIFT_THREADS, lift_min_blocks<double>()) k_lift_lines(const DgDevice d,
+                                                                                      const double *__restrict__ U) {
+  if constexpr (n % 2 == 0) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    double *W = reinterpret_cast<double *>(sm_raw);  // [EPB][4][nnn]
+    double *S = W + LIFT_EPB * 4 * nnn;              // [EPB][12][nnn]
+    __shared__ double sD[n][n + 1];
+    for (int t = threadIdx.x; t < nn; t += blockDim.x) sD[t / n][t % n] = c_D[t];
+    const int e0 = blockIdx.x * LIFT_EPB;
+    const double gm1 = d.gm1, iR = d.iR;
+    for (int t = threadIdx.x; t < LIFT_EPB * nnn; t += blockDim.x) {
+      const int le = t / nnn, node = t % nnn, e = e0 + le;
+      if (e >= d.nE) continue;
+      double Uv[5], Wn[4];
+      load_state<double>(d, U, e, node, Uv);
+      lift_prim<double>(Uv, gm1, iR, 0.0, Wn);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) W[(le * 4 + q) * nnn + node] = Wn[q];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < LIFT_EPB * 3 * nn; t += blockDim.x) {
+      const int le = t / (3 * nn), r = t % (3 * nn), dir = r / nn, line = r % nn;
+      if (e0 + le >= d.nE) continue;
+      const int a = line % n, b = line / n;
+      const int base = dir == 0 ? n * (a + n * b) : dir == 1 ? a + nn * b : a + n * b;
+      const int st = dir == 0 ? 1 : dir == 1 ? n : nn;
+      const double *We = W + le * 4 * nnn;
+      double *Se = S + (le * 12 + dir * 4) * nnn;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        double ev[EO_H], od[EO_H];
+#pragma unroll
+        for (int m = 0; m < EO_H; ++m) {
+          const double f0 = We[q * nnn + base + m * st], f1 = We[q * nnn + base + (N - m) * st];
+          ev[m] = f0 + f1;
+          od[m] = f0 - f1;
+        }
+#pragma unroll
+        for (int i = 0; i < EO_H; ++i) {
+          double pa = 0.0, pb = 0.0;
+#pragma unroll
+          for (int m = 0; m < EO_H; ++m) {
+            pa += c_FP[i * EO_H + m] * ev[m];
+            pb += c_FM[i * EO_H + m] * od[m];
+          }
+          Se[q * nnn + base + i * st] = pa + pb;
+          Se[q * nnn + base + (N - i) * st] = pb - pa;
+        }
+      }
+    }
+    __syncthreads();
+    const double mu = d.mu, kappa = d.kappa;
+#pragma unroll
+    for (int rr = 0; rr < (LIFT_EPB * nnn + LIFT_THREADS - 1) / LIFT_THREADS; ++rr) {
+      const int t = threadIdx.x + rr * LIFT_THREADS;
+      if (t >= LIFT_EPB * nnn) continue;
+      const int le = t / nnn, node = t % nnn, e = e0 + le;
+      if (e >= d.nE) continue;
+      lift_node<double, true>(d, node, W + le * 4 * nnn, sD, d.Ja + (size_t)e * 9 * nnn,
+                              d.Wsurf + (size_t)e * 6 * 4 * nn, d.invJ[(size_t)e * nnn + node], mu, kappa,
+                              d.Fv + (size_t)e * 12 * nnn, S + le * 12 * nnn);
+    }
   }
 }
 
@@ -1279,7 +1359,7 @@ cudaError_t upload(const DgTables &t) {
     }
   for (int i = 0; i < n; ++i) { fw[i] = (float)t.w[i]; finvw[i] = (float)t.invw[i]; fxi[i] = (float)t.xi[i]; }
   for (int i = 0; i <= n; ++i) fxh[i] = (float)t.xh[i];
-  double vp[EO_H * EO_H] = {0.0}, vm[EO_H * EO_H] = {0.0};
+  double vp[EO_H * EO_H] = {0.0}, vm[EO_H * EO_H] = {0.0}, fp_[EO_H * EO_H] = {0.0}, fm_[EO_H * EO_H] = {0.0};
   float fvp[EO_H * EO_H] = {0.0f}, fvm[EO_H * EO_H] = {0.0f};
   if (n % 2 == 0)
     for (int i = 0; i < EO_H; ++i)
@@ -1289,6 +1369,8 @@ cudaError_t upload(const DgTables &t) {
         vm[i * EO_H + m] = 0.5 * (a - b);
         fvp[i * EO_H + m] = (float)vp[i * EO_H + m];
         fvm[i * EO_H + m] = (float)vm[i * EO_H + m];
+        fp_[i * EO_H + m] = 0.5 * (t.D[i * n + m] + t.D[i * n + (N - m)]);
+        fm_[i * EO_H + m] = 0.5 * (t.D[i * n + m] - t.D[i * n + (N - m)]);
       }
   double ihx[n];
   float fihx[n];
@@ -1301,6 +1383,8 @@ cudaError_t upload(const DgTables &t) {
   err = err ? err : cudaMemcpyToSymbol(c_VM, vm, sizeof(vm));
   err = err ? err : cudaMemcpyToSymbol(f_VP, fvp, sizeof(fvp));
   err = err ? err : cudaMemcpyToSymbol(f_VM, fvm, sizeof(fvm));
+  err = err ? err : cudaMemcpyToSymbol(c_FP, fp_, sizeof(fp_));
+  err = err ? err : cudaMemcpyToSymbol(c_FM, fm_, sizeof(fm_));
   err = err ? err : cudaMemcpyToSymbol(f_ihx, fihx, sizeof(float) * n);
   err = err ? err : cudaMemcpyToSymbol(c_D, t.D, sizeof(double) * nn);
   err = err ? err : cudaMemcpyToSymbol(c_D2, D2, sizeof(double) * nn);
@@ -1366,8 +1450,18 @@ void launch_lift(const DgDevice &d, const double *U, cudaStream_t s) {
     return;
   }
   const unsigned grid = (d.nE + LIFT_EPB - 1) / LIFT_EPB;
-  if (d.precision == 1) k_lift<float><<<grid, LIFT_THREADS, 0, s>>>(d, U);
-  else k_lift<double><<<grid, LIFT_THREADS, 0, s>>>(d, U);
+  if (d.precision == 1) {
+    k_lift<float><<<grid, LIFT_THREADS, 0, s>>>(d, U);
+  } else if (n % 2 == 0) {
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaFuncSetAttribute(k_lift_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LIFT_LINES_SMEM);
+      attr_set = true;
+    }
+    k_lift_lines<<<grid, LIFT_THREADS, LIFT_LINES_SMEM, s>>>(d, U);
+  } else {
+    k_lift<double><<<grid, LIFT_THREADS, 0, s>>>(d, U);
+  }
 }
 
 template <typename R, int VF, bool SC>

@@ -211,6 +211,27 @@ def test_host_buffer_step_equals_device_step(env):
     Up = torch.from_numpy(U0.copy())  # pageable: copied by the copy engines, four streams
     gpu.lserk_step_host(Up, 1e-3)
     assert torch.equal(Up, U.cpu())
+    # page-locked but not 16-byte aligned (a view one double in): the copy engines again
+    big = torch.zeros(U0.size + 1, dtype=torch.float64).pin_memory()
+    Uo = big[1:].view(U0.shape)
+    Uo.copy_(torch.from_numpy(U0))
+    gpu.lserk_step_host(Uo, 1e-3)
+    assert torch.equal(Uo, U.cpu())
+
+
+def test_host_buffer_step_with_a_size_not_a_multiple_of_16_bytes(env):
+    """N = 2 on three elements: 405 doubles, so the state is not a whole number of 16-byte words."""
+    dg, orc, torch = env
+    N = 2
+    xyz, faces = W.box_mesh(N, (3, 1, 1), mapping=_generic_map)
+    U0 = jumpy(W.random_smooth_state(xyz, seed=4, amp=0.1), seed=5)
+    assert (U0.size * 8) % 16 != 0
+    gpu = dg.DG(N, xyz, faces, equations="ns", vflux="pirozzoli", sflux="roe", mu=0.02)
+    U = torch.from_numpy(U0).cuda()
+    gpu.lserk_step(U, 1e-4)
+    Uh = torch.from_numpy(U0.copy()).pin_memory()
+    gpu.lserk_step_host(Uh, 1e-4)
+    assert torch.equal(Uh, U.cpu())
 
 
 # ------------------------------------------------------------------ full-size workloads, sampled outputs
