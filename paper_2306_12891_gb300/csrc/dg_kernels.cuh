@@ -689,7 +689,7 @@ __global__ void __launch_bounds__(LIFT_THREADS, lift_min_blocks<R>()) k_lift(con
   }
 }
 
-// FP64 lifting with the reference derivatives formed along lines (n even): one thread per line of the
+// FP64 lifting with the reference derivatives formed along lines (used at N = 7): one thread per line of the
 // element(s) applies D to all four lifted quantities with the even-odd halves of D (the LGL D is
 // centro-antisymmetric), n^2/2 + 2n operations per line and quantity instead of the n^2 of n node-wise
 // sweeps; the derivatives go to shared memory, and the node-wise part (metric contraction, surface
@@ -1452,7 +1452,7 @@ void launch_lift(const DgDevice &d, const double *U, cudaStream_t s) {
   const unsigned grid = (d.nE + LIFT_EPB - 1) / LIFT_EPB;
   if (d.precision == 1) {
     k_lift<float><<<grid, LIFT_THREADS, 0, s>>>(d, U);
-  } else if (n % 2 == 0) {
+  } else if (n == 8) {  // measured faster at N = 7 (7.32 -> 7.00 ms at 32^3); slower at N = 5 (+3 %)
     static bool attr_set = false;
     if (!attr_set) {
       cudaFuncSetAttribute(k_lift_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LIFT_LINES_SMEM);
