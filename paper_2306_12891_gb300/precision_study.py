@@ -9,7 +9,9 @@ dissipation rate -dKE/dt (from the right-hand side through dg_invariants) are re
         [--out precision.json]
 
 The FP64 path stands in for the FP64 oracle at this size: it matches the oracle to rounding on
-the same physics (tests/test_gpu_parity.py), while the oracle cannot run 1000 steps of 56.6M DOF.
+the same physics, right-hand side by right-hand side (tests/test_gpu_parity.py) and over 500 steps of
+the same workload on 4^3 elements (tests/test_gpu_long_run.py, within the oracle's own one-ulp
+spread), while the oracle cannot run 1000 steps of 56.6M DOF.
 """
 from __future__ import annotations
 
