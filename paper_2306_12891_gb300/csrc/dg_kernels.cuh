@@ -638,8 +638,10 @@ __device__ __forceinline__ void lift_node(const DgDevice &d, int node, const R *
       }
     }
   }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) { g[q][0] *= iJ; g[q][1] *= iJ; g[q][2] *= iJ; }
+  // g holds J grad w; the flux below is linear in grad w, so 1/J goes into mu and kappa (two
+  // multiplies per node instead of twelve)
+  mu *= iJ;
+  kappa *= iJ;
   // Navier-Stokes-Fourier flux in Cartesian direction c: (tau_xc, tau_yc, tau_zc, u.tau_c + kappa dT/dx_c)
   const R u = W[node], v = W[nnn + node], w = W[2 * nnn + node];
   const R div = g[0][0] + g[1][1] + g[2][2];
@@ -1147,10 +1149,11 @@ __global__ void __launch_bounds__(vol_threads<R, SC>(), vol_min_blocks<R, SC>())
 #pragma unroll
       for (int v = 0; v < 5; ++v) out[gi + v * nnn] = miJ * to_double(s[v]);
     } else {
+      const double fac = dt * miJ;  // the stage increment dt Ut = (dt (-1/J)) s: one multiply per node
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const double ut = miJ * to_double(s[v]);
-        const double gv = first ? dt * ut : A * g[gi + v * nnn] + dt * ut;
+        const double du = fac * to_double(s[v]);
+        const double gv = first ? du : A * g[gi + v * nnn] + du;
         g[gi + v * nnn] = gv;
         const double un = U[gi + v * nnn] + B * gv;
         out[gi + v * nnn] = un;
