@@ -8,9 +8,11 @@ paper's performance index, Sec. 2 Eq. (1), with #cores := #GPUs), plus the PID i
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 For N > 1 (launched by torch.distributed.run) every rank runs an independent replica of the
-workload (the path is not sharded in this build); value = total DOF-stage updates / max time.
-`--impl reference` times the FP64 CPU oracle (single-threaded) on a bounded sample of the same
-workload instead.
+workload (the solver keeps each mesh on one GPU); value = total DOF-stage updates / max time.
+`--impl reference` times the FP64 CPU oracle instead, one process per host core, each on a bounded
+sub-box of the same workload. The default line also carries the FP32-bulk form, the adjoint, the
+wall model, the shock-capturing workload's 200 steps, the other named workloads and the oracle's
+host rate (each block can be switched off for profiling runs).
 """
 from __future__ import annotations
 

@@ -33,7 +33,7 @@ typedef enum {
   DG_ERR_JACOBIAN = -3,     /* J <= 0 or not finite at some node */
   DG_ERR_CUDA = -4,         /* a CUDA runtime call failed (text in dg_last_error) */
   DG_ERR_NONPHYSICAL = -5,  /* rho <= 0, p <= 0 or a non-finite value met by a kernel */
-  DG_ERR_UNSUPPORTED = -6,  /* valid request this build does not implement */
+  DG_ERR_UNSUPPORTED = -6,  /* valid request the library does not implement */
   DG_ERR_OOM = -7           /* device allocation failed */
 } dg_status;
 

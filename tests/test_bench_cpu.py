@@ -1,6 +1,6 @@
 """Host-side pieces of bench.py that need no GPU: the algorithmic counts and the roofline objects it
 assembles from kernel timings (so that a missing capture or an odd timing dict cannot break the JSON
-line on the GPU machine)."""
+line)."""
 import bench
 
 

@@ -1,4 +1,4 @@
-"""The multi-GPU path of bench.py is replicas only (the hot path is not sharded in this build): every
+"""The multi-GPU path of bench.py is replicas only (the solver keeps each mesh on one GPU): every
 rank runs the whole workload, the ranks meet at barriers around the timed region, and the reported
 value is all ranks' units divided by the slowest rank's time. This exercises that host logic with
 world_size 2 on the gloo backend (CPU processes, no GPU)."""
