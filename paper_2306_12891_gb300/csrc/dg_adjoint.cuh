@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(LIFT_THREADS) k_adj_visc(const DgDevice d, con
   __shared__ double sD[n][n + 1];
   for (int t = threadIdx.x; t < nn; t += blockDim.x) sD[t / n][t % n] = c_D[t];
   const int e0 = blockIdx.x * LIFT_EPB;
-  const double gm1 = d.gamma - 1.0, iR = 1.0 / d.R, mu = d.mu, kappa = d.kappa;
+  const double gm1 = d.gamma - 1.0, iR = 1.0 / d.R;
   for (int t = threadIdx.x; t < LIFT_EPB * nnn; t += blockDim.x) {
     const int le = t / nnn, node = t % nnn, e = e0 + le;
     if (e >= d.nE) continue;
@@ -392,9 +392,10 @@ __global__ void __launch_bounds__(LIFT_THREADS) k_adj_visc(const DgDevice d, con
         }
       }
     }
+    // g holds J grad w; tau, the heat flux and their transposes are linear in grad w, so 1/J goes
+    // into mu and kappa (which then also carry the 1/J of H below)
     const double iJ = d.invJ[(size_t)e * nnn + node];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) { g[q][0] *= iJ; g[q][1] *= iJ; g[q][2] *= iJ; }
+    const double mu = d.mu * iJ, kappa = d.kappa * iJ;
     const double u[3] = {W[node], W[nnn + node], W[2 * nnn + node]};
     const double div = g[0][0] + g[1][1] + g[2][2];
     double tau[3][3];
@@ -428,7 +429,7 @@ __global__ void __launch_bounds__(LIFT_THREADS) k_adj_visc(const DgDevice d, con
     for (int dd = 0; dd < 3; ++dd)
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        H[(dd * 4 + q) * nnn] = iJ * (Ja[dd][0] * Gm[q][0] + Ja[dd][1] * Gm[q][1] + Ja[dd][2] * Gm[q][2]);
+        H[(dd * 4 + q) * nnn] = Ja[dd][0] * Gm[q][0] + Ja[dd][1] * Gm[q][1] + Ja[dd][2] * Gm[q][2];
 #pragma unroll
     for (int k = 0; k < 3; ++k) Os[(le * 3 + k) * nnn + node] = om[k];
   }

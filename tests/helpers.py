@@ -261,3 +261,31 @@ def full_size_ulp_spread(name, extra, sample, base, count=3, seed=20230622):
     for o in outs:
         spread = np.maximum(spread, per_var_max(o - base))
     return spread
+
+
+def _saved_state_oracle_rhs(args):
+    """Spawned worker: the oracle's right-hand side of a named full-size workload at a state saved in
+    a .npy file, on a sample of elements, with the mesh points and the state moved by one ulp (seed)."""
+    name, path, sample, seed = args
+    import oracle
+    from paper_2306_12891_gb300 import workloads as W
+
+    w = W.WORKLOADS[name]
+    xyz, faces = w.mesh()
+    U = np.load(path)
+    period = np.asarray(w.hi) - np.asarray(w.lo)
+    xyz, U = mesh_ulp_perturb(xyz, seed, period), ulp_perturb(U, np.random.default_rng(seed))
+    return oracle.Oracle(w.N, xyz, faces, **w.physics()).rhs(U, mask=sample)[sample]
+
+
+def saved_state_ulp_spread(name, path, sample, base, count=3, seed=20230622):
+    """ulp_spread of a full-size workload's sampled right-hand side at a saved state (spawned processes)."""
+    import multiprocessing
+
+    ctx = multiprocessing.get_context("spawn")
+    with ctx.Pool(count) as pool:
+        outs = pool.map(_saved_state_oracle_rhs, [(name, path, list(sample), seed + k) for k in range(count)])
+    spread = np.zeros(5)
+    for o in outs:
+        spread = np.maximum(spread, per_var_max(o - base))
+    return spread

@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 from helpers import (TOL, check_fp64, face_jump_magnitude, flux_scale, full_size_ulp_spread, parity,
-                     subcell_range_magnitude, ulp_spread)
+                     saved_state_ulp_spread, subcell_range_magnitude, ulp_spread)
 from paper_2306_12891_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -267,6 +267,44 @@ def test_full_size_rhs_sampled(env, name, extra):
         jump = jump + subcell_range_magnitude(U0[sample], ref.Ja[sample])
     scale = flux_scale(U0[sample], ref.Ja[sample], ref.J[sample], orc.dmatrix(w.N), jump=jump)
     check_fp64(f"full-size {name} {extra}", Ut[sample], Ut_ref[sample], spread, scale)
+
+
+def test_full_size_shocked_blast_indicator_and_fv_rhs(env, tmp_path):
+    """The shock-capturing workload where it does FV work: the blast at 64^3 advanced on the GPU for
+    its 200 LSERK steps (dt from the CFL condition every 20 steps), when the indicator flags a shell of
+    elements around the shock. At that state: alpha of every element against the oracle's indicator,
+    and the right-hand side of sampled troubled and untroubled elements against the oracle (the FV
+    subcell operator on real troubled elements, not a fixed alpha)."""
+    dg, orc, torch = env
+    name = "blast_euler_fv_n5_64x64x64"
+    w = W.WORKLOADS[name]
+    xyz, faces = w.mesh()
+    gpu = dg.DG(w.N, xyz, faces, **w.physics())
+    U = torch.from_numpy(w.initial_state(xyz)).cuda()
+    for _ in range(w.steps // 20):
+        gpu.lserk_steps(U, gpu.max_dt(U, w.cfl), 20)
+    gpu.check()
+    alpha = gpu.indicator(U).cpu().numpy()
+    Ut = gpu.rhs(U).cpu().numpy()
+    Uh = U.cpu().numpy()
+    ref = orc.Oracle(w.N, xyz, faces, **w.physics())
+    _, alpha_ref = ref.indicator(Uh)
+    troubled = np.flatnonzero(alpha_ref > 0)
+    print(f"SHOCKED blast: troubled fraction {troubled.size / w.n_elems:.4f}, "
+          f"max |alpha - alpha_oracle| {np.abs(alpha - alpha_ref).max():.2e}")
+    assert 0.02 < troubled.size / w.n_elems < 0.3
+    np.testing.assert_allclose(alpha, alpha_ref, rtol=0, atol=1e-12)
+    rng = np.random.default_rng(20230625)
+    calm = np.flatnonzero(alpha_ref == 0)
+    sample = sorted(set(rng.choice(troubled, 12, replace=False)) | set(rng.choice(calm, 4, replace=False)))
+    Ut_ref = ref.rhs(Uh, mask=sample)[sample]
+    path = str(tmp_path / "U.npy")
+    np.save(path, Uh)
+    spread = saved_state_ulp_spread(name, path, sample, Ut_ref)
+    jump = face_jump_magnitude(Uh, faces, w.N, ref.Ja, elements=sample)[sample]
+    jump = jump + subcell_range_magnitude(Uh[sample], ref.Ja[sample])
+    scale = flux_scale(Uh[sample], ref.Ja[sample], ref.J[sample], orc.dmatrix(w.N), jump=jump)
+    check_fp64("shocked blast 64^3 after 200 steps, sampled elements", Ut[sample], Ut_ref, spread, scale)
 
 
 def test_full_size_lserk_step_matches_stagewise_definition(env):
