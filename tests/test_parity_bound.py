@@ -70,3 +70,21 @@ def test_parity_bound_is_a_rounding_bound(oracle_mod, tag, N, w, seed, phys):
     print(f"BOUND {tag}: bound/|Ut| {bound / mag} (state alone {ULP_FACTOR * state_only / mag}) "
           f"fma/spread {e_fma / spread} planted({rel:g})/bound {e_bad / bound} planted flux-scale {e_bad / scale}")
     assert (e_bad > 2.0 * bound).any(), (tag, e_bad / bound)
+
+
+def test_mesh_perturbation_keeps_the_mesh_closed():
+    """The mesh points move as a set: copies of one physical point in neighbouring elements, and its
+    periodic images, get the same one-ulp move, so every face still matches its neighbour's."""
+    from helpers import mesh_ulp_perturb
+
+    xyz, faces = W.box_mesh(3, (3, 2, 2), mapping="sine_0.05")
+    X = mesh_ulp_perturb(xyz, 7)
+    assert 0.3 < (X != xyz).mean() < 0.9  # about two thirds of the coordinates move
+    assert np.abs(X - xyz).max() <= 1e-14 * np.abs(xyz).max() + 1e-300
+    # element 0's +x face against element 1's -x face (shared nodes), and the y and z faces
+    np.testing.assert_array_equal(X[0][:, :, :, -1], X[1][:, :, :, 0])
+    np.testing.assert_array_equal(X[0][:, :, -1, :], X[3][:, :, 0, :])
+    np.testing.assert_array_equal(X[0][:, -1, :, :], X[6][:, 0, :, :])
+    # the periodic image across x: tangential coordinates identical, x one period apart to an ulp
+    np.testing.assert_array_equal(X[2][1:, :, :, -1], X[0][1:, :, :, 0])
+    assert np.abs(X[2][0, :, :, -1] - X[0][0, :, :, 0] - 2 * np.pi).max() <= 4 * np.spacing(2 * np.pi)
