@@ -305,6 +305,15 @@ def test_full_size_shocked_blast_indicator_and_fv_rhs(env, tmp_path):
     jump = jump + subcell_range_magnitude(Uh[sample], ref.Ja[sample])
     scale = flux_scale(Uh[sample], ref.Ja[sample], ref.J[sample], orc.dmatrix(w.N), jump=jump)
     check_fp64("shocked blast 64^3 after 200 steps, sampled elements", Ut[sample], Ut_ref, spread, scale)
+    # the FP32-bulk form's right-hand side at the same state (FV subcells in FP32), within its tolerance
+    g32 = dg.DG(w.N, xyz, faces, precision="fp32_bulk", **w.physics())
+    Ut32 = g32.rhs(U).cpu().numpy()[sample]
+    g32.check()
+    scale32 = flux_scale(Uh[sample], ref.Ja[sample], ref.J[sample], orc.dmatrix(w.N), state_dissipation=True,
+                         jump=jump)
+    err32 = parity(Ut32, Ut_ref, scale32)
+    print(f"PARITY32 shocked blast 64^3 sampled elements: flux-scale {err32}")
+    assert (err32 <= 64 * 2.0 ** -24).all(), err32
 
 
 def test_full_size_lserk_step_matches_stagewise_definition(env):

@@ -5,13 +5,15 @@
 - the right-hand side of wall-bounded channels (walls at z = 0 and z = Hz, periodic in x and y):
   FP64 element by element within ULP_FACTOR times the oracle's one-ulp spread and 1e-12 of the
   flux scale (tests/helpers.py), FP32-bulk within 64 * 2^-24 of the flux scale, for several degrees, flux pairs, exchange indices and the DG/FV blend;
-- at full size (N = 5, 48 x 24 x 24 channel): discrete conservation of mass and energy, and the
-  exact wall-shear drain of x-momentum for uniform flow along the walls.
+- at full size (N = 5, 48 x 24 x 24 channel): sampled wall and interior elements against the oracle,
+  discrete conservation of mass and energy, and the exact wall-shear drain of x-momentum for uniform
+  flow along the walls.
 """
 import numpy as np
 import pytest
 
-from helpers import check_fp64, flux_scale, normwise, parity, subcell_range_magnitude, ulp_spread
+from helpers import (check_fp64, face_jump_magnitude, flux_scale, normwise, parity, subcell_range_magnitude,
+                     ulp_spread)
 from paper_2306_12891_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -134,8 +136,22 @@ def test_full_size_channel_conservation_and_wall_shear(env):
     _, J = gpu.metrics()
     xi, w, _ = dg.basis(N)
     wq = torch.from_numpy(np.einsum("k,j,i->kji", w, w, w)).cuda()[None] * J
-    U = torch.from_numpy(_state(xyz, seed=12)).cuda()
+    U0 = _state(xyz, seed=12)
+    U = torch.from_numpy(U0).cuda()
     Ut = gpu.rhs(U)
+    # element by element against the oracle on sampled elements: both walls and the interior
+    nx, ny, nz = nel
+    rng = np.random.default_rng(20230626)
+    bottom, top = rng.choice(nx * ny, 5, replace=False), (nz - 1) * nx * ny + rng.choice(nx * ny, 5, replace=False)
+    sample = sorted(set(bottom) | set(top) | set(rng.choice(nx * ny * nz, 6, replace=False)))
+    period = (2 * np.pi, np.pi, Hz)
+    ref = orc.Oracle(N, xyz, faces, **phys)
+    Ut_ref = ref.rhs(U0, mask=sample)[sample]
+    spread, _ = ulp_spread(lambda X, V: orc.Oracle(N, X, faces, **phys).rhs(V, mask=sample)[sample], xyz, U0,
+                           period=period, base=Ut_ref)
+    scale = flux_scale(U0[sample], ref.Ja[sample], ref.J[sample], orc.dmatrix(N),
+                       jump=face_jump_magnitude(U0, faces, N, ref.Ja, elements=sample)[sample])
+    check_fp64("wall channel 48x24x24 sampled elements", Ut.cpu().numpy()[sample], Ut_ref, spread, scale)
     tot = torch.einsum("ekji,evkji->v", wq, Ut).cpu().numpy()
     mag = torch.einsum("ekji,evkji->v", wq, Ut.abs()).cpu().numpy()
     print(f"WALL full size: sum J w Ut / sum J w |Ut| = {tot / mag}")
