@@ -195,7 +195,10 @@ def ulp_spread(evaluate, xyz, U0, count=3, seed=20230622, period=2.0 * np.pi, ba
 def check_fp64(tag, Ut, Ut_ref, spread, scale, tol=TOL, factor=ULP_FACTOR):
     """Assert and print both FP64 parity figures (module docstring). Returns (flux-scale, normwise)."""
     err = per_var_max(np.asarray(Ut) - np.asarray(Ut_ref))
-    mag = np.maximum(per_var_max(Ut_ref), 1e-300)
+    # a variable whose right-hand side is exactly zero (the energy of a fluid at rest) has no normwise
+    # figure; it is printed relative to 1 (absolute)
+    mag = per_var_max(Ut_ref)
+    mag = np.where(mag > 0, mag, 1.0)
     # 0/0 (a variable with no flux terms and no error, e.g. the energy of a fluid at rest) counts as 0
     fs = np.divide(err, scale, out=np.where(err > 0, np.inf, 0.0), where=scale > 0)
     nw, bound = err / mag, factor * spread / mag
