@@ -38,13 +38,10 @@ UNIT = "DOF-stage/s"
 STAGES = 5
 P0_TGV = 1.0 / (1.4 * 0.1 ** 2)  # background pressure of the Ma 0.1 Taylor-Green vortex
 # DRAM bytes per element of one volume-kernel launch (dram__bytes_read.sum + dram__bytes_write.sum),
-# from an ncu capture of the current kernel on the 16^3 case (a first LSERK stage: 517.87 MB read,
-# 143.12 MB written), scaled to a launch by the element count (the kernel's traffic is per element).
-# None once the kernel has changed since that capture.
-VOLUME_DRAM_BYTES_PER_ELEMENT = 661.0e6 / 16 ** 3
-# DRAM bytes (read + write) of one FP32-bulk volume launch (pair-symmetric line kernel) per element,
-# from one ncu capture of the 16^3 case (351.5 MB read, 157.2 MB written for 4096 elements), scaled
-# by the element count
+# from an ncu capture of the current kernel on the 24^3 case (a later LSERK stage: 2060.27 MB read,
+# 545.17 MB written for 13824 elements), scaled to a launch by the element count (the kernel's
+# traffic is per element). None once the kernel has changed since that capture.
+VOLUME_DRAM_BYTES_PER_ELEMENT = (2060.267008e6 + 545.168640e6) / 24 ** 3
 # DRAM bytes (read + write) of one FP32-bulk volume launch (pair-symmetric line kernel, stage factor) per
 # element, from one ncu capture at the full 32^3 size of the second stage of a step (3492.2 MB read,
 # 1625.3 MB written for 32768 elements)
@@ -57,38 +54,57 @@ def scaled_traffic(bytes_per_element, n_elems: int, applies: bool = True):
     return bytes_per_element * n_elems if (bytes_per_element is not None and applies) else None
 
 
+def viscous_sweep_flops_per_node(N: int) -> float:
+    """Flops per node, direction and quantity of a line sweep with the zero-diagonal D (the viscous
+    divergence): with the even-odd halves of the centro-antisymmetric LGL D (even n = N + 1) a line
+    of n nodes takes n sums and differences, n^2 / 2 FMA and 2n combinations: n^2 + 3n flops with the
+    accumulation; otherwise N FMA and the accumulation: 2N + 1 per node."""
+    n = N + 1
+    return (n + 3.0) if n % 2 == 0 else (2.0 * N + 1.0)
+
+
 def volume_kernel_flops_per_element(N: int, navier_stokes: bool) -> float:
-    """Algorithmic FP64 flops of one volume-kernel launch per element (FMA = 2 flops), counted
-    from the formulas the kernel evaluates:
+    """Algorithmic FP64 flops of one volume-kernel launch (a later LSERK stage) per element (FMA = 2
+    flops, a division or reciprocal square root 1), counted from the formulas the kernel evaluates:
       pair flux (Pirozzoli, plain sums, 1/2 factors folded into D):
         6 sums + V (mul + 2 FMA = 5) + F_rho (add + mul = 2) + p-sum 1 + momentum 3 x (mul + FMA) = 9
         + energy (add + mul = 2) + accumulation into both nodes 10 FMA = 20        -> 45 per pair,
         3 n^2 n(n-1)/2 pairs per element;
-      per node: primitives 15; direction sum 10; surface terms 10 per face point (6 n^2 per element);
-        Jacobian 5; LSERK update 25; Navier-Stokes: viscous divergence 3*4*N FMA = 24 N,
-        neighbour viscous trace 8 per face point, 4 subtractions."""
+      per node: primitives 15; direction sum 10; stage factor dt (-1/J) 1 and per variable the
+        increment, the register and the state (mul + 2 FMA) 25; Navier-Stokes: the viscous
+        divergence 12 viscous_sweep_flops_per_node(N) and 4 subtractions;
+      per face point (6 n^2 per element): surface terms 10; Navier-Stokes: the neighbour's viscous
+        trace 8."""
     n = N + 1
     pairs = 3 * n * n * n * (n - 1) // 2
-    per_node = 15 + 10 + 5 + 25 + ((24 * N + 4) if navier_stokes else 0)
+    per_node = 15 + 10 + 26 + ((12 * viscous_sweep_flops_per_node(N) + 4) if navier_stokes else 0)
     per_face_pt = 10 + (8 if navier_stokes else 0)
     return 45.0 * pairs + per_node * n ** 3 + per_face_pt * 6 * n * n
 
 
+def lift_uses_lines(N: int) -> bool:
+    """Whether the FP64 lifting forms the reference derivatives along lines (k_lift_lines)."""
+    return N == 7
+
+
 def lift_kernel_flops_per_element(N: int) -> float:
-    """Algorithmic FP64 flops of one BR1 lifting launch per element (FMA = 2), from the kernel's
-    statements: primitives and T 15 per node; per direction and lifted variable a D sweep of n FMA
-    and the metric contraction 3 FMA (12 (2n + 6) per node); surface terms 4 x (1 mul + 3 FMA) = 28
-    per (node, face) pair, 6 n^2 pairs per element; 1/J 12; viscous flux 43; contravariant flux
-    12 x (mul + 2 FMA) = 60."""
+    """Algorithmic FP64 flops of one BR1 lifting launch per element (FMA = 2, a division 1), from the
+    kernel's statements: primitives and T 15 per node; per direction and lifted variable the
+    reference derivative -- along lines with the even-odd halves of D (N = 7: n^2 + 2n per line and
+    quantity, n + 2 per node) or node-wise (n FMA, 2n) -- and the metric contraction 3 FMA; 1/J into
+    mu and kappa 2; the viscous flux 40; the contravariant flux 12 x (mul + 2 FMA) = 60; surface terms
+    4 x (1 mul + 3 FMA) = 28 per (node, face) pair, 6 n^2 pairs per element."""
     n = N + 1
-    return (15 + 12 * (2 * n + 6) + 12 + 43 + 60) * n ** 3 + 28 * 6 * n * n
+    sweep = (n + 2.0) if lift_uses_lines(N) else 2.0 * n
+    return (15 + 12 * (sweep + 6) + 2 + 40 + 60) * n ** 3 + 28 * 6 * n * n
 
 
 def face_kernel_flops_per_point() -> float:
-    """Algorithmic FP64 flops per face point of the face kernel for Roe + Navier-Stokes, from its
-    statements: two Euler fluxes 2 x 29, Roe averages, wave strengths and dissipation 149, the two
-    outward slot values 10, the BR1 jumps of (u, v, w, T) 40."""
-    return 58.0 + 149.0 + 10.0 + 40.0
+    """Algorithmic FP64 flops per face point of the face kernel for Roe + Navier-Stokes (FMA = 2, a
+    division or reciprocal square root 1), from its statements: two Euler fluxes 2 x 28; Roe's
+    averages from one reciprocal square root per side, the sound speed, wave strengths and the
+    dissipation 131; the two outward slot values 10; the BR1 jumps of (u, v, w, T) 11."""
+    return 56.0 + 131.0 + 10.0 + 11.0
 
 
 def adjoint_volume_flops_per_element(N: int, navier_stokes: bool) -> float:
@@ -108,17 +124,17 @@ def adjoint_volume_flops_per_element(N: int, navier_stokes: bool) -> float:
 
 
 def adjoint_visc_flops_per_element(N: int) -> float:
-    """Algorithmic FP64 flops of one adjoint-viscous launch per element (FMA = 2 flops), counted from
-    the statements of the kernel (BR1 lifting, viscous flux and viscous divergence transposed):
-      per node: staging of (u, v, w, T) and l = -lambda/J 21; per direction and lifted variable the
-        forward D sweep (n FMA), the transposed sweep of l (n - 1 FMA) and the metric contraction
-        (3 FMA): 12 (4n + 4); 1/J 12; div and tau 28; Z = Ja^T zeta 60; omega and Y 33; Gamma 26;
-        H = (1/J) Ja Gamma 72; the transposed D sweeps of H 12 (2n + 1); omega added 3
-        -> 72 n + 317 per node;
-      per (node, face) pair on the element surface (6 n^2 per element): the neighbour's lifted
-        quantities 16, the central face value and its cotangent 4 x 13, the face slot 9 -> 77."""
+    """Algorithmic FP64 flops of one adjoint-viscous launch per element (FMA = 2 flops, a division 1),
+    counted from the statements of the kernel (BR1 lifting, viscous flux and viscous divergence
+    transposed, at the viscous stress the forward lifting recorded):
+      per node: (u, v, w) and l = -lambda/J 9; per direction and lifted variable the transposed
+        sweep of l, N FMA: 24 N; mu/J, kappa/J 2; Z = Ja^T zeta 60; omega and Y 33; trace 2;
+        Gamma 26; H = Ja Gamma 60; the transposed D sweeps of H and their sums 12 (2n + 1); omega
+        added 3 -> 48 n + 183 per node;
+      per (node, face) pair on the element surface (6 n^2 per element): the neighbour's share of the
+        transposed divergence 14, the face slot 9 -> 23."""
     n = N + 1
-    return (72.0 * n + 317.0) * n ** 3 + 77.0 * 6 * n * n
+    return (48.0 * n + 183.0) * n ** 3 + 23.0 * 6 * n * n
 
 
 def fv_subcell_flops_per_element(N: int, riemann_flops: float) -> float:

@@ -155,7 +155,10 @@ dg_status dg_invariants_noalloc(int N, int n_elems, double gamma, const double *
  * launch. The Roe and LLF fluxes contain |.| and max: where an argument is exactly zero (or two are
  * equal) the one-sided derivative of the branch the forward kernel takes is used.
  * Work buffers are library-owned; the state buffers of the LSERK adjoints are allocated on first
- * use (DG_ERR_OOM if that fails) and kept until dg_free. All arrays are device arrays
+ * use (DG_ERR_OOM if that fails) and kept until dg_free. For Navier-Stokes every product is taken at
+ * the viscous stress that the forward lifting forms at the same state: the calls below that
+ * recompute stage states keep that record beside each (6 doubles per node), and dg_rhs_vjp runs the
+ * face and lifting kernels at U first. All arrays are device arrays
  * [n_elems][5][n]^3 on the context stream; asynchronous unless stated. ---- */
 
 /* (Meshes with wall faces are not supported by the adjoint: DG_ERR_UNSUPPORTED.) */
@@ -180,15 +183,16 @@ dg_status dg_lserk_step_vjp(dg_ctx *ctx, const double *U, double *Ubar, double d
 dg_status dg_lserk_steps_vjp(dg_ctx *ctx, const double *U0, double *Ubar, double dt, double t, int n_steps,
                              int interval);
 
-/* Budget in bytes for the state buffers of dg_lserk_steps_vjp (decides whether a segment's stage
- * states are kept); 0 restores the default (free device memory less 10% of the total). Buffers
- * already allocated are kept. */
+/* Budget in bytes for the buffers of dg_lserk_steps_vjp and dg_lserk_steps_record (decides whether a
+ * segment's stage states, or a recording's, are kept; for Navier-Stokes each kept state also keeps
+ * the lifting's viscous stress record of it, 6/5 of a state); 0 restores the default (free device
+ * memory less 10% of the total). Buffers already allocated are kept. */
 dg_status dg_adjoint_memory_limit(dg_ctx *ctx, double bytes);
 
 /* The forward run recorded for a later reverse sweep (what an autograd framework does): advances U
- * by n_steps LSERK steps like dg_lserk_steps and keeps, in library buffers, every stage state when
- * 5 n_steps state buffers fit in the adjoint's memory budget (dg_adjoint_memory_limit), else the
- * state every `interval` steps. *tape identifies the recording; a new recording invalidates the
+ * by n_steps LSERK steps like dg_lserk_steps and keeps, in library buffers, every stage state (with
+ * its viscous stress record for Navier-Stokes) when they fit in the adjoint's memory budget
+ * (dg_adjoint_memory_limit), else the state every `interval` steps. *tape identifies the recording; a new recording invalidates the
  * previous one. */
 dg_status dg_lserk_steps_record(dg_ctx *ctx, double *U, double dt, double t, int n_steps, int interval,
                                 long long *tape);

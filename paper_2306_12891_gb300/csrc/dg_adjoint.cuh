@@ -11,11 +11,11 @@
 //               transposed Jacobian goes to both sides' face slots. Roe and LLF: hand-written
 //               reverse mode of the forward statements; EC: forward-mode dual numbers (5 seeds per
 //               pass, 2 passes) through the same templated code the forward kernel runs.
-//   adj_visc    (Navier-Stokes) per element: recompute the lifted gradients; transpose the
-//               viscous divergence (D^T sweeps of l, neighbour term through the face), the
-//               contravariant projection and the Navier-Stokes-Fourier flux (pointwise), then the
-//               lifting (D^T sweeps, central face value): cotangents of (u, v, w, T) per node plus
-//               face slots for the neighbour's share.
+//   adj_visc    (Navier-Stokes) per element: transpose the viscous divergence (D^T sweeps of l,
+//               neighbour term through the face), the contravariant projection and the
+//               Navier-Stokes-Fourier flux (pointwise, at the viscous stress the forward lifting
+//               recorded for this state), then the lifting (D^T sweeps, central face value):
+//               cotangents of (u, v, w, T) per node plus face slots for the neighbour's share.
 //   adj_volume  per element: the two-point flux differencing transposed pair by pair. With
 //               sums S = x_i + x_m the Kennedy-Gruber / Pirozzoli fluxes are polynomials in
 //               (S_rho, S_u, S_p, S_X), so each pair adds the same cotangent vector to both of its
@@ -32,14 +32,15 @@ namespace {
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ double sgn_of(double x) { return x < 0.0 ? -1.0 : 1.0; }  // d|x|/dx, +1 at 0
 
-// primitives of one side: ir = 1/rho, u = m ir, p = (gamma-1)(E - |m|^2 ir / 2)
+// primitives of one side: ir = 1/rho (given: (1/sqrt(rho))^2, as the forward solver forms it),
+// u = m ir, p = (gamma-1)(E - |m|^2 ir / 2)
 struct Side {
   double ir, u[3], p, un;
 };
 
-__device__ __forceinline__ Side side_of(const double U[5], const double nv[3], double gm1) {
+__device__ __forceinline__ Side side_of(const double U[5], const double nv[3], double gm1, double ir) {
   Side s;
-  s.ir = 1.0 / U[0];
+  s.ir = ir;
   s.u[0] = U[1] * s.ir;
   s.u[1] = U[2] * s.ir;
   s.u[2] = U[3] * s.ir;
@@ -79,8 +80,9 @@ __device__ __forceinline__ void flux_back(const double U[5], const Side &s, cons
 __device__ void llf_vjp(const double UL[5], const double UR[5], const double nv[3], double gam, const double cF[5],
                         double gL[5], double gR[5]) {
   const double gm1 = gam - 1.0;
-  const Side L = side_of(UL, nv, gm1), R = side_of(UR, nv, gm1);
-  const double cL = sqrt(gam * L.p / UL[0]), cR = sqrt(gam * R.p / UR[0]);
+  const double rsL = rsq(UL[0]), rsR = rsq(UR[0]);
+  const Side L = side_of(UL, nv, gm1, rsL * rsL), R = side_of(UR, nv, gm1, rsR * rsR);
+  const double cL = sqrt(gam * L.p * L.ir), cR = sqrt(gam * R.p * R.ir);
   const double aL = fabs(L.un) + cL, aR = fabs(R.un) + cR;
   const bool rwins = aR > aL;  // the forward's max picks the right argument only when strictly larger
   const double lam = rwins ? aR : aL;
@@ -99,23 +101,26 @@ __device__ void llf_vjp(const double UL[5], const double UR[5], const double nv[
   if (rwins) {
     cunR += clam * sgn_of(R.un);
     cpR += clam * 0.5 * cR / R.p;
-    gR[0] -= clam * 0.5 * cR / UR[0];
+    gR[0] -= clam * 0.5 * cR * R.ir;
   } else {
     cunL += clam * sgn_of(L.un);
     cpL += clam * 0.5 * cL / L.p;
-    gL[0] -= clam * 0.5 * cL / UL[0];
+    gL[0] -= clam * 0.5 * cL * L.ir;
   }
   side_back(UL, L, nv, gm1, cuL, cpL, cunL, cirL, gL);
   side_back(UR, R, nv, gm1, cuR, cpR, cunR, cirR, gR);
 }
 
-// the same for Roe's flux (no entropy fix), statement by statement in reverse
+// the same for Roe's flux (no entropy fix), statement by statement in reverse; as in the forward
+// solver, one reciprocal square root per side (1/rho = rs^2, sqrt(rho) = rho rs, 1/(2 sqrt(rho)) = rs/2)
+// and one for the sound speed (c = c^2 rc, 1/c^2 = rc^2, 1/(2c) = rc/2)
 __device__ void roe_vjp(const double UL[5], const double UR[5], const double nv[3], double gam, const double cF[5],
                         double gL[5], double gR[5]) {
   const double gm1 = gam - 1.0;
-  const Side L = side_of(UL, nv, gm1), R = side_of(UR, nv, gm1);
+  const double rsL = rsq(UL[0]), rsR = rsq(UR[0]);
+  const Side L = side_of(UL, nv, gm1, rsL * rsL), R = side_of(UR, nv, gm1, rsR * rsR);
   // forward
-  const double sL = sqrt(UL[0]), sR = sqrt(UR[0]);
+  const double sL = UL[0] * rsL, sR = UR[0] * rsR;
   const double iw = 1.0 / (sL + sR);
   double ut[3];
 #pragma unroll
@@ -125,7 +130,8 @@ __device__ void roe_vjp(const double UL[5], const double UR[5], const double nv[
   const double Ht = (sL * hL + sR * hR) * iw;
   const double q2 = ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2];
   const double c2 = gm1 * (Ht - 0.5 * q2);
-  const double ct = sqrt(c2), ic2 = 1.0 / c2;
+  const double rc = rsq(c2);
+  const double ct = c2 * rc, ic2 = rc * rc;
   const double rt = sL * sR;
   const double unt = ut[0] * nv[0] + ut[1] * nv[1] + ut[2] * nv[2];
   const double dr = UR[0] - UL[0], dp = R.p - L.p;
@@ -184,7 +190,7 @@ __device__ void roe_vjp(const double UL[5], const double UR[5], const double nv[
 #pragma unroll
   for (int k = 0; k < 3; ++k) { c_du[k] += c_dun * nv[k]; c_ut[k] += c_unt * nv[k]; }
   // Roe averages
-  double c_c2 = -c_ic2 * ic2 * ic2 + c_ct * 0.5 / ct;
+  double c_c2 = -c_ic2 * ic2 * ic2 + c_ct * 0.5 * rc;
   c_Ht += gm1 * c_c2;
   c_q2 -= 0.5 * gm1 * c_c2;
 #pragma unroll
@@ -210,8 +216,8 @@ __device__ void roe_vjp(const double UL[5], const double UR[5], const double nv[
   for (int v = 0; v < 5; ++v) { gL[v] = 0.0; gR[v] = 0.0; }
   gL[4] += c_hL * L.ir;
   gR[4] += c_hR * R.ir;
-  gL[0] += -c_dr + c_sL * 0.5 / sL;
-  gR[0] += c_dr + c_sR * 0.5 / sR;
+  gL[0] += -c_dr + c_sL * 0.5 * rsL;
+  gR[0] += c_dr + c_sR * 0.5 * rsR;
   double cunL = 0.0, cunR = 0.0;
   flux_back(UL, L, nv, hF, cpL, cunL, gL);
   flux_back(UR, R, nv, hF, cpR, cunR, gR);
@@ -285,10 +291,13 @@ __global__ void __launch_bounds__(128) k_adj_face(const DgDevice d, const double
 
 // ---------------------------------------------------------------------------------------------
 // adjoint of the lifting + viscous flux + viscous divergence (Navier-Stokes)
-// shared memory per element: W[4][nnn] (u, v, w, T), L[4][nnn] (l of momentum and energy),
+// The flux is linear in the lifted gradients except for the work term u.tau, whose derivative
+// needs the viscous stress tau at the state: the forward lifting records it per node (the record
+// the reverse sweep keeps with each stage state), so no gradient is formed here.
+// shared memory per element: W[3][nnn] (u, v, w), L[4][nnn] (l of momentum and energy),
 // H[12][nnn] (cotangent of the direction-d reference derivative of w_q), Om[3][nnn]
 // ---------------------------------------------------------------------------------------------
-constexpr int ADJV_SLOTS = 23;
+constexpr int ADJV_SLOTS = 22;
 
 // the neighbour's volume node facing face point (pp, qq) of element e's face f
 __device__ __forceinline__ void neighbour_node(const DgDevice &d, size_t e, int f, int pp, int qq, int &nb, int &fnb,
@@ -303,11 +312,12 @@ __device__ __forceinline__ void neighbour_node(const DgDevice &d, size_t e, int 
 }
 
 __global__ void __launch_bounds__(LIFT_THREADS) k_adj_visc(const DgDevice d, const double *__restrict__ U,
-                                                           const double *__restrict__ lam, double *__restrict__ cotW,
+                                                           const double *__restrict__ lam,
+                                                           const double *__restrict__ tau, double *__restrict__ cotW,
                                                            double *__restrict__ sigma) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  double *Ws = reinterpret_cast<double *>(sm_raw);  // [EPB][4][nnn]
-  double *Ls = Ws + LIFT_EPB * 4 * nnn;              // [EPB][4][nnn]
+  double *Ws = reinterpret_cast<double *>(sm_raw);  // [EPB][3][nnn]
+  double *Ls = Ws + LIFT_EPB * 3 * nnn;              // [EPB][4][nnn]
   double *Hs = Ls + LIFT_EPB * 4 * nnn;              // [EPB][12][nnn]
   double *Os = Hs + LIFT_EPB * 12 * nnn;             // [EPB][3][nnn]
   // D in shared memory, rows padded: the sweeps index it by the thread's own node, which would
@@ -315,42 +325,28 @@ __global__ void __launch_bounds__(LIFT_THREADS) k_adj_visc(const DgDevice d, con
   __shared__ double sD[n][n + 1];
   for (int t = threadIdx.x; t < nn; t += blockDim.x) sD[t / n][t % n] = c_D[t];
   const int e0 = blockIdx.x * LIFT_EPB;
-  const double gm1 = d.gamma - 1.0, iR = 1.0 / d.R;
   for (int t = threadIdx.x; t < LIFT_EPB * nnn; t += blockDim.x) {
     const int le = t / nnn, node = t % nnn, e = e0 + le;
     if (e >= d.nE) continue;
-    double Uv[5];
-    load_state<double>(d, U, e, node, Uv);
-    const double r = Uv[0], ir = 1.0 / r;
-    const double u = Uv[1] * ir, v = Uv[2] * ir, w = Uv[3] * ir;
-    const double p = gm1 * (Uv[4] - 0.5 * r * (u * u + v * v + w * w));
-    double *W = Ws + le * 4 * nnn + node;
-    W[0] = u;
-    W[nnn] = v;
-    W[2 * nnn] = w;
-    W[3 * nnn] = p * ir * iR;
+    const size_t gi = (size_t)e * 5 * nnn + node;
+    const double ir = 1.0 / U[gi];  // u as the lifting forms it
+    double *W = Ws + le * 3 * nnn + node;
+    W[0] = U[gi + nnn] * ir;
+    W[nnn] = U[gi + 2 * nnn] * ir;
+    W[2 * nnn] = U[gi + 3 * nnn] * ir;
     const double miJ = -d.invJ[(size_t)e * nnn + node];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) Ls[(le * 4 + q) * nnn + node] = miJ * lam[((size_t)e * 5 + 1 + q) * nnn + node];
+    for (int q = 0; q < 4; ++q) Ls[(le * 4 + q) * nnn + node] = miJ * lam[gi + (1 + q) * nnn];
   }
   __syncthreads();
   for (int t = threadIdx.x; t < LIFT_EPB * nnn; t += blockDim.x) {
     const int le = t / nnn, node = t % nnn, e = e0 + le;
     if (e >= d.nE) continue;
     const int ijk[3] = {node % n, (node / n) % n, node / nn};
-    const double *W = Ws + le * 4 * nnn;
+    const double *W = Ws + le * 3 * nnn;
     const double *L = Ls + le * 4 * nnn;
-    double Ja[3][3];
-#pragma unroll
-    for (int dd = 0; dd < 3; ++dd)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) Ja[dd][c] = d.Ja[(((size_t)e * 3 + dd) * 3 + c) * nnn + node];
-    // forward: lifted gradients g[q][c] of w_q, as the lifting kernel forms them
-    double g[4][3];
     // reverse seed: zeta[dd][q] = cotangent of the contravariant viscous flux Fv^dd_q at this node
     double zeta[3][4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) g[q][0] = g[q][1] = g[q][2] = 0.0;
 #pragma unroll
     for (int dd = 0; dd < 3; ++dd) {
       const int id = ijk[dd];
@@ -358,51 +354,38 @@ __global__ void __launch_bounds__(LIFT_THREADS) k_adj_visc(const DgDevice d, con
       const int base = node - id * st;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        double s = 0.0, z = 0.0;
+        double z = 0.0;
 #pragma unroll
-        for (int m = 0; m < n; ++m) {
-          s += sD[id][m] * W[q * nnn + base + m * st];
+        for (int m = 0; m < n; ++m)
           if (m != id) z -= sD[m][id] * L[q * nnn + base + m * st];
-        }
-        g[q][0] += Ja[dd][0] * s;
-        g[q][1] += Ja[dd][1] * s;
-        g[q][2] += Ja[dd][2] * s;
         zeta[dd][q] = z;
       }
-      if (id == 0 || id == N) {
+      if (id == 0 || id == N) {  // the neighbour's viscous divergence reads this node's flux
         const int f = 2 * dd + (id == N ? 1 : 0);
         const int pp = dd == 0 ? ijk[1] : ijk[0], qq = dd == 2 ? ijk[1] : ijk[2];
         int nb, fnb, nbnode, nbpq;
         neighbour_node(d, e, f, pp, qq, nb, fnb, nbnode, nbpq);
-        double Un[5];
-        load_state<double>(d, U, nb, nbnode, Un);
-        const double r = Un[0], ir = 1.0 / r;
-        const double wn[4] = {Un[1] * ir, Un[2] * ir, Un[3] * ir,
-                              gm1 * (Un[4] - 0.5 * (Un[1] * Un[1] + Un[2] * Un[2] + Un[3] * Un[3]) * ir) * ir * iR};
-        const double sc = (id == N ? 1.0 : -1.0) * c_invw[id];
         const double sgf = (f & 1) ? 0.5 : -0.5;
         const double miJn = -d.invJ[(size_t)nb * nnn + nbnode];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const double jq = sc * (0.5 * (wn[q] - W[q * nnn + node]));
-          g[q][0] += Ja[dd][0] * jq;
-          g[q][1] += Ja[dd][1] * jq;
-          g[q][2] += Ja[dd][2] * jq;
+        for (int q = 0; q < 4; ++q)
           zeta[dd][q] += c_invw[id] * sgf * (miJn * lam[((size_t)nb * 5 + 1 + q) * nnn + nbnode]);
-        }
       }
     }
-    // g holds J grad w; tau, the heat flux and their transposes are linear in grad w, so 1/J goes
-    // into mu and kappa (which then also carry the 1/J of H below)
+    double Ja[3][3];
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Ja[dd][c] = d.Ja[(((size_t)e * 3 + dd) * 3 + c) * nnn + node];
+    // the lifting forms tau and the heat flux from J grad w with 1/J in mu and kappa; their
+    // transposes carry the same factors, and with them the 1/J of H below
     const double iJ = d.invJ[(size_t)e * nnn + node];
     const double mu = d.mu * iJ, kappa = d.kappa * iJ;
     const double u[3] = {W[node], W[nnn + node], W[2 * nnn + node]};
-    const double div = g[0][0] + g[1][1] + g[2][2];
-    double tau[3][3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) tau[k][c] = mu * (g[k][c] + g[c][k]) - (k == c ? 2.0 / 3.0 * mu * div : 0.0);
+    const double *tr = tau + (size_t)e * 6 * nnn + node;
+    const double txx = tr[0], tyy = tr[nnn], tzz = tr[2 * nnn], txy = tr[3 * nnn], txz = tr[4 * nnn],
+                 tyz = tr[5 * nnn];
+    const double ta[3][3] = {{txx, txy, txz}, {txy, tyy, tyz}, {txz, tyz, tzz}};
     // Z[c][q]: cotangent of the Cartesian viscous flux F_c,q (F_c,k = tau_kc; F_c,3 = u.tau_c + kappa dT/dx_c)
     double Z[3][4];
 #pragma unroll
@@ -412,7 +395,7 @@ __global__ void __launch_bounds__(LIFT_THREADS) k_adj_visc(const DgDevice d, con
     double Y[3][3], om[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      om[k] = Z[0][3] * tau[k][0] + Z[1][3] * tau[k][1] + Z[2][3] * tau[k][2];
+      om[k] = Z[0][3] * ta[k][0] + Z[1][3] * ta[k][1] + Z[2][3] * ta[k][2];
 #pragma unroll
       for (int c = 0; c < 3; ++c) Y[k][c] = Z[c][k] + Z[c][3] * u[k];
     }
@@ -734,15 +717,15 @@ void launch_adj_face(const DgDevice &d, const double *U, const double *lam, doub
   }
 }
 
-void launch_adj_visc(const DgDevice &d, const double *U, const double *lam, double *cotW, double *sigma,
-                     cudaStream_t s) {
+void launch_adj_visc(const DgDevice &d, const double *U, const double *lam, const double *tau, double *cotW,
+                     double *sigma, cudaStream_t s) {
   const size_t smem = sizeof(double) * LIFT_EPB * ADJV_SLOTS * nnn;
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_adj_visc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_set = true;
   }
-  k_adj_visc<<<(d.nE + LIFT_EPB - 1) / LIFT_EPB, LIFT_THREADS, smem, s>>>(d, U, lam, cotW, sigma);
+  k_adj_visc<<<(d.nE + LIFT_EPB - 1) / LIFT_EPB, LIFT_THREADS, smem, s>>>(d, U, lam, tau, cotW, sigma);
 }
 
 template <int VF>

@@ -70,11 +70,16 @@ struct dg_ctx {
   double t_ms[KC_COUNT] = {0};
   long long t_count[KC_COUNT] = {0};
   size_t n_state = 0;          // doubles in U
+  size_t n_tau = 0;            // doubles in a viscous stress record [nE][6][n^3] (Navier-Stokes adjoint)
   // adjoint: library-owned state buffers (stage states, gbar, checkpoints), allocated on first use
   std::vector<double *> adj_pool;
-  size_t adj_limit = 0;        // bytes the adjoint's state buffers may use (0: free memory less 10%)
-  // recorded forward run (dg_lserk_steps_record): every stage state, or checkpoints
-  std::vector<double *> tape_pool;
+  // adjoint, Navier-Stokes: the lifting's viscous stress record of each state the reverse sweep
+  // differentiates at (one step's stages, or a segment's)
+  std::vector<double *> tau_pool;
+  size_t adj_limit = 0;        // bytes the adjoint's buffers may use (0: free memory less 10%)
+  // recorded forward run (dg_lserk_steps_record): every stage state (with its stress record), or
+  // checkpoints
+  std::vector<double *> tape_pool, tape_tau;
   long long tape_id = 0, tape_serial = 0;
   int tape_steps = 0, tape_interval = 0;
   bool tape_all = false;
@@ -161,11 +166,13 @@ dg_status stage_alpha(dg_ctx *c, const double *U) {
   return DG_OK;
 }
 
-// one right-hand-side evaluation; mode 0 writes Ut, mode 1 performs LSERK stage `stage`
-dg_status stage(dg_ctx *c, const double *U, double *out, int mode, int st, double dt) {
+// one right-hand-side evaluation; mode 0 writes Ut, mode 1 performs LSERK stage `stage`; tau
+// (Navier-Stokes, optional): the lifting also writes its viscous stress record of U there
+dg_status stage(dg_ctx *c, const double *U, double *out, int mode, int st, double dt, double *tau = nullptr) {
   DG_TRY(stage_alpha(c, U));
   DG_TRY(launch(c, KC_FACE, [&] { c->K->face(c->d, U, c->stream); }));
-  if (c->d.equations == DG_NAVIER_STOKES) DG_TRY(launch(c, KC_LIFT, [&] { c->K->lift(c->d, U, c->stream); }));
+  if (c->d.equations == DG_NAVIER_STOKES)
+    DG_TRY(launch(c, KC_LIFT, [&] { c->K->lift(c->d, U, tau, c->stream); }));
   const double A = mode ? kA[st] : 0.0, B = mode ? kB[st] : 0.0;
   DG_TRY(launch(c, KC_VOLUME, [&] { c->K->volume(c->d, U, out, c->g, mode, st == 0, dt, A, B, c->stream); }));
   return DG_OK;
@@ -202,14 +209,37 @@ dg_status adj_pool(dg_ctx *c, size_t count) {
   return DG_OK;
 }
 
+// at least `count` viscous stress records in the adjoint's pool (Navier-Stokes; none for Euler)
+dg_status tau_fill(dg_ctx *c, size_t count) {
+  if (!c->n_tau) return DG_OK;
+  while (c->tau_pool.size() < count) {
+    double *p = nullptr;
+    DG_TRY(dev_alloc(c, &p, c->n_tau));
+    c->tau_pool.push_back(p);
+  }
+  return DG_OK;
+}
+
+// the viscous stress record of U alone (the face and lifting kernels of a stage, no volume work)
+dg_status record_tau(dg_ctx *c, const double *U, double *tau) {
+  if (c->d.equations != DG_NAVIER_STOKES) return DG_OK;
+  DG_TRY(launch(c, KC_FACE, [&] { c->K->face(c->d, U, c->stream); }));
+  DG_TRY(launch(c, KC_LIFT, [&] { c->K->lift(c->d, U, tau, c->stream); }));
+  return DG_OK;
+}
+
+// stress record i of the pool (null for Euler)
+double *tau_at(dg_ctx *c, size_t i) { return c->n_tau ? c->tau_pool[i] : nullptr; }
+
 // one vector-Jacobian product of L at U with cotangent lam (see DgKernelTable::adj_volume for modes);
-// the forward work buffers serve as scratch: Fsurf = face slots, Fv = cotW, Wsurf = sigma
+// tau: the lifting's stress record of U (Navier-Stokes). The forward work buffers serve as scratch:
+// Fsurf = face slots, Fv = cotW, Wsurf = sigma
 dg_status vjp(dg_ctx *c, const double *U, const double *lam, double *out, int mode, double dt, double A, double B,
-              int update_g) {
+              int update_g, const double *tau) {
   DgDevice &d = c->d;
   DG_TRY(launch(c, KC_ADJ_FACE, [&] { c->K->adj_face(d, U, lam, d.Fsurf, c->stream); }));
   if (d.equations == DG_NAVIER_STOKES)
-    DG_TRY(launch(c, KC_ADJ_VISC, [&] { c->K->adj_visc(d, U, lam, d.Fv, d.Wsurf, c->stream); }));
+    DG_TRY(launch(c, KC_ADJ_VISC, [&] { c->K->adj_visc(d, U, lam, tau, d.Fv, d.Wsurf, c->stream); }));
   DG_TRY(launch(c, KC_ADJ_VOLUME, [&] {
     c->K->adj_volume(d, U, lam, d.Fsurf, d.Fv, d.Wsurf, out, const_cast<double *>(lam), mode, dt, A, B, update_g,
                      c->stream);
@@ -222,71 +252,93 @@ dg_status copy_state(dg_ctx *c, double *dst, const double *src) {
   return e ? cuda_fail(c, e, "state copy") : DG_OK;
 }
 
-// reverse of one LSERK step whose five stage input states are S[0..4] (gbar in pool[4]):
+// reverse of one LSERK step whose five stage input states are S[0..4], with their stress records
+// T[0..4] (gbar in pool[4]):
 // gbar = B_5 Ubar; for s = 5..1: Ubar += dt (dL/dU)(S[s-1])^T gbar; gbar = A_s gbar + B_(s-1) Ubar
-dg_status reverse_stages(dg_ctx *c, double *const S[5], double *Ubar, double dt) {
+dg_status reverse_stages(dg_ctx *c, double *const S[5], double *const T[5], double *Ubar, double dt) {
   double *gbar = c->adj_pool[4];
   DG_TRY(launch(c, KC_OTHER, [&] { k_scale<<<8 * 152, 256, 0, c->stream>>>(gbar, Ubar, kB[4], c->n_state); }));
   for (int st = 4; st >= 0; --st)
-    DG_TRY(vjp(c, S[st], gbar, Ubar, 1, dt, kA[st], st > 0 ? kB[st - 1] : 0.0, st > 0));
+    DG_TRY(vjp(c, S[st], gbar, Ubar, 1, dt, kA[st], st > 0 ? kB[st - 1] : 0.0, st > 0, T[st]));
   return DG_OK;
 }
 
 dg_status steps_impl(dg_ctx *c, double *U, double dt, int n_steps);
 
-// whether `buffers` state buffers fit in the adjoint's memory budget, counting `have` already held
-bool budget_allows(dg_ctx *c, size_t buffers, size_t have) {
-  const size_t state_bytes = sizeof(double) * c->n_state;
-  if (c->adj_limit) return buffers * state_bytes <= c->adj_limit;
+// device bytes of `states` state buffers and `taus` stress records
+size_t adj_bytes(const dg_ctx *c, size_t states, size_t taus) {
+  return sizeof(double) * (states * c->n_state + taus * c->n_tau);
+}
+
+// bytes the adjoint's and the tape's buffers hold now
+size_t adj_held(const dg_ctx *c) {
+  return adj_bytes(c, c->adj_pool.size() + c->tape_pool.size(), c->tau_pool.size() + c->tape_tau.size());
+}
+
+// whether buffers of `need` bytes fit in the adjoint's memory budget, counting `have` already held
+bool budget_allows(dg_ctx *c, size_t need, size_t have) {
+  if (c->adj_limit) return need <= c->adj_limit;
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
-  const size_t extra = buffers > have ? (buffers - have) * state_bytes : 0;
+  const size_t extra = need > have ? need - have : 0;
   return extra + total_b / 10 < free_b;
 }
 
-// at least `count` library-owned state buffers in `pool`
-dg_status pool_fill(dg_ctx *c, std::vector<double *> &pool, size_t count) {
+// at least `count` library-owned buffers of `doubles` doubles (default: a state) in `pool`
+dg_status pool_fill(dg_ctx *c, std::vector<double *> &pool, size_t count, size_t doubles = 0) {
   while (pool.size() < count) {
     double *p = nullptr;
-    DG_TRY(dev_alloc(c, &p, c->n_state));
+    DG_TRY(dev_alloc(c, &p, doubles ? doubles : c->n_state));
     pool.push_back(p);
   }
   return DG_OK;
 }
 
-// reverse of one LSERK step from U, recomputing its four inner stage states into pool[0..3]
+// reverse of one LSERK step from U, recomputing its four inner stage states into pool[0..3] and the
+// five stress records into the stress pool [0..4]
 dg_status step_vjp(dg_ctx *c, const double *U, double *Ubar, double dt) {
   DG_TRY(adj_pool(c, 5));
+  DG_TRY(tau_fill(c, 5));
   double *S[5] = {const_cast<double *>(U), c->adj_pool[0], c->adj_pool[1], c->adj_pool[2], c->adj_pool[3]};
-  for (int st = 0; st < 4; ++st) DG_TRY(stage(c, S[st], S[st + 1], 1, st, dt));
-  return reverse_stages(c, S, Ubar, dt);
+  double *T[5] = {tau_at(c, 0), tau_at(c, 1), tau_at(c, 2), tau_at(c, 3), tau_at(c, 4)};
+  for (int st = 0; st < 4; ++st) DG_TRY(stage(c, S[st], S[st + 1], 1, st, dt, T[st]));
+  DG_TRY(record_tau(c, S[4], T[4]));
+  return reverse_stages(c, S, T, Ubar, dt);
 }
 
 // Reverse sweep over n_steps from checkpoints cp[j] = state at step j * interval: each segment is
 // recomputed once from its checkpoint and reversed step by step. When the budget allows, the
-// recomputation keeps all five stage states of the segment (5 interval buffers); otherwise the step
-// start states only (interval - 1 buffers) and each step's stages are recomputed before reversal.
-// Segment buffers live in the adjoint pool from index `first` on.
+// recomputation keeps all five stage states of the segment and their stress records (5 interval
+// buffers of each); otherwise the step start states only (interval - 1 buffers) and each step's
+// stages are recomputed before reversal. Segment buffers live in the adjoint pool from index `first`
+// on, segment stress records in the stress pool from index 0 on.
 dg_status reverse_from_checkpoints(dg_ctx *c, const std::vector<double *> &cp, int interval, int n_steps,
                                    double *Ubar, double dt, size_t first) {
   const int ncp = (int)cp.size();
-  const bool store = budget_allows(c, first + 5 * (size_t)interval, c->adj_pool.size() + c->tape_pool.size());
+  const bool store = budget_allows(c, adj_bytes(c, first + 5 * (size_t)interval, 5 * (size_t)interval),
+                                   adj_held(c));
   DG_TRY(adj_pool(c, first + (store ? 5 * (size_t)interval : (size_t)interval - 1)));
+  if (store) DG_TRY(tau_fill(c, 5 * (size_t)interval));
   double **seg = c->adj_pool.data() + first;
   for (int j = ncp - 1; j >= 0; --j) {
     const int len = std::min(interval, n_steps - j * interval);
     if (store) {
       // S(i, s): input state of stage s of step i of the segment; S(0, 0) is the checkpoint
       auto S = [&](int i, int st) { return (i == 0 && st == 0) ? cp[j] : seg[5 * i + st]; };
+      auto T = [&](int i, int st) { return tau_at(c, 5 * (size_t)i + st); };
       for (int i = 0; i < len; ++i)
         for (int st = 0; st < 5; ++st) {
-          if (i == len - 1 && st == 4) break;  // the segment's end state is not needed
+          if (i == len - 1 && st == 4) {  // the segment's end state is not needed, its input's record is
+            DG_TRY(record_tau(c, S(i, st), T(i, st)));
+            break;
+          }
           double *out = st < 4 ? S(i, st + 1) : S(i + 1, 0);
-          DG_TRY(stage(c, S(i, st), out, 1, st, dt));
+          DG_TRY(stage(c, S(i, st), out, 1, st, dt, T(i, st)));
         }
       for (int i = len - 1; i >= 0; --i) {
         double *st5[5] = {S(i, 0), S(i, 1), S(i, 2), S(i, 3), S(i, 4)};
-        DG_TRY(reverse_stages(c, st5, Ubar, dt));
+        double *tau5[5] = {T(i, 0), T(i, 1), T(i, 2), T(i, 3), T(i, 4)};
+        DG_TRY(reverse_stages(c, st5, tau5, Ubar, dt));
       }
     } else {
       auto state = [&](int i) { return i == 0 ? cp[j] : seg[i - 1]; };
@@ -442,6 +494,7 @@ dg_status dg_init(const dg_mesh *mesh, int N, int nodes, const dg_params *prm, v
     d.wm_b = std::sqrt(m) / std::sqrt(1.0 + m);  // van Driest transform (Sec. 3, Eq. (5))
   }
   c->n_state = (size_t)nE * 5 * nnn;
+  c->n_tau = prm->equations == DG_NAVIER_STOKES ? (size_t)nE * 6 * nnn : 0;
   const bool fp32 = prm->precision == DG_FP32_BULK;
 
   double *xyz = nullptr;
@@ -706,7 +759,9 @@ dg_status dg_rhs_vjp(dg_ctx *c, const double *U, const double *lambda, double *U
   if (!c || !U || !lambda || !Ubar || Ubar == U || Ubar == lambda)
     return fail(c, DG_ERR_ARG, "dg_rhs_vjp: null or aliased arrays");
   DG_TRY(adjoint_supported(c, "dg_rhs_vjp"));
-  return vjp(c, U, lambda, Ubar, 0, 0.0, 0.0, 0.0, 0);
+  DG_TRY(tau_fill(c, 1));
+  DG_TRY(record_tau(c, U, tau_at(c, 0)));
+  return vjp(c, U, lambda, Ubar, 0, 0.0, 0.0, 0.0, 0, tau_at(c, 0));
 }
 
 dg_status dg_lserk_step_vjp(dg_ctx *c, const double *U, double *Ubar, double dt, double t) {
@@ -746,17 +801,18 @@ dg_status dg_lserk_steps_record(dg_ctx *c, double *U, double dt, double t, int n
   c->tape_id = 0;  // any earlier tape is invalid from here on
   if (interval > n_steps) interval = n_steps;
   const size_t full = 5 * (size_t)n_steps, ncp = (size_t)((n_steps + interval - 1) / interval);
-  // every stage state when the budget holds them (and the reverse sweep's 5 scratch buffers), else
-  // checkpoints every `interval` steps
-  const bool store_all = budget_allows(c, full + 5, c->tape_pool.size() + c->adj_pool.size());
+  // every stage state and its stress record when the budget holds them (and the reverse sweep's 5
+  // scratch buffers), else checkpoints every `interval` steps
+  const bool store_all = budget_allows(c, adj_bytes(c, full + 5, full), adj_held(c));
   DG_TRY(pool_fill(c, c->tape_pool, store_all ? full : ncp));
+  if (store_all && c->n_tau) DG_TRY(pool_fill(c, c->tape_tau, full, c->n_tau));
   double **T = c->tape_pool.data();
   if (store_all) {
     DG_TRY(copy_state(c, T[0], U));
     for (int k = 0; k < n_steps; ++k)
       for (int st = 0; st < 5; ++st) {
         double *out = st < 4 ? T[5 * k + st + 1] : (k + 1 < n_steps ? T[5 * (k + 1)] : U);
-        DG_TRY(stage(c, T[5 * k + st], out, 1, st, dt));
+        DG_TRY(stage(c, T[5 * k + st], out, 1, st, dt, c->n_tau ? c->tape_tau[5 * k + st] : nullptr));
       }
   } else {
     for (int j = 0; j < (int)ncp; ++j) {
@@ -785,7 +841,10 @@ dg_status dg_lserk_steps_vjp_recorded(dg_ctx *c, long long tape, double *Ubar) {
     double **T = c->tape_pool.data();
     for (int k = n_steps - 1; k >= 0; --k) {
       double *S[5] = {T[5 * k], T[5 * k + 1], T[5 * k + 2], T[5 * k + 3], T[5 * k + 4]};
-      DG_TRY(reverse_stages(c, S, Ubar, dt));
+      double *tau5[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+      if (c->n_tau)
+        for (int st = 0; st < 5; ++st) tau5[st] = c->tape_tau[5 * k + st];
+      DG_TRY(reverse_stages(c, S, tau5, Ubar, dt));
     }
     return DG_OK;
   }

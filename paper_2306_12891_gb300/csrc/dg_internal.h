@@ -70,7 +70,8 @@ struct DgKernelTable {
   void (*metrics)(const DgDevice &d, cudaStream_t s);
   void (*face_normals)(const DgDevice &d, cudaStream_t s);
   void (*face)(const DgDevice &d, const double *U, cudaStream_t s);
-  void (*lift)(const DgDevice &d, const double *U, cudaStream_t s);
+  // tau: null, or (FP64) the viscous stress record [nE][6][n^3] the lifting also writes for the adjoint
+  void (*lift)(const DgDevice &d, const double *U, double *tau, cudaStream_t s);
   // mode 0: out = Ut. mode 1: LSERK stage in place on out (== U): g = first ? dt*Ut : A g + dt*Ut;
   // U += B g.
   void (*volume)(const DgDevice &d, const double *U, double *out, double *g, int mode, int first, double dt,
@@ -85,8 +86,9 @@ struct DgKernelTable {
   // volume adjoint. mode 0: out = (dL/dU)^T lam. mode 1: reverse LSERK stage, out (= Ubar) += dt *
   // VJP, then, if update_g, gbar (== lam) = A gbar + B Ubar.
   void (*adj_face)(const DgDevice &d, const double *U, const double *lam, double *slots, cudaStream_t s);
-  void (*adj_visc)(const DgDevice &d, const double *U, const double *lam, double *cotW, double *sigma,
-                   cudaStream_t s);
+  // tau: the lifting's viscous stress record of the same state U
+  void (*adj_visc)(const DgDevice &d, const double *U, const double *lam, const double *tau, double *cotW,
+                   double *sigma, cudaStream_t s);
   void (*adj_volume)(const DgDevice &d, const double *U, const double *lam, const double *fslots, const double *cotW,
                      const double *sigma, double *out, double *gbar, int mode, double dt, double A, double B,
                      int update_g, cudaStream_t s);

@@ -588,12 +588,14 @@ __device__ __forceinline__ void lift_prim(const R Uv[5], R gm1, R iR, R pref, R 
 
 // one node's BR1 gradients and contravariant viscous flux: W = the element's lifted quantities
 // [4][nnn] (shared memory), Jae its metric terms [3 d][3 c][nnn], Wse its BR1 face jumps [6][4][nn],
-// iJ this node's 1/J; writes the element's Fv [3 d][4][nnn] at `node` (out = the element's Fv)
+// iJ this node's 1/J; writes the element's Fv [3 d][4][nnn] at `node` (out = the element's Fv).
+// tau (FP64 only, optional): the element's viscous stress record [6][nnn] (xx, yy, zz, xy, xz, yz),
+// which the adjoint's viscous kernel reads instead of forming the gradients again
 template <typename R, bool PRE = false>
 __device__ __forceinline__ void lift_node(const DgDevice &d, int node, const R *__restrict__ W,
                                           const R (*__restrict__ sD)[n + 1], const R *__restrict__ Jae,
                                           const R *__restrict__ Wse, R iJ, R mu, R kappa, R *__restrict__ out,
-                                          const R *__restrict__ S = nullptr) {
+                                          const R *__restrict__ S = nullptr, double *__restrict__ tau = nullptr) {
   // PRE: the reference derivatives D_dd w_q of this element come precomputed in S [3 dd][4 q][nnn]
   const int ijk[3] = {node % n, (node / n) % n, node / nn};
   R Ja[3][3];
@@ -648,6 +650,12 @@ __device__ __forceinline__ void lift_node(const DgDevice &d, int node, const R *
   const R t23 = R(2.0 / 3.0) * mu * div;
   const R txx = R(2) * mu * g[0][0] - t23, tyy = R(2) * mu * g[1][1] - t23, tzz = R(2) * mu * g[2][2] - t23;
   const R txy = mu * (g[0][1] + g[1][0]), txz = mu * (g[0][2] + g[2][0]), tyz = mu * (g[1][2] + g[2][1]);
+  if constexpr (std::is_same<R, double>::value) {
+    if (tau) {
+      tau[node] = txx; tau[nnn + node] = tyy; tau[2 * nnn + node] = tzz;
+      tau[3 * nnn + node] = txy; tau[4 * nnn + node] = txz; tau[5 * nnn + node] = tyz;
+    }
+  }
   R Fc[3][4];
   Fc[0][0] = txx; Fc[0][1] = txy; Fc[0][2] = txz; Fc[0][3] = u * txx + v * txy + w * txz + kappa * g[3][0];
   Fc[1][0] = txy; Fc[1][1] = tyy; Fc[1][2] = tyz; Fc[1][3] = u * txy + v * tyy + w * tyz + kappa * g[3][1];
@@ -660,7 +668,8 @@ __device__ __forceinline__ void lift_node(const DgDevice &d, int node, const R *
 }
 
 template <typename R>
-__global__ void __launch_bounds__(LIFT_THREADS, lift_min_blocks<R>()) k_lift(const DgDevice d, const double *__restrict__ U) {
+__global__ void __launch_bounds__(LIFT_THREADS, lift_min_blocks<R>()) k_lift(const DgDevice d, const double *__restrict__ U,
+                                                                             double *__restrict__ tau) {
   __shared__ R W[LIFT_EPB][4][nnn];
   __shared__ R sD[n][n + 1];  // D, rows padded: lanes read different rows without bank conflicts
   for (int t = threadIdx.x; t < nn; t += blockDim.x) sD[t / n][t % n] = Tab<R>::D(t);
@@ -687,7 +696,8 @@ __global__ void __launch_bounds__(LIFT_THREADS, lift_min_blocks<R>()) k_lift(con
     if (e >= d.nE) continue;
     const R iJ = kShift<R> ? (R)d.invJf[(size_t)e * nnn + node] : (R)d.invJ[(size_t)e * nnn + node];
     lift_node<R>(d, node, &W[le][0][0], sD, Buf<R>::Ja(d) + (size_t)e * 9 * nnn,
-                 Buf<R>::Wsurf(d) + (size_t)e * 6 * 4 * nn, iJ, mu, kappa, Buf<R>::Fv(d) + (size_t)e * 12 * nnn);
+                 Buf<R>::Wsurf(d) + (size_t)e * 6 * 4 * nn, iJ, mu, kappa, Buf<R>::Fv(d) + (size_t)e * 12 * nnn,
+                 nullptr, tau ? tau + (size_t)e * 6 * nnn : nullptr);
   }
 }
 
@@ -699,7 +709,8 @@ __global__ void __launch_bounds__(LIFT_THREADS, lift_min_blocks<R>()) k_lift(con
 // W [EPB][4][nnn] and S [EPB][3][4][nnn] doubles.
 constexpr size_t LIFT_LINES_SMEM = sizeof(double) * LIFT_EPB * 16 * nnn;
 __global__ void __launch_bounds__(LIFT_THREADS, lift_min_blocks<double>()) k_lift_lines(const DgDevice d,
-                                                                                      const double *__restrict__ U) {
+                                                                                      const double *__restrict__ U,
+                                                                                      double *__restrict__ tau) {
   if constexpr (n % 2 == 0) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     double *W = reinterpret_cast<double *>(sm_raw);  // [EPB][4][nnn]
@@ -758,7 +769,8 @@ __global__ void __launch_bounds__(LIFT_THREADS, lift_min_blocks<double>()) k_lif
       if (e >= d.nE) continue;
       lift_node<double, true>(d, node, W + le * 4 * nnn, sD, d.Ja + (size_t)e * 9 * nnn,
                               d.Wsurf + (size_t)e * 6 * 4 * nn, d.invJ[(size_t)e * nnn + node], mu, kappa,
-                              d.Fv + (size_t)e * 12 * nnn, S + le * 12 * nnn);
+                              d.Fv + (size_t)e * 12 * nnn, S + le * 12 * nnn,
+                              tau ? tau + (size_t)e * 6 * nnn : nullptr);
     }
   }
 }
@@ -1437,7 +1449,7 @@ void launch_face(const DgDevice &d, const double *U, cudaStream_t s) {
   else launch_face_t<double>(d, U, s);
 }
 
-void launch_lift(const DgDevice &d, const double *U, cudaStream_t s) {
+void launch_lift(const DgDevice &d, const double *U, double *tau, cudaStream_t s) {
   if (TMA_OK && d.precision == 1 && d.use_tma) {  // FP32-bulk: the TMA-fed persistent form
     static int grid_lt = 0;
     if (!grid_lt) {
@@ -1454,16 +1466,16 @@ void launch_lift(const DgDevice &d, const double *U, cudaStream_t s) {
   }
   const unsigned grid = (d.nE + LIFT_EPB - 1) / LIFT_EPB;
   if (d.precision == 1) {
-    k_lift<float><<<grid, LIFT_THREADS, 0, s>>>(d, U);
+    k_lift<float><<<grid, LIFT_THREADS, 0, s>>>(d, U, nullptr);
   } else if (n == 8) {  // measured faster at N = 7 (7.32 -> 7.00 ms at 32^3); slower at N = 5 (+3 %)
     static bool attr_set = false;
     if (!attr_set) {
       cudaFuncSetAttribute(k_lift_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LIFT_LINES_SMEM);
       attr_set = true;
     }
-    k_lift_lines<<<grid, LIFT_THREADS, LIFT_LINES_SMEM, s>>>(d, U);
+    k_lift_lines<<<grid, LIFT_THREADS, LIFT_LINES_SMEM, s>>>(d, U, tau);
   } else {
-    k_lift<double><<<grid, LIFT_THREADS, 0, s>>>(d, U);
+    k_lift<double><<<grid, LIFT_THREADS, 0, s>>>(d, U, tau);
   }
 }
 
