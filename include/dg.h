@@ -114,7 +114,10 @@ dg_status dg_lserk_step(dg_ctx *ctx, double *U, double dt, double t);
 dg_status dg_lserk_steps(dg_ctx *ctx, double *U, double dt, double t, int n_steps);
 
 /* The same step on a HOST array U_host: copies it to a library-owned device buffer, steps, and
- * copies the result back; synchronising. U_host should be pinned for full copy bandwidth. */
+ * returns the result in U_host; synchronising. Page-locked U_host (16-byte aligned, a whole number of
+ * 16-byte words) is read by a copy kernel over the host link, and the last stage's volume kernel
+ * writes the new state straight into it; other host memory goes through the copy engines both ways.
+ * The bits equal dg_lserk_step's. DG_ERR_ARG for a null array or a non-finite dt. */
 dg_status dg_lserk_step_host(dg_ctx *ctx, double *U_host, double dt, double t);
 
 /* alpha[e] = blending coefficient of element e (Sec. 4.1, Eq. (7): modified Persson indicator on

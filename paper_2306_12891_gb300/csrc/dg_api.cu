@@ -703,16 +703,24 @@ dg_status copy_split(dg_ctx *c, void *dst, const void *src, size_t bytes, cudaMe
 // a host <-> device copy of the state: page-locked host memory that the device can address is copied by
 // k_copy16 on the context stream (the SMs keep many 16-byte loads in flight over the host-device link);
 // other host memory, or an unaligned buffer, by copy engines (copy_split)
-dg_status copy_state_host(dg_ctx *c, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind) {
-  const void *host = kind == cudaMemcpyHostToDevice ? src : dst;
+// the device's address of page-locked host memory `host` when it is 16-byte aligned and `bytes` is a
+// multiple of 16, else null (other host memory, or a failed query, whose error is not left behind)
+void *host_device_pointer(const void *host, size_t bytes) {
   cudaPointerAttributes a{};
-  void *hdev = nullptr;
   const cudaError_t qe = cudaPointerGetAttributes(&a, host);
-  if (qe != cudaSuccess) cudaGetLastError();  // the query's own error: not left behind for the caller
-  else if (a.type == cudaMemoryTypeHost && a.devicePointer && bytes % 16 == 0 &&
-           (reinterpret_cast<uintptr_t>(a.devicePointer) & 15u) == 0 &&
-           (reinterpret_cast<uintptr_t>(kind == cudaMemcpyHostToDevice ? dst : src) & 15u) == 0)
-    hdev = a.devicePointer;
+  if (qe != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeHost && a.devicePointer && bytes % 16 == 0 &&
+      (reinterpret_cast<uintptr_t>(a.devicePointer) & 15u) == 0)
+    return a.devicePointer;
+  return nullptr;
+}
+
+dg_status copy_state_host(dg_ctx *c, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind) {
+  void *hdev = host_device_pointer(kind == cudaMemcpyHostToDevice ? src : dst, bytes);
+  if (hdev && (reinterpret_cast<uintptr_t>(kind == cudaMemcpyHostToDevice ? dst : src) & 15u)) hdev = nullptr;
   if (!hdev) return copy_split(c, dst, src, bytes, kind);
   const uint4 *from = static_cast<const uint4 *>(kind == cudaMemcpyHostToDevice ? hdev : src);
   uint4 *to = static_cast<uint4 *>(kind == cudaMemcpyHostToDevice ? dst : hdev);
@@ -744,11 +752,21 @@ dg_status dg_lserk_steps(dg_ctx *c, double *U, double dt, double t, int n_steps)
 
 dg_status dg_lserk_step_host(dg_ctx *c, double *U_host, double dt, double t) {
   if (!c || !U_host) return fail(c, DG_ERR_ARG, "dg_lserk_step_host: null array");
+  if (!std::isfinite(dt)) return fail(c, DG_ERR_ARG, "dg_lserk_step_host: bad argument");
   if (!c->Ustage) DG_TRY(dev_alloc(c, &c->Ustage, c->n_state));
   const size_t bytes = sizeof(double) * c->n_state;
   DG_TRY(copy_state_host(c, c->Ustage, U_host, bytes, cudaMemcpyHostToDevice));
-  DG_TRY(dg_lserk_step(c, c->Ustage, dt, t));
-  DG_TRY(copy_state_host(c, U_host, c->Ustage, bytes, cudaMemcpyDeviceToHost));
+  if (double *hdev = static_cast<double *>(host_device_pointer(U_host, bytes))) {
+    // page-locked host state: the last stage's volume kernel writes the new state straight into it
+    // over the host link, spread over the kernel's run, instead of a copy after it (same kernels,
+    // same bits)
+    DG_TRY(refresh_shadow(c, c->Ustage));
+    DG_TRY(ensure_stage_factor(c, dt));
+    for (int st = 0; st < 5; ++st) DG_TRY(stage(c, c->Ustage, st < 4 ? c->Ustage : hdev, 1, st, dt));
+  } else {
+    DG_TRY(dg_lserk_step(c, c->Ustage, dt, t));
+    DG_TRY(copy_state_host(c, U_host, c->Ustage, bytes, cudaMemcpyDeviceToHost));
+  }
   const cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e) return cuda_fail(c, e, "D2H");
   return DG_OK;

@@ -234,6 +234,26 @@ def test_host_buffer_step_with_a_size_not_a_multiple_of_16_bytes(env):
     assert torch.equal(Uh, U.cpu())
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+def test_host_buffer_step_navier_stokes_n7(env, precision):
+    """With a page-locked host state the last stage's volume kernel writes the new state straight into
+    host memory: the same bits as the device step, for the FP64 and the FP32-bulk kernels at N = 7,
+    over consecutive calls (each call uploads its own input)."""
+    dg, orc, torch = env
+    w = W.WORKLOADS["tgv_ns_n7_32x32x32_curved"].with_(nel=(3, 3, 3))
+    xyz, faces = w.mesh()
+    U0 = w.initial_state(xyz)
+    gpu = dg.DG(w.N, xyz, faces, precision=precision, **w.physics())
+    U = torch.from_numpy(U0).cuda()
+    dt = gpu.max_dt(U, w.cfl)
+    Uh = torch.from_numpy(U0.copy()).pin_memory()
+    for _ in range(3):
+        gpu.lserk_step(U, dt)
+        gpu.lserk_step_host(Uh, dt)
+        assert torch.equal(Uh, U.cpu())
+    gpu.check()
+
+
 # ------------------------------------------------------------------ full-size workloads, sampled outputs
 
 @pytest.mark.parametrize("name,extra", [("tgv_ns_n7_32x32x32_curved", {}), ("blast_euler_fv_n5_64x64x64", {}),
