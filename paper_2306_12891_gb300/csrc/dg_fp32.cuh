@@ -787,21 +787,13 @@ __global__ void __launch_bounds__(LN_THREADS, 1) k_volume_f32_line(const DgDevic
             float fv[n];
 #pragma unroll
             for (int m = 0; m < n; ++m) fv[m] = Fb[(dd * 4 + q) * nnn + base + m * st];
-            // even-odd halves of the zero-diagonal D (centro-antisymmetric): 48 instead of 56
-            // operations per line and quantity
-            float ev[EO_H], od[EO_H];
 #pragma unroll
-            for (int m = 0; m < EO_H; ++m) { ev[m] = fv[m] + fv[N - m]; od[m] = fv[m] - fv[N - m]; }
+            for (int i = 0; i < n; ++i) {
+              float t = 0.0f;
 #pragma unroll
-            for (int i = 0; i < EO_H; ++i) {
-              float a = 0.0f, b = 0.0f;
-#pragma unroll
-              for (int m = 0; m < EO_H; ++m) {
-                a += f_VP[i * EO_H + m] * ev[m];
-                b += f_VM[i * EO_H + m] * od[m];
-              }
-              acc[i][1 + q] -= ISC1 * (a + b);
-              acc[N - i][1 + q] -= ISC1 * (b - a);
+              for (int m = 0; m < n; ++m)
+                if (m != i) t += f_D[i * n + m] * fv[m];
+              acc[i][1 + q] -= ISC1 * t;
             }
             const float sg0 = (rec[0].y & 1) ? 0.5f : -0.5f, sg1 = (rec[1].y & 1) ? 0.5f : -0.5f;
             acc[0][1 + q] += wall[0] ? -(ISC1 * iw0) * (fnb[0][q] + 0.5f * fv[0]) : (ISC1 * iw0 * sg0) * fnb[0][q];
