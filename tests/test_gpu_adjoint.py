@@ -233,6 +233,44 @@ def test_recorded_run_reverses_to_the_same_bits(env):
     gpu.check()
 
 
+def test_recording_budget_counts_the_stress_records(env):
+    """A Navier-Stokes recording keeps each stage state with the lifting's viscous stress record (6/5 of a
+    state): under a budget that holds the states but not their records it keeps checkpoints instead,
+    and both recordings reverse to the same bits as the checkpointed sweep from U0."""
+    dg, orc, torch = env
+    w = W.WORKLOADS["tgv_ns_n5_24x24x24_adjoint"].with_(nel=(4, 4, 4))
+    xyz, faces = w.mesh()
+    U0 = torch.from_numpy(w.initial_state(xyz)).cuda()
+    S = U0.numel() * 8
+    T = S // 5 * 6
+    K = 4
+    full = 5 * K
+    ref = _gpu(env, w.N, xyz, faces, **w.physics())
+    dt = ref.max_dt(U0, w.cfl)
+    seed = ref.kinetic_energy_grad(ref.lserk_steps(U0.clone(), dt, K))
+    want = seed.clone()
+    ref.lserk_steps_vjp(U0, want, dt, K, 2)
+    grown = []
+    for limit in ((full + 5) * S + full * T - 1, (full + 5) * S + full * T):
+        gpu = _gpu(env, w.N, xyz, faces, **w.physics())
+        gpu.adjoint_memory_limit(float(limit))
+        U = U0.clone()
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        tape = gpu.lserk_steps_record(U, dt, K, 2)
+        torch.cuda.synchronize()
+        grown.append(free0 - torch.cuda.mem_get_info()[0])
+        Ub = seed.clone()
+        gpu.lserk_steps_vjp_recorded(tape, Ub)
+        assert torch.equal(Ub, want)
+        gpu.check()
+        gpu.close()
+    # one byte short: two checkpoints only (1.1 MB; allocation granularity may round it up to a few
+    # MB); at the limit: every stage state and its record (24 MB)
+    assert grown[0] < 0.25 * full * (S + T), grown
+    assert grown[1] >= 0.9 * full * (S + T), grown
+
+
 def _ke_complex(U, J, w):
     """Kinetic-energy integral of a complex state (analytic continuation, no conjugation)."""
     wq = np.einsum("k,j,i->kji", w, w, w)[None] * J
