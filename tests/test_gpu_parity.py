@@ -217,6 +217,11 @@ def test_host_buffer_step_equals_device_step(env):
     Uo.copy_(torch.from_numpy(U0))
     gpu.lserk_step_host(Uo, 1e-3)
     assert torch.equal(Uo, U.cpu())
+    # a non-finite step size is refused before anything is copied
+    with pytest.raises(dg.DGError) as ei:
+        gpu.lserk_step_host(Uo, float("nan"))
+    assert ei.value.status == -1
+    assert torch.equal(Uo, U.cpu())
 
 
 def test_host_buffer_step_with_a_size_not_a_multiple_of_16_bytes(env):
