@@ -611,20 +611,19 @@ __device__ __forceinline__ void lift_node(const DgDevice &d, int node, const R *
     const int id = ijk[dd];
     const int st = dd == 0 ? 1 : dd == 1 ? n : nn;
     const int base = node - id * st;
+    // the reference derivative along dd, plus the surface term (1/w_b)(+-)(w* - w) on the face of
+    // direction dd through this node, before the one contraction with Ja^dd
+    R s[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      R s = R(0);
+      s[q] = R(0);
       if constexpr (PRE) {
-        s = S[(dd * 4 + q) * nnn + node];
+        s[q] = S[(dd * 4 + q) * nnn + node];
       } else {
 #pragma unroll
-        for (int m = 0; m < n; ++m) s += sD[id][m] * W[q * nnn + base + m * st];
+        for (int m = 0; m < n; ++m) s[q] += sD[id][m] * W[q * nnn + base + m * st];
       }
-      g[q][0] += Ja[dd][0] * s;
-      g[q][1] += Ja[dd][1] * s;
-      g[q][2] += Ja[dd][2] * s;
     }
-    // surface terms on the faces of direction dd through this node
     if (id == 0 || id == N) {
       const int f = 2 * dd + (id == N ? 1 : 0);
       const R sc = (id == N ? R(1) : R(-1)) * Tab<R>::invw(id);
@@ -632,12 +631,13 @@ __device__ __forceinline__ void lift_node(const DgDevice &d, int node, const R *
       const int qq = dd == 2 ? ijk[1] : ijk[2];
       const R *js = Wse + f * 4 * nn + pp + n * qq;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const R jq = sc * js[q * nn];
-        g[q][0] += Ja[dd][0] * jq;
-        g[q][1] += Ja[dd][1] * jq;
-        g[q][2] += Ja[dd][2] * jq;
-      }
+      for (int q = 0; q < 4; ++q) s[q] += sc * js[q * nn];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      g[q][0] += Ja[dd][0] * s[q];
+      g[q][1] += Ja[dd][1] * s[q];
+      g[q][2] += Ja[dd][2] * s[q];
     }
   }
   // g holds J grad w; the flux below is linear in grad w, so 1/J goes into mu and kappa (two
