@@ -111,9 +111,9 @@ def face_kernel_flops_per_point() -> float:
 def adjoint_volume_flops_per_element(N: int, navier_stokes: bool) -> float:
     """Algorithmic FP64 flops of one adjoint-volume launch per element (FMA = 2 flops), counted from
     the statements of the kernel:
-      pair (KG/Pirozzoli transposed): 9 sums, 5 pair cotangents c_v (2 mul + add = 15), V 5, F0 1,
-        d(c.F)/dF0 8, gV 1, gP 5, the six primitive cotangents 12, accumulation into both nodes 12
-        -> 67 per pair, 3 n^2 n(n-1)/2 pairs per element;
+      pair (KG/Pirozzoli transposed): 9 sums, 5 pair cotangents t_v = l_i + (D_mi/D_im) l_m (FMA,
+        10), V 5, F0 scaled by D_im/8 2, d(c.F)/dF0 9, gV 1, gP 6, the six primitive cotangents 12,
+        accumulation into both nodes 12 -> 65 per pair, 3 n^2 n(n-1)/2 pairs per element;
       per node: primitives and l = -lambda/J 20, direction sum 12, chain to U 25, reverse LSERK 20,
         Navier-Stokes: T chain 6 and the neighbours' face shares 4 per face point;
       per face point: 5 additions of the face slots."""
@@ -121,7 +121,7 @@ def adjoint_volume_flops_per_element(N: int, navier_stokes: bool) -> float:
     pairs = 3 * n * n * n * (n - 1) // 2
     per_node = 20 + 12 + 25 + 20 + (6 if navier_stokes else 0)
     per_face_pt = 5 + (4 if navier_stokes else 0)
-    return 67.0 * pairs + per_node * n ** 3 + per_face_pt * 6 * n * n
+    return 65.0 * pairs + per_node * n ** 3 + per_face_pt * 6 * n * n
 
 
 def adjoint_visc_flops_per_element(N: int) -> float:

@@ -148,7 +148,7 @@ __device__ void roe_vjp(const double UL[5], const double UR[5], const double nv[
   // reverse: F = (FL + FR - D) / 2
   double cD[5], hF[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) { cD[v] = -0.5 * cF[v]; hF[v] = 0.5 * cF[v]; }
+  for (int v = 0; v < 5; ++v) { hF[v] = 0.5 * cF[v]; cD[v] = -hF[v]; }
   double cnt = cD[1] * nv[0] + cD[2] * nv[1] + cD[3] * nv[2];  // sum_k cD_k n_k
   double cut_dot = cD[1] * ut[0] + cD[2] * ut[1] + cD[3] * ut[2];
   const double c_l1a1 = cD[0] + cut_dot - ct * cnt + cD[4] * (Ht - unt * ct);
@@ -195,20 +195,19 @@ __device__ void roe_vjp(const double UL[5], const double UR[5], const double nv[
   c_q2 -= 0.5 * gm1 * c_c2;
 #pragma unroll
   for (int k = 0; k < 3; ++k) c_ut[k] += 2.0 * ut[k] * c_q2;
-  double c_sL = c_rt * sR + c_Ht * hL * iw, c_sR = c_rt * sL + c_Ht * hR * iw;
-  double c_iw = c_Ht * (sL * hL + sR * hR);
-  const double c_hL = c_Ht * sL * iw, c_hR = c_Ht * sR * iw;
+  // the weights: d ut/d sL = iw (uL - ut), d Ht/d sL = iw (hL - Ht) (the same for R), d ut/d uL = sL iw
+  double xL = c_Ht * (hL - Ht), xR = c_Ht * (hR - Ht);
+  const double wL = sL * iw, wR = sR * iw;
+  const double c_hL = c_Ht * wL, c_hR = c_Ht * wR;
   double cuL[3], cuR[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    c_sL += c_ut[k] * L.u[k] * iw;
-    c_sR += c_ut[k] * R.u[k] * iw;
-    c_iw += c_ut[k] * (sL * L.u[k] + sR * R.u[k]);
-    cuL[k] = c_ut[k] * sL * iw - c_du[k];
-    cuR[k] = c_ut[k] * sR * iw + c_du[k];
+    xL += c_ut[k] * (L.u[k] - ut[k]);
+    xR += c_ut[k] * (R.u[k] - ut[k]);
+    cuL[k] = c_ut[k] * wL - c_du[k];
+    cuR[k] = c_ut[k] * wR + c_du[k];
   }
-  c_sL -= c_iw * iw * iw;
-  c_sR -= c_iw * iw * iw;
+  const double c_sL = c_rt * sR + iw * xL, c_sR = c_rt * sL + iw * xR;
   // enthalpies h = (E + p) ir
   double cpL = -c_dp + c_hL * L.ir, cpR = c_dp + c_hR * R.ir;
   double cirL = c_hL * EpL, cirR = c_hR * EpR;
@@ -366,10 +365,9 @@ __global__ void __launch_bounds__(LIFT_THREADS) k_adj_visc(const DgDevice d, con
         int nb, fnb, nbnode, nbpq;
         neighbour_node(d, e, f, pp, qq, nb, fnb, nbnode, nbpq);
         const double sgf = (f & 1) ? 0.5 : -0.5;
-        const double miJn = -d.invJ[(size_t)nb * nnn + nbnode];
+        const double kn = c_invw[id] * sgf * -d.invJ[(size_t)nb * nnn + nbnode];  // (1/w_b)(+-1/2) l = -lam/J
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          zeta[dd][q] += c_invw[id] * sgf * (miJn * lam[((size_t)nb * 5 + 1 + q) * nnn + nbnode]);
+        for (int q = 0; q < 4; ++q) zeta[dd][q] += kn * lam[((size_t)nb * 5 + 1 + q) * nnn + nbnode];
       }
     }
     double Ja[3][3];
@@ -488,32 +486,35 @@ __device__ __forceinline__ AdjNode adj_node(const double *__restrict__ P, const 
   return q;
 }
 
-// the six primitive cotangents of the pair (i, m), shared by both nodes
+// the six primitive cotangents of the pair (i, m), shared by both nodes. The pair cotangents
+// c_v = D'_im l_i,v + D'_mi l_m,v are D'_im t_v with t_v = l_i,v + (D_mi/D_im) l_m,v (the mass part's
+// factor 2, D/4 against D/8, is in the staged l_0); D'_im = D_im/8 then scales phi, the pressure
+// cotangent and F0 once instead of every c_v.
 template <int VF>
-__device__ __forceinline__ void adj_pair(const AdjNode &a, const AdjNode &b, double dqi, double dqm, double dei,
-                                         double dem, double g[6]) {
+__device__ __forceinline__ void adj_pair(const AdjNode &a, const AdjNode &b, double de, double dr, double g[6]) {
   const double Sr = a.r + b.r, Su = a.u + b.u, Sv = a.v + b.v, Sw = a.w + b.w;
   const double Sp = a.p + b.p, Sx = a.x + b.x;
   const double Sjx = a.jx + b.jx, Sjy = a.jy + b.jy, Sjz = a.jz + b.jz;
-  const double c0 = dqi * a.l[0] + dqm * b.l[0];
-  const double c1 = dei * a.l[1] + dem * b.l[1];
-  const double c2 = dei * a.l[2] + dem * b.l[2];
-  const double c3 = dei * a.l[3] + dem * b.l[3];
-  const double c4 = dei * a.l[4] + dem * b.l[4];
+  const double t0 = a.l[0] + dr * b.l[0];
+  const double t1 = a.l[1] + dr * b.l[1];
+  const double t2 = a.l[2] + dr * b.l[2];
+  const double t3 = a.l[3] + dr * b.l[3];
+  const double t4 = a.l[4] + dr * b.l[4];
   const double Vp = Su * Sjx + Sv * Sjy + Sw * Sjz;
-  const double F0 = Sr * Vp;
-  const double phi = c0 + c1 * Su + c2 * Sv + c3 * Sw + c4 * Sx;  // d(c.F)/dF0
-  double gV = phi * Sr, gP = c1 * Sjx + c2 * Sjy + c3 * Sjz;
+  const double F0 = de * (Sr * Vp);                                   // D'_im F0
+  const double phi = de * (t0 + t1 * Su + t2 * Sv + t3 * Sw + t4 * Sx);  // d(c.F)/dF0
+  double gV = phi * Sr, gP = de * (t1 * Sjx + t2 * Sjy + t3 * Sjz);
   if (VF == VF_KG) {
+    const double c4 = de * t4;
     gV += 0.5 * c4 * Sp;
     gP += 0.5 * c4 * Vp;
   }
   g[0] = phi * Vp;
-  g[1] = c1 * F0 + gV * Sjx;
-  g[2] = c2 * F0 + gV * Sjy;
-  g[3] = c3 * F0 + gV * Sjz;
+  g[1] = t1 * F0 + gV * Sjx;
+  g[2] = t2 * F0 + gV * Sjy;
+  g[3] = t3 * F0 + gV * Sjz;
   g[4] = gP;
-  g[5] = c4 * F0;
+  g[5] = t4 * F0;
 }
 
 // Transposed flux differencing along one line, two rows at a time (as the forward line_fluxdiff2):
@@ -534,7 +535,7 @@ __device__ __forceinline__ void adj_line(const double *__restrict__ P, const dou
     }
     {
       double g[6];
-      adj_pair<VF>(n0, n1, c_Dq[i * n + i + 1], c_Dq[(i + 1) * n + i], c_De[i * n + i + 1], c_De[(i + 1) * n + i], g);
+      adj_pair<VF>(n0, n1, c_De[i * n + i + 1], c_Dr[i * n + i + 1], g);
 #pragma unroll
       for (int v = 0; v < 6; ++v) { ac0[v] += g[v]; ac1[v] += g[v]; }
     }
@@ -543,8 +544,8 @@ __device__ __forceinline__ void adj_line(const double *__restrict__ P, const dou
       const int am = pb + m * ps;
       const AdjNode nm = adj_node(P, Lm, am, Jd, gb + m * gs);
       double g0[6], g1[6];
-      adj_pair<VF>(n0, nm, c_Dq[i * n + m], c_Dq[m * n + i], c_De[i * n + m], c_De[m * n + i], g0);
-      adj_pair<VF>(n1, nm, c_Dq[(i + 1) * n + m], c_Dq[m * n + i + 1], c_De[(i + 1) * n + m], c_De[m * n + i + 1], g1);
+      adj_pair<VF>(n0, nm, c_De[i * n + m], c_Dr[i * n + m], g0);
+      adj_pair<VF>(n1, nm, c_De[(i + 1) * n + m], c_Dr[(i + 1) * n + m], g1);
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
         ac0[v] += g0[v];
@@ -575,12 +576,19 @@ __global__ void __launch_bounds__(ADJ_THREADS, ADJ_MINB) k_adj_volume(const DgDe
   double *Acc = Lm + ADJ_EPB * 5 * PS;             // [EPB][3][6][PS]
   const int e0 = blockIdx.x * ADJ_EPB;
   const double gam = d.gamma, gm1 = gam - 1.0;
-  for (int t = threadIdx.x; t < ADJ_EPB * nnn; t += blockDim.x) {
+  // the thread's nodes (the same in staging and in the per-node part): their 1/rho stays in registers
+  constexpr int RN = (ADJ_EPB * nnn + ADJ_THREADS - 1) / ADJ_THREADS;
+  double irr[RN];
+#pragma unroll
+  for (int rr = 0; rr < RN; ++rr) {
+    const int t = threadIdx.x + rr * ADJ_THREADS;
+    if (t >= ADJ_EPB * nnn) continue;
     const int le = t / nnn, node = t % nnn, e = e0 + le;
     if (e >= d.nE) continue;
     double Uv[5];
     load_state<double>(d, U, e, node, Uv);
     const double r = Uv[0], ir = 1.0 / r;
+    irr[rr] = ir;
     const double u = Uv[1] * ir, v = Uv[2] * ir, w = Uv[3] * ir;
     const double p = gm1 * (Uv[4] - 0.5 * (Uv[1] * u + Uv[2] * v + Uv[3] * w));
     if (!(r > 0.0) || !(p > 0.0) || !isfinite(Uv[4])) flag_set(d.flag, 1);
@@ -589,8 +597,10 @@ __global__ void __launch_bounds__(ADJ_THREADS, ADJ_MINB) k_adj_volume(const DgDe
     Pe[0] = r; Pe[PS] = u; Pe[2 * PS] = v; Pe[3 * PS] = w; Pe[4 * PS] = 4.0 * p;
     Pe[5 * PS] = VF == VF_PIR ? (Uv[4] + p) * ir : Uv[4] * ir;
     const double miJ = -d.invJ[(size_t)e * nnn + node];
+    // l = -lambda/J; the mass component doubled (its split-form factor is D/4, the others' D/8)
 #pragma unroll
-    for (int k = 0; k < 5; ++k) Lm[(le * 5 + k) * PS + pn] = miJ * lam[((size_t)e * 5 + k) * nnn + node];
+    for (int k = 0; k < 5; ++k)
+      Lm[(le * 5 + k) * PS + pn] = (k == 0 ? 2.0 * miJ : miJ) * lam[((size_t)e * 5 + k) * nnn + node];
   }
   __syncthreads();
   for (int t = threadIdx.x; t < ADJ_EPB * 3 * nn; t += blockDim.x) {
@@ -604,19 +614,22 @@ __global__ void __launch_bounds__(ADJ_THREADS, ADJ_MINB) k_adj_volume(const DgDe
   __syncthreads();
   const bool ns = d.equations == 1;
   const double iR = 1.0 / d.R;
-  for (int t = threadIdx.x; t < ADJ_EPB * nnn; t += blockDim.x) {
+#pragma unroll
+  for (int rr = 0; rr < RN; ++rr) {
+    const int t = threadIdx.x + rr * ADJ_THREADS;
+    if (t >= ADJ_EPB * nnn) continue;
     const int le = t / nnn, node = t % nnn, e = e0 + le;
     if (e >= d.nE) continue;
     const int ijk[3] = {node % n, (node / n) % n, node / nn};
     const int pn = pidx(node);
     const double *Pe = P + le * ADJ_NP * PS + pn;
-    const double r = Pe[0], u[3] = {Pe[PS], Pe[2 * PS], Pe[3 * PS]}, p = 0.25 * Pe[4 * PS], X = Pe[5 * PS];
+    const double u[3] = {Pe[PS], Pe[2 * PS], Pe[3 * PS]}, p = 0.25 * Pe[4 * PS], X = Pe[5 * PS];
     double gp[6];
 #pragma unroll
     for (int v = 0; v < 6; ++v)
       gp[v] = Acc[(le * 3 + 0) * ADJ_NP * PS + v * PS + pn] + Acc[(le * 3 + 1) * ADJ_NP * PS + v * PS + pn] +
               Acc[(le * 3 + 2) * ADJ_NP * PS + v * PS + pn];
-    const double ir = 1.0 / r;
+    const double ir = irr[rr];
     double g_r = gp[0], g_u[3] = {gp[1], gp[2], gp[3]}, g_p = 4.0 * gp[4];
     const double g_x = gp[5];
     if (ns) {  // cotangents of (u, v, w, T) from the viscous adjoint, own part + the neighbours' face shares
@@ -641,22 +654,17 @@ __global__ void __launch_bounds__(ADJ_THREADS, ADJ_MINB) k_adj_volume(const DgDe
       g_p += cw[3] * ir * iR;         // T = p / (rho R)
       g_r -= cw[3] * p * ir * ir * iR;
     }
-    // chain to U = (rho, m, E): u = m / rho, p = (gamma-1)(E - |m|^2 / (2 rho)), X = h or e
+    // chain to U = (rho, m, E): u = m / rho, p = (gamma-1)(E - |m|^2 / (2 rho)), X = h = (E + p)/rho
+    // (Pirozzoli) or e = E/rho (KG). With gx = g_X/rho, p reaches U with weight a = (gamma-1) g_p, and
+    // for h also through E + p: a = (gamma-1)(g_p + gx), and dh/dE = gamma/rho = (gamma-1)/rho + 1/rho
     const double q2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const double gx = g_x * ir;
+    const double a = VF == VF_PIR ? gm1 * (g_p + gx) : gm1 * g_p;
     double gU[5];
-    gU[0] = g_r - ir * (g_u[0] * u[0] + g_u[1] * u[1] + g_u[2] * u[2]) + g_p * gm1 * 0.5 * q2;
+    gU[0] = g_r - ir * (g_u[0] * u[0] + g_u[1] * u[1] + g_u[2] * u[2]) + (0.5 * a) * q2 - gx * X;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) gU[1 + k] = ir * g_u[k] - g_p * gm1 * u[k];
-    gU[4] = g_p * gm1;
-    if (VF == VF_PIR) {  // h = (E + p) / rho
-      gU[0] += g_x * ir * (gm1 * 0.5 * q2 - X);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) gU[1 + k] -= g_x * ir * gm1 * u[k];
-      gU[4] += g_x * ir * gam;
-    } else {  // e = E / rho
-      gU[0] -= g_x * ir * X;
-      gU[4] += g_x * ir;
-    }
+    for (int k = 0; k < 3; ++k) gU[1 + k] = ir * g_u[k] - a * u[k];
+    gU[4] = a + gx;
     // advective surface terms: transposed Riemann-flux Jacobians in this element's face slots
 #pragma unroll
     for (int dd = 0; dd < 3; ++dd) {

@@ -51,6 +51,7 @@ __constant__ double c_D[nn];      // D_im
 __constant__ double c_D2[nn];     // 2 D_im, zero diagonal
 __constant__ double c_Dq[nn];     // D_im / 4 (scaled mass flux), zero diagonal
 __constant__ double c_De[nn];     // D_im / 8 (scaled momentum / energy flux), zero diagonal
+__constant__ double c_Dr[nn];     // D_mi / D_im (i != m; the LGL D has no zero off the diagonal), zero diagonal
 __constant__ double c_w[n], c_invw[n], c_xi[n], c_xh[n + 1];
 __constant__ double c_ihx[n];  // 1 / (xi_i - xi_{i-1}), i = 1..N (minmod slopes)
 // even-odd halves of the zero-diagonal D (n even, h = n/2): the LGL D is centro-antisymmetric,
@@ -1359,7 +1360,7 @@ __global__ void __launch_bounds__(256) k_max_dt(const DgDevice d, const double *
 // ---------------------------------------------------------------------------------------------
 cudaError_t upload(const DgTables &t) {
   if (t.N != N) return cudaErrorInvalidValue;
-  double D2[nn], Dq[nn], De[nn];
+  double D2[nn], Dq[nn], De[nn], Dr[nn];
   float fD[nn], fD2[nn], fDq[nn], fDe[nn], fw[n], finvw[n], fxi[n], fxh[n + 1];
   for (int i = 0; i < n; ++i)
     for (int m = 0; m < n; ++m) {
@@ -1367,6 +1368,7 @@ cudaError_t upload(const DgTables &t) {
       D2[i * n + m] = 2.0 * v;
       Dq[i * n + m] = 0.25 * v;
       De[i * n + m] = 0.125 * v;
+      Dr[i * n + m] = (i == m) ? 0.0 : t.D[m * n + i] / t.D[i * n + m];
       fD[i * n + m] = (float)t.D[i * n + m];
       fD2[i * n + m] = (float)D2[i * n + m];
       fDq[i * n + m] = (float)Dq[i * n + m];
@@ -1405,6 +1407,7 @@ cudaError_t upload(const DgTables &t) {
   err = err ? err : cudaMemcpyToSymbol(c_D2, D2, sizeof(double) * nn);
   err = err ? err : cudaMemcpyToSymbol(c_Dq, Dq, sizeof(double) * nn);
   err = err ? err : cudaMemcpyToSymbol(c_De, De, sizeof(double) * nn);
+  err = err ? err : cudaMemcpyToSymbol(c_Dr, Dr, sizeof(double) * nn);
   err = err ? err : cudaMemcpyToSymbol(c_w, t.w, sizeof(double) * n);
   err = err ? err : cudaMemcpyToSymbol(c_invw, t.invw, sizeof(double) * n);
   err = err ? err : cudaMemcpyToSymbol(c_xi, t.xi, sizeof(double) * n);
