@@ -339,12 +339,15 @@ __device__ __forceinline__ void riemann(int sf, const R UL[5], const R UR[5], co
   const R dut = du - dun * nv[0], dvt = dv - dun * nv[1], dwt = dw - dun * nv[2];
   const R l1a1 = fabs(unt - ct) * a1, l5a5 = fabs(unt + ct) * a5, l2 = fabs(unt);
   const R l2a2 = l2 * a2, l2r = l2 * rt;
+  // dissipation sum_k |lambda_k| alpha_k r_k, collected: with s15 = l1a1 + l5a5 and c15 = c (l5a5 - l1a1),
+  // the two acoustic waves give s15 (u~, H~) + c15 (n, u~_n)
+  const R s15 = l1a1 + l5a5, c15 = ct * (l5a5 - l1a1);
   R D[5];
-  D[0] = l1a1 + l5a5 + l2a2;
-  D[1] = l1a1 * (ut - ct * nv[0]) + l5a5 * (ut + ct * nv[0]) + l2a2 * ut + l2r * dut;
-  D[2] = l1a1 * (vt - ct * nv[1]) + l5a5 * (vt + ct * nv[1]) + l2a2 * vt + l2r * dvt;
-  D[3] = l1a1 * (wt - ct * nv[2]) + l5a5 * (wt + ct * nv[2]) + l2a2 * wt + l2r * dwt;
-  D[4] = l1a1 * (Ht - unt * ct) + l5a5 * (Ht + unt * ct) + l2a2 * R(0.5) * q2 + l2r * (ut * dut + vt * dvt + wt * dwt);
+  D[0] = s15 + l2a2;
+  D[1] = D[0] * ut + c15 * nv[0] + l2r * dut;
+  D[2] = D[0] * vt + c15 * nv[1] + l2r * dvt;
+  D[3] = D[0] * wt + c15 * nv[2] + l2r * dwt;
+  D[4] = s15 * Ht + c15 * unt + l2a2 * R(0.5) * q2 + l2r * (ut * dut + vt * dvt + wt * dwt);
 #pragma unroll
   for (int v = 0; v < 5; ++v) F[v] = R(0.5) * (FL[v] + FR[v] - D[v]);
 }
