@@ -48,6 +48,12 @@ VOLUME_DRAM_BYTES_PER_ELEMENT = (2060.267008e6 + 545.168640e6) / 24 ** 3
 VOLUME_F32_DRAM_BYTES_PER_ELEMENT = (3492.2e6 + 1625.3e6) / 32 ** 3
 
 
+# how the FP64 flop counts below are made: from the statements of each kernel as built (an FMA two
+# flops, a division or reciprocal square root one; the even-odd line sweeps count what they execute),
+# which ncu's executed DFMA/DADD/DMUL counts match to a few per cent
+FLOPS_BASIS = "kernel statements as built (FMA = 2, div/rsqrt = 1, even-odd sweeps as executed)"
+
+
 def scaled_traffic(bytes_per_element, n_elems: int, applies: bool = True):
     """A captured per-element DRAM count scaled to a launch by the element count; None when there is no
     capture of the current kernel (or it does not apply to this configuration)."""
@@ -438,7 +444,7 @@ def step_roofline(N: int, dof_stage_per_s: float, peak_fp64: float) -> dict:
     pid = 1.0 / dof_stage_per_s
     return {"bound": "alu", "flops_per_dof_stage": flops, "pid_roof_s": flops / peak_fp64, "pid_s": pid,
             "frac": flops / peak_fp64 / pid, "peak": peak_fp64 / 1e12, "unit": "TFLOP/s",
-            "peak_source": "measured FP64 FMA probe (dg_probe_fma), live"}
+            "peak_source": "measured FP64 FMA probe (dg_probe_fma), live", "flops_basis": FLOPS_BASIS}
 
 
 ADJOINT_WORKLOAD = "tgv_ns_n5_24x24x24_adjoint"
@@ -807,7 +813,8 @@ def run_gpu(args):
                     "achieved": achieved / 1e12, "peak": peak_fp64 / 1e12, "unit": "TFLOP/s",
                     "frac": achieved / peak_fp64,
                     "traffic": scaled_traffic(VOLUME_DRAM_BYTES_PER_ELEMENT, w.n_elems),
-                    "flops_per_launch": flops_launch, "peak_source": "measured FP64 FMA probe (dg_probe_fma), live"}
+                    "flops_per_launch": flops_launch, "peak_source": "measured FP64 FMA probe (dg_probe_fma), live",
+                    "flops_basis": FLOPS_BASIS}
     state_bytes = U.numel() * 8
     if rank != 0:
         return
